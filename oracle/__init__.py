@@ -1,0 +1,253 @@
+"""FP64 CPU oracle of the pixelated-LArTPC charge path (arXiv:2212.09807, Sec. 3).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the
+benchmark's CPU-baseline leg, never by the CUDA path.  The arithmetic lives in
+``larsim_oracle.c`` (plain C, FP64); this module builds it with gcc and
+marshals numpy arrays through ctypes.  Parity pins: see tests/test_oracle_*.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "larsim_oracle.c")
+LIB = os.path.join(HERE, "liblarsim_oracle.so")
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle library with gcc (IEEE order kept: no FMA contraction)."""
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        tmp = LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
+                               "-ffp-contract=off", "-fno-fast-math", "-Wall",
+                               SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+class _Cfg(C.Structure):
+    _fields_ = [
+        ("n_mod_x", C.c_int32), ("n_mod_y", C.c_int32), ("n_tpc", C.c_int32),
+        ("tiles_x", C.c_int32), ("tiles_y", C.c_int32), ("px_per_tile", C.c_int32),
+        ("pitch", C.c_double), ("drift_len", C.c_double),
+        ("recomb_model", C.c_int32),
+        ("Ab", C.c_double), ("kb", C.c_double), ("alpha", C.c_double), ("beta", C.c_double),
+        ("efield", C.c_double), ("density", C.c_double), ("w_ion", C.c_double),
+        ("vdrift", C.c_double), ("lifetime", C.c_double), ("DL", C.c_double), ("DT", C.c_double),
+        ("step", C.c_double), ("M", C.c_int32), ("clip", C.c_double),
+        ("tick", C.c_double), ("n_ticks", C.c_int32), ("t_w0", C.c_double),
+        ("thr", C.c_double), ("s_reset", C.c_double), ("s_disc", C.c_double),
+        ("s_unc", C.c_double), ("gain", C.c_double), ("lsb_mV", C.c_double),
+        ("hold", C.c_int32), ("min_int", C.c_int32), ("periodic", C.c_int32),
+        ("adc_bits", C.c_int32),
+        ("seed", C.c_uint64),
+        ("nb", C.c_int32), ("nt", C.c_int32), ("bins_per_pitch", C.c_int32), ("pad", C.c_int32),
+    ]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(LIB)
+        P = C.POINTER
+        f32p, f64p, i32p, i64p, u32p = (P(C.c_float), P(C.c_double), P(C.c_int32),
+                                        P(C.c_int64), P(C.c_uint32))
+        L.ora_cfg_size.restype = C.c_size_t
+        L.ora_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.ora_normals.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32,
+                                  C.c_uint32, C.c_uint32, f64p]
+        L.ora_recomb.argtypes = [P(_Cfg), C.c_double]
+        L.ora_recomb.restype = C.c_double
+        L.ora_quench_drift.argtypes = [P(_Cfg), C.c_int64] + [f32p] * 9 + [f64p] * 8 + [i32p, i32p]
+        L.ora_cheb_distance.argtypes = [C.c_double] * 6
+        L.ora_cheb_distance.restype = C.c_double
+        L.ora_map_radius.argtypes = [P(_Cfg), C.c_double]
+        L.ora_map_radius.restype = C.c_double
+        L.ora_map_segment.argtypes = [P(_Cfg), C.c_float, C.c_float, C.c_float, C.c_float,
+                                      C.c_double, C.c_int32, i32p, f64p, C.c_int64]
+        L.ora_map_segment.restype = C.c_int64
+        L.ora_pair_margin.argtypes = [P(_Cfg), C.c_float, C.c_float, C.c_float, C.c_float,
+                                      C.c_double, C.c_int32, C.c_int32]
+        L.ora_pair_margin.restype = C.c_double
+        L.ora_pixel_current.argtypes = ([P(_Cfg), f64p] + [f32p] * 8 + [f64p] * 3
+                                        + [i32p, i32p, C.c_uint64, C.c_int32, i64p, C.c_int64, f64p])
+        L.ora_electronics.argtypes = [P(_Cfg), C.c_uint64, C.c_int32, f64p, C.c_int64,
+                                      i32p, i32p, i32p, f64p, C.c_double, i32p]
+        L.ora_electronics.restype = C.c_int64
+        assert L.ora_cfg_size() == C.sizeof(_Cfg), "oracle config struct mismatch"
+        _lib = L
+    return _lib
+
+
+def _f32(v):
+    return float(np.float32(v))
+
+
+def make_cfg(cfg: dict, lut_par: dict) -> _Cfg:
+    """Oracle configuration: FP32 configuration values widened to FP64."""
+    c = _Cfg()
+    for k in ("n_mod_x", "n_mod_y", "n_tpc", "tiles_x", "tiles_y", "px_per_tile"):
+        setattr(c, k, int(cfg[k]))
+    c.pitch = _f32(cfg["pitch_cm"])
+    c.drift_len = _f32(cfg["drift_len_cm"])
+    c.recomb_model = int(cfg["recomb_model"])
+    c.Ab, c.kb = _f32(cfg["birks_Ab"]), _f32(cfg["birks_kb"])
+    c.alpha, c.beta = _f32(cfg["box_alpha"]), _f32(cfg["box_beta"])
+    c.efield, c.density = _f32(cfg["efield_kV_cm"]), _f32(cfg["lar_density_g_cm3"])
+    c.w_ion = _f32(cfg["w_ion_MeV"])
+    c.vdrift, c.lifetime = _f32(cfg["vdrift_cm_us"]), _f32(cfg["lifetime_us"])
+    c.DL, c.DT = _f32(cfg["diff_long_cm2_s"]), _f32(cfg["diff_tran_cm2_s"])
+    c.step, c.M, c.clip = _f32(cfg["sample_step_cm"]), int(cfg["mc_per_sample"]), _f32(cfg["diff_clip_sigma"])
+    c.tick, c.n_ticks, c.t_w0 = _f32(cfg["tick_us"]), int(cfg["n_ticks"]), _f32(cfg["t_window0_us"])
+    c.thr, c.s_reset = _f32(cfg["thr_e"]), _f32(cfg["sigma_reset_e"])
+    c.s_disc, c.s_unc = _f32(cfg["sigma_disc_e"]), _f32(cfg["sigma_unc_e"])
+    c.gain, c.lsb_mV = _f32(cfg["gain_e_per_mV"]), _f32(cfg["adc_lsb_mV"])
+    c.hold, c.min_int = int(cfg["hold_ticks"]), int(cfg["min_adc_interval_ticks"])
+    c.periodic, c.adc_bits = int(cfg["periodic_reset_ticks"]), int(cfg["adc_bits"])
+    c.seed = int(cfg["seed"]) & 0xFFFFFFFFFFFFFFFF
+    c.nb, c.nt, c.bins_per_pitch = int(lut_par["nb"]), int(lut_par["nt"]), int(lut_par["bins_per_pitch"])
+    return c
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def philox4x32_10(ctr, key):
+    """Raw Philox4x32-10 block for a 4-word counter and a 2-word key."""
+    L = lib()
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    o = np.zeros(4, dtype=np.uint32)
+    L.ora_philox4x32_10(_p(c, C.c_uint32), _p(k, C.c_uint32), _p(o, C.c_uint32))
+    return o
+
+
+def normals(seed, event_id, c0, c1, c2, c3=0):
+    L = lib()
+    o = np.zeros(4)
+    L.ora_normals(seed, event_id, c0, c1, c2, c3, _p(o, C.c_double))
+    return o
+
+
+class Oracle:
+    """Per-step oracle for one configuration and response table."""
+
+    def __init__(self, cfg: dict, lut_par: dict, lut: np.ndarray | None = None):
+        self.L = lib()
+        self.cfg = cfg
+        self.c = make_cfg(cfg, lut_par)
+        self.nb = int(lut_par["nb"])
+        self.nt = int(lut_par["nt"])
+        if lut is not None:
+            lut = np.ascontiguousarray(np.asarray(lut, dtype=np.float64)[..., : self.nt])
+            assert lut.shape == (self.nb, self.nb, self.nt)
+        self.lut = lut
+        self.npx_x = cfg["tiles_x"] * cfg["px_per_tile"]
+        self.npx_y = cfg["tiles_y"] * cfg["px_per_tile"]
+        self.n_anodes = cfg["n_mod_x"] * cfg["n_mod_y"] * cfg["n_tpc"]
+
+    # -- steps 1-2 ---------------------------------------------------------
+    def recomb(self, dedx: float) -> float:
+        return self.L.ora_recomb(C.byref(self.c), float(dedx))
+
+    def quench_drift(self, seg: dict) -> dict:
+        n = len(seg["x0"])
+        cols = [np.ascontiguousarray(seg[k], dtype=np.float32)
+                for k in ("x0", "y0", "z0", "t0", "x1", "y1", "z1", "t1", "dE")]
+        names = ("dx", "dedx", "R", "QR", "Qa", "t_drift", "sigma_T", "sigma_L")
+        out = {k: np.zeros(n) for k in names}
+        out["anode"] = np.zeros(n, dtype=np.int32)
+        out["n_samples"] = np.zeros(n, dtype=np.int32)
+        self.L.ora_quench_drift(C.byref(self.c), n, *[_p(a, C.c_float) for a in cols],
+                                *[_p(out[k], C.c_double) for k in names],
+                                _p(out["anode"], C.c_int32), _p(out["n_samples"], C.c_int32))
+        out["_seg"] = cols
+        return out
+
+    # -- step 3 ------------------------------------------------------------
+    def map_radius(self, sigma_T: float) -> float:
+        return self.L.ora_map_radius(C.byref(self.c), float(sigma_T))
+
+    def map_segment(self, seg: dict, dr: dict, s: int):
+        """(ids, margins) of the pixels segment s is mapped to (brute force)."""
+        cap = 4096
+        while True:
+            ids = np.zeros(cap, dtype=np.int32)
+            mg = np.zeros(cap)
+            n = self.L.ora_map_segment(C.byref(self.c), float(seg["x0"][s]), float(seg["y0"][s]),
+                                       float(seg["x1"][s]), float(seg["y1"][s]),
+                                       float(dr["sigma_T"][s]), int(dr["anode"][s]),
+                                       _p(ids, C.c_int32), _p(mg, C.c_double), cap)
+            if n <= cap:
+                return ids[:n].copy(), mg[:n].copy()
+            cap = int(n)
+
+    def pair_margin(self, seg, dr, s, pixel) -> float:
+        return self.L.ora_pair_margin(C.byref(self.c), float(seg["x0"][s]), float(seg["y0"][s]),
+                                      float(seg["x1"][s]), float(seg["y1"][s]),
+                                      float(dr["sigma_T"][s]), int(dr["anode"][s]), int(pixel))
+
+    def pixel_map(self, seg: dict, dr: dict):
+        """Brute-force map of every segment: returns (pixel -> sorted segment list, pairs, margins)."""
+        pix = {}
+        pairs_s, pairs_p, margins = [], [], []
+        for s in range(len(seg["x0"])):
+            if dr["anode"][s] < 0:
+                continue
+            ids, mg = self.map_segment(seg, dr, s)
+            for p, m in zip(ids.tolist(), mg.tolist()):
+                pix.setdefault(p, []).append(s)
+                pairs_s.append(s)
+                pairs_p.append(p)
+                margins.append(m)
+        return pix, np.array(pairs_s, dtype=np.int64), np.array(pairs_p, dtype=np.int64), np.array(margins)
+
+    def segments_for_pixel(self, seg: dict, dr: dict, pixel: int):
+        """Segments mapped to one pixel and their margins (brute force over segments)."""
+        out, mg = [], []
+        for s in np.nonzero(dr["anode"] >= 0)[0].tolist():
+            m = self.pair_margin(seg, dr, s, pixel)
+            if m >= 0:
+                out.append(s)
+                mg.append(m)
+        return np.array(out, dtype=np.int64), np.array(mg)
+
+    # -- step 4 ------------------------------------------------------------
+    def pixel_current(self, seg: dict, dr: dict, pixel: int, segs, event_id: int = 0,
+                      lut: np.ndarray | None = None) -> np.ndarray:
+        lut = self.lut if lut is None else np.ascontiguousarray(np.asarray(lut, np.float64)[..., : self.nt])
+        assert lut is not None
+        cols = dr["_seg"]
+        segs = np.ascontiguousarray(segs, dtype=np.int64)
+        I = np.zeros(int(self.c.n_ticks))
+        self.L.ora_pixel_current(C.byref(self.c), _p(lut, C.c_double),
+                                 *[_p(a, C.c_float) for a in cols[:8]],
+                                 _p(dr["Qa"], C.c_double), _p(dr["sigma_T"], C.c_double),
+                                 _p(dr["sigma_L"], C.c_double), _p(dr["anode"], C.c_int32),
+                                 _p(dr["n_samples"], C.c_int32), event_id, int(pixel),
+                                 _p(segs, C.c_int64), len(segs), _p(I, C.c_double))
+        return I
+
+    # -- step 5 ------------------------------------------------------------
+    def electronics(self, pixel: int, I: np.ndarray, event_id: int = 0, band: float = 0.0) -> dict:
+        I = np.ascontiguousarray(I, dtype=np.float64)
+        assert len(I) == self.c.n_ticks
+        cap = self.c.n_ticks
+        tc = np.zeros(cap, np.int32)
+        ta = np.zeros(cap, np.int32)
+        ad = np.zeros(cap, np.int32)
+        qv = np.zeros(cap)
+        tie = np.zeros(1, np.int32)
+        n = self.L.ora_electronics(C.byref(self.c), event_id, int(pixel), _p(I, C.c_double), cap,
+                                   _p(tc, C.c_int32), _p(ta, C.c_int32), _p(ad, C.c_int32),
+                                   _p(qv, C.c_double), float(band), _p(tie, C.c_int32))
+        return dict(t_cross=tc[:n].copy(), t_adc=ta[:n].copy(), adc=ad[:n].copy(),
+                    q=qv[:n].copy(), tie_tick=int(tie[0]))

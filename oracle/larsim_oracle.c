@@ -1,0 +1,502 @@
+/*
+ * larsim_oracle.c -- plain, slow FP64 CPU oracle of the charge-readout path of
+ * "Highly-parallelized simulation of a pixelated LArTPC on a GPU"
+ * (DUNE collaboration, arXiv:2212.09807, Sec. 3).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code,
+ * header, table or constant generator with the CUDA path; the only thing both
+ * sides receive is the seeded synthetic input (segments, configuration
+ * numbers, response table).
+ *
+ * Every step follows the paper's statement in its own order and notation:
+ *   ora_recomb          Sec. 3.1, Eq. (birks) and Eq. (box)
+ *   ora_quench_drift    Sec. 3.1 + Sec. 3.2, Eq. (drift), Eq. (lifetime) and
+ *                       the diffusion width sigma = sqrt(2 D t_drift)
+ *   ora_map_segment     Sec. 3.3.2 (pixels a segment can induce on): brute
+ *                       force over every pixel of the anode
+ *   ora_pixel_current   Sec. 3.3.2, the charge density rho (N points x M
+ *                       perturbations) and Eq. (current), with the table of
+ *                       Sec. 3.3.1 interpolated trilinearly
+ *   ora_electronics     Sec. 3.4 (CSA integration, discriminator with noise,
+ *                       hold, ADC, reset)
+ *   ora_philox4x32_10   counter-based generator of Salmon et al., SC'11
+ *                       ("Parallel random numbers: as easy as 1, 2, 3")
+ *
+ * Arithmetic is FP64 throughout.  Integer decisions that the path takes from
+ * floating-point values (which drift volume a segment belongs to, how many
+ * points it is cut into) are taken in FP64 from the FP32 inputs with plain
+ * IEEE operations in the order written here; the electronics' threshold and
+ * ADC decisions round their FP64 operands to FP32 first (the precision the
+ * GPU kernels decide in).  Where a decision lies within a stated band of its
+ * threshold, the oracle reports it so that tests can exclude that tie.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORA_PI 3.14159265358979323846
+
+typedef struct ora_cfg {
+    /* geometry */
+    int32_t n_mod_x, n_mod_y, n_tpc, tiles_x, tiles_y, px_per_tile;
+    double pitch, drift_len;
+    /* recombination and drift */
+    int32_t recomb_model;
+    double Ab, kb, alpha, beta, efield, density, w_ion;
+    double vdrift, lifetime, DL, DT; /* D in cm^2/s */
+    /* sampling */
+    double step;
+    int32_t M;
+    double clip;
+    /* readout */
+    double tick;
+    int32_t n_ticks;
+    double t_w0;
+    /* front end */
+    double thr, s_reset, s_disc, s_unc, gain, lsb_mV;
+    int32_t hold, min_int, periodic, adc_bits;
+    uint64_t seed;
+    /* response table */
+    int32_t nb, nt, bins_per_pitch;
+    int32_t pad;
+} ora_cfg;
+
+size_t ora_cfg_size(void) { return sizeof(ora_cfg); }
+
+/* ------------------------------------------------------------------ RNG -- */
+
+static void mulhilo32(uint32_t a, uint32_t b, uint32_t *hi, uint32_t *lo)
+{
+    uint64_t p = (uint64_t)a * (uint64_t)b;
+    *hi = (uint32_t)(p >> 32);
+    *lo = (uint32_t)p;
+}
+
+/* Philox4x32 with 10 rounds: each round multiplies words 0 and 2 by the two
+ * round multipliers, exchanges the words and mixes in the key; the key is
+ * bumped by the two Weyl constants between rounds. */
+void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hi0, lo0, hi1, lo1;
+        mulhilo32(0xD2511F53u, c0, &hi0, &lo0);
+        mulhilo32(0xCD9E8D57u, c2, &hi1, &lo1);
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Uniform in (0,1): (x + 1/2) 2^-32, exact in FP64. */
+static double ora_u01(uint32_t x) { return ((double)x + 0.5) * (1.0 / 4294967296.0); }
+
+/* Four standard normals from one Philox block by the Box-Muller transform:
+ * (n0, n1) from (u0, u1) and (n2, n3) from (u2, u3).  Key = seed ^ event id. */
+void ora_normals(uint64_t seed, uint64_t event_id, uint32_t c0, uint32_t c1,
+                 uint32_t c2, uint32_t c3, double n[4])
+{
+    uint64_t k = seed ^ event_id;
+    uint32_t key[2] = {(uint32_t)k, (uint32_t)(k >> 32)};
+    uint32_t ctr[4] = {c0, c1, c2, c3};
+    uint32_t x[4];
+    ora_philox4x32_10(ctr, key, x);
+    double r0 = sqrt(-2.0 * log(ora_u01(x[0])));
+    double a0 = 2.0 * ORA_PI * ora_u01(x[1]);
+    double r1 = sqrt(-2.0 * log(ora_u01(x[2])));
+    double a1 = 2.0 * ORA_PI * ora_u01(x[3]);
+    n[0] = r0 * cos(a0);
+    n[1] = r0 * sin(a0);
+    n[2] = r1 * cos(a1);
+    n[3] = r1 * sin(a1);
+}
+
+/* ------------------------------------------------------- recombination -- */
+
+/* Recombination factor at stopping power dEdx (MeV/cm), Sec. 3.1.
+ * epsilon = E-field (kV/cm) x LAr density (g/cm^3).
+ * Birks, Eq. (birks):  R = A_b / (1 + (k_b/epsilon) dE/dx)
+ * modified Box, Eq. (box):  R = ln(alpha + (beta/epsilon) dE/dx) / ((beta/epsilon) dE/dx) */
+double ora_recomb(const ora_cfg *c, double dEdx)
+{
+    double eps = c->efield * c->density;
+    if (c->recomb_model == 1) {
+        double xi = c->beta / eps * dEdx;
+        return log(c->alpha + xi) / xi;
+    }
+    return c->Ab / (1.0 + c->kb / eps * dEdx);
+}
+
+/* ------------------------------------------------------------ geometry -- */
+
+typedef struct {
+    int ok, anode, mx, my, tpc;
+    double ox, oy, za;
+} ora_loc;
+
+/* Drift volume of a point.  Modules tile x-y from the origin, each
+ * npx*pitch wide; TPC 0 spans z in [0, D) with its anode at z = 0, TPC 1
+ * spans [D, 2D] with its anode at z = 2D (cathode at z = D). */
+static ora_loc ora_locate(const ora_cfg *c, double x, double y, double z)
+{
+    ora_loc L;
+    memset(&L, 0, sizeof L);
+    double Wx = (double)(c->tiles_x * c->px_per_tile) * c->pitch;
+    double Wy = (double)(c->tiles_y * c->px_per_tile) * c->pitch;
+    double xmax = (double)c->n_mod_x * Wx;
+    double ymax = (double)c->n_mod_y * Wy;
+    double zmax = (double)c->n_tpc * c->drift_len;
+    if (!(x >= 0.0 && x < xmax && y >= 0.0 && y < ymax && z >= 0.0 && z <= zmax)) {
+        L.ok = 0;
+        L.anode = -1;
+        return L;
+    }
+    int mx = (int)floor(x / Wx);
+    int my = (int)floor(y / Wy);
+    if (mx > c->n_mod_x - 1) mx = c->n_mod_x - 1;
+    if (my > c->n_mod_y - 1) my = c->n_mod_y - 1;
+    int tpc = (c->n_tpc == 2 && z >= c->drift_len) ? 1 : 0;
+    L.ok = 1;
+    L.mx = mx;
+    L.my = my;
+    L.tpc = tpc;
+    L.anode = (my * c->n_mod_x + mx) * c->n_tpc + tpc;
+    L.ox = (double)mx * Wx;
+    L.oy = (double)my * Wy;
+    L.za = tpc == 0 ? 0.0 : 2.0 * c->drift_len;
+    return L;
+}
+
+/* Centre (global cm) of a pixel and its anode's z. */
+static void ora_pixel_centre(const ora_cfg *c, int32_t pixel, double *xc, double *yc,
+                             double *za, int32_t *anode)
+{
+    int32_t nx = c->tiles_x * c->px_per_tile;
+    int32_t ny = c->tiles_y * c->px_per_tile;
+    int32_t g = pixel / (nx * ny);
+    int32_t rem = pixel % (nx * ny);
+    int32_t iy = rem / nx, ix = rem % nx;
+    int32_t m = g / c->n_tpc, tpc = g % c->n_tpc;
+    int32_t mx = m % c->n_mod_x, my = m / c->n_mod_x;
+    double Wx = (double)nx * c->pitch, Wy = (double)ny * c->pitch;
+    *xc = (double)mx * Wx + ((double)ix + 0.5) * c->pitch;
+    *yc = (double)my * Wy + ((double)iy + 0.5) * c->pitch;
+    *za = tpc == 0 ? 0.0 : 2.0 * c->drift_len;
+    *anode = g;
+}
+
+/* --------------------------------------------------- quench and drift -- */
+
+/* Steps 1-2 for n segments (SoA FP32 input, cm / us / MeV).
+ * Outputs per segment: dx (cm), dE/dx, R, Q_R and Q_a (electrons), t_drift
+ * (us), sigma_T and sigma_L (cm), anode (-1 = inactive) and the number of
+ * points N along the segment (10 um spacing, Sec. 3.3.2).
+ * A segment is active when its midpoint lies in a drift volume and its
+ * length is at least 1e-6 cm (dE/dx is undefined for a point deposit). */
+void ora_quench_drift(const ora_cfg *c, int64_t n,
+                      const float *x0, const float *y0, const float *z0, const float *t0,
+                      const float *x1, const float *y1, const float *z1, const float *t1,
+                      const float *dE,
+                      double *dx_out, double *dedx_out, double *R_out, double *QR_out,
+                      double *Qa, double *t_drift, double *sigma_T, double *sigma_L,
+                      int32_t *anode, int32_t *n_samples)
+{
+    (void)t0; (void)t1;
+    for (int64_t i = 0; i < n; ++i) {
+        double ddx = (double)x1[i] - (double)x0[i];
+        double ddy = (double)y1[i] - (double)y0[i];
+        double ddz = (double)z1[i] - (double)z0[i];
+        double dx = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
+        double xm = 0.5 * ((double)x0[i] + (double)x1[i]);
+        double ym = 0.5 * ((double)y0[i] + (double)y1[i]);
+        double zm = 0.5 * ((double)z0[i] + (double)z1[i]);
+        ora_loc L = ora_locate(c, xm, ym, zm);
+        dx_out[i] = dx;
+        if (!L.ok || dx < 1e-6) {
+            dedx_out[i] = R_out[i] = QR_out[i] = 0.0;
+            Qa[i] = t_drift[i] = sigma_T[i] = sigma_L[i] = 0.0;
+            anode[i] = -1;
+            n_samples[i] = 0;
+            continue;
+        }
+        /* Sec. 3.1: Q_0 = E / W_ion, Q_R = R Q_0 */
+        double dedx = (double)dE[i] / dx;
+        double R = ora_recomb(c, dedx);
+        double Q0 = (double)dE[i] / c->w_ion;
+        double QR = R * Q0;
+        /* Sec. 3.2, Eq. (drift): t = |z - z_anode| / v_drift, at the midpoint */
+        double td = fabs(zm - L.za) / c->vdrift;
+        /* Eq. (lifetime) */
+        double qa = QR * exp(-td / c->lifetime);
+        /* sigma = sqrt(2 D t), D converted from cm^2/s to cm^2/us */
+        double sT = sqrt(2.0 * (c->DT * 1e-6) * td);
+        double sL = sqrt(2.0 * (c->DL * 1e-6) * td);
+        double N = ceil(dx / c->step);
+        if (N < 1.0) N = 1.0;
+        dedx_out[i] = dedx;
+        R_out[i] = R;
+        QR_out[i] = QR;
+        Qa[i] = qa;
+        t_drift[i] = td;
+        sigma_T[i] = sT;
+        sigma_L[i] = sL;
+        anode[i] = L.anode;
+        n_samples[i] = (int32_t)N;
+    }
+}
+
+/* ------------------------------------------------------------ pixel map -- */
+
+/* Chebyshev (L-infinity) distance between the 2-D segment (ax,ay)-(bx,by)
+ * and the point (px,py): min over t in [0,1] of
+ * max(|ax + t(bx-ax) - px|, |ay + t(by-ay) - py|).  The function is convex
+ * and piecewise linear in t, so its minimum sits at t = 0, t = 1, a zero of
+ * one of the two terms, or a point where the two terms are equal. */
+double ora_cheb_distance(double ax, double ay, double bx, double by, double px, double py)
+{
+    double u0 = ax - px, du = bx - ax;
+    double v0 = ay - py, dv = by - ay;
+    double cand[8];
+    int nc = 0;
+    cand[nc++] = 0.0;
+    cand[nc++] = 1.0;
+    if (du != 0.0) cand[nc++] = -u0 / du;
+    if (dv != 0.0) cand[nc++] = -v0 / dv;
+    if (du - dv != 0.0) cand[nc++] = (v0 - u0) / (du - dv);
+    if (du + dv != 0.0) cand[nc++] = -(u0 + v0) / (du + dv);
+    double best = INFINITY;
+    for (int i = 0; i < nc; ++i) {
+        double t = cand[i];
+        if (!(t >= 0.0 && t <= 1.0)) continue;
+        double a = fabs(u0 + t * du), b = fabs(v0 + t * dv);
+        double f = a > b ? a : b;
+        if (f < best) best = f;
+    }
+    return best;
+}
+
+/* Half-width of the square around a pixel centre inside which a segment can
+ * induce current on it: the table reaches (nb + 1/2) bins (its last node sits
+ * at (nb - 1/2) bins and interpolation runs to the next, zero, node) and every
+ * diffusion offset is clipped at clip * sigma_T. */
+double ora_map_radius(const ora_cfg *c, double sigma_T)
+{
+    double h = c->pitch / (double)c->bins_per_pitch;
+    return ((double)c->nb + 0.5) * h + c->clip * sigma_T;
+}
+
+/* Pixels of the segment's own anode that the segment can induce on
+ * (Sec. 3.3.2): brute force over every pixel of that anode.  Writes up to
+ * ``cap`` pixel ids in increasing order and, per id, the distance margin
+ * R_map - d (>= 0).  Returns the number of mapped pixels (may exceed cap). */
+int64_t ora_map_segment(const ora_cfg *c, float x0, float y0, float x1, float y1,
+                        double sigma_T, int32_t anode, int32_t *ids, double *margin,
+                        int64_t cap)
+{
+    if (anode < 0) return 0;
+    int32_t nx = c->tiles_x * c->px_per_tile;
+    int32_t ny = c->tiles_y * c->px_per_tile;
+    double R = ora_map_radius(c, sigma_T);
+    int64_t cnt = 0;
+    for (int32_t iy = 0; iy < ny; ++iy) {
+        for (int32_t ix = 0; ix < nx; ++ix) {
+            int32_t pid = anode * nx * ny + iy * nx + ix;
+            double xc, yc, za;
+            int32_t g;
+            ora_pixel_centre(c, pid, &xc, &yc, &za, &g);
+            double d = ora_cheb_distance(x0, y0, x1, y1, xc, yc);
+            if (d <= R) {
+                if (cnt < cap) {
+                    ids[cnt] = pid;
+                    if (margin) margin[cnt] = R - d;
+                }
+                ++cnt;
+            }
+        }
+    }
+    return cnt;
+}
+
+/* Margin R_map - d of one (segment, pixel) pair; negative when not mapped. */
+double ora_pair_margin(const ora_cfg *c, float x0, float y0, float x1, float y1,
+                       double sigma_T, int32_t anode, int32_t pixel)
+{
+    double xc, yc, za;
+    int32_t g;
+    ora_pixel_centre(c, pixel, &xc, &yc, &za, &g);
+    if (g != anode || anode < 0) return -INFINITY;
+    return ora_map_radius(c, sigma_T) - ora_cheb_distance(x0, y0, x1, y1, xc, yc);
+}
+
+/* ------------------------------------------------------ induced current -- */
+
+/* Response value R[bx][by][j] with out-of-table nodes and ticks reading 0. */
+static double ora_lut(const ora_cfg *c, const double *lut, int bx, int by, int64_t j)
+{
+    if (bx >= c->nb || by >= c->nb || j < 0 || j >= c->nt) return 0.0;
+    return lut[((int64_t)bx * c->nb + by) * c->nt + j];
+}
+
+/* Current I[k], k in [0, n_ticks), induced on one pixel by the listed
+ * segments (Sec. 3.3.2).  Each segment s is cut into N_s points at
+ * r_mu = r_s + (mu + 1/2)/N_s (r_e - r_s) (same for the time coordinate); each
+ * point gets M perturbations (sigma_T n0, sigma_T n1, sigma_L n2) with standard
+ * normals from Philox counter (s, mu M + nu, 1, 0), clipped at +-clip; each
+ * perturbed point carries q = Q_a / (N_s M) and arrives at
+ * t_a = t_mu + |z_mu + dz - z_anode| / v_drift (Eq. (drift) per point).
+ * The table is read at the folded offset (|dx|, |dy|) by bilinear
+ * interpolation between bin-centred nodes (node nb reads 0; offsets below
+ * half a bin read node 0) and at the fractional arrival tick by linear
+ * interpolation, as in Eq. (current):
+ *   I[k] += q ((1-f) Rxy[k - A + L - 1] + f Rxy[k - A + L - 2]),
+ *   a = (t_a - t_window0) / tick, A = floor(a), f = a - A.
+ * The pixel's current is written to I (zeroed first). */
+void ora_pixel_current(const ora_cfg *c, const double *lut,
+                       const float *x0, const float *y0, const float *z0, const float *t0,
+                       const float *x1, const float *y1, const float *z1, const float *t1,
+                       const double *Qa, const double *sigma_T, const double *sigma_L,
+                       const int32_t *anode, const int32_t *n_samples,
+                       uint64_t event_id, int32_t pixel, const int64_t *segs, int64_t n_segs,
+                       double *I)
+{
+    int T = c->n_ticks;
+    int L = c->nt;
+    double h = c->pitch / (double)c->bins_per_pitch;
+    double xc, yc, za;
+    int32_t g;
+    ora_pixel_centre(c, pixel, &xc, &yc, &za, &g);
+    for (int k = 0; k < T; ++k) I[k] = 0.0;
+    double *Rxy = (double *)malloc(sizeof(double) * (size_t)L);
+    for (int64_t si = 0; si < n_segs; ++si) {
+        int64_t s = segs[si];
+        if (anode[s] != g) continue;
+        int64_t N = n_samples[s];
+        double q = Qa[s] / ((double)N * (double)c->M);
+        for (int64_t mu = 0; mu < N; ++mu) {
+            double u = ((double)mu + 0.5) / (double)N;
+            double x = (double)x0[s] + u * ((double)x1[s] - (double)x0[s]);
+            double y = (double)y0[s] + u * ((double)y1[s] - (double)y0[s]);
+            double z = (double)z0[s] + u * ((double)z1[s] - (double)z0[s]);
+            double t = (double)t0[s] + u * ((double)t1[s] - (double)t0[s]);
+            for (int nu = 0; nu < c->M; ++nu) {
+                double n[4];
+                ora_normals(c->seed, event_id, (uint32_t)s, (uint32_t)(mu * c->M + nu), 1u, 0u, n);
+                for (int d = 0; d < 3; ++d) {
+                    if (n[d] > c->clip) n[d] = c->clip;
+                    if (n[d] < -c->clip) n[d] = -c->clip;
+                }
+                double dxp = x + sigma_T[s] * n[0] - xc;
+                double dyp = y + sigma_T[s] * n[1] - yc;
+                double zz = z + sigma_L[s] * n[2];
+                double ta = t + fabs(zz - za) / c->vdrift;
+                double xi = fabs(dxp) / h - 0.5;
+                double yi = fabs(dyp) / h - 0.5;
+                if (xi < 0.0) xi = 0.0;
+                if (yi < 0.0) yi = 0.0;
+                if (xi >= (double)c->nb || yi >= (double)c->nb) continue;
+                int bx = (int)floor(xi), by = (int)floor(yi);
+                double wx = xi - bx, wy = yi - by;
+                for (int j = 0; j < L; ++j) {
+                    Rxy[j] = (1.0 - wx) * (1.0 - wy) * ora_lut(c, lut, bx, by, j)
+                           + wx * (1.0 - wy) * ora_lut(c, lut, bx + 1, by, j)
+                           + (1.0 - wx) * wy * ora_lut(c, lut, bx, by + 1, j)
+                           + wx * wy * ora_lut(c, lut, bx + 1, by + 1, j);
+                }
+                double a = (ta - c->t_w0) / c->tick;
+                double Af = floor(a);
+                double f = a - Af;
+                int64_t A = (int64_t)Af;
+                for (int k = 0; k < T; ++k) {
+                    int64_t j1 = (int64_t)k - A + L - 1;
+                    int64_t j2 = j1 - 1;
+                    double r1 = (j1 >= 0 && j1 < L) ? Rxy[j1] : 0.0;
+                    double r2 = (j2 >= 0 && j2 < L) ? Rxy[j2] : 0.0;
+                    I[k] += q * ((1.0 - f) * r1 + f * r2);
+                }
+            }
+        }
+    }
+    free(Rxy);
+}
+
+/* ---------------------------------------------------------- electronics -- */
+
+/* Front end of one pixel (Sec. 3.4), tick by tick:
+ *   q += I[k] (charge-sensitive amplifier integrates the current);
+ *   idle: v = q + s_unc n_unc(k) is compared with thr + s_disc n_disc(k)
+ *     (Philox counter (pixel, k, 2, 0): n_unc = n0, n_disc = n1); on a
+ *     crossing the digitisation is scheduled at
+ *     t_adc = max(k + hold, last_adc + min_interval);
+ *   at k == t_adc: v = q + s_unc n_unc(k), ADC = clamp(floor(v / lsb_e), 0,
+ *     2^bits - 1) with lsb_e = gain x lsb_mV, the hit (pixel, t_cross, t_adc,
+ *     ADC, v) is stored, and the CSA resets to a pedestal s_reset n0 of
+ *     counter (pixel, k, 3, 0);
+ *   optional periodic reset (period > 0, idle, k % period == 0, k > 0):
+ *     q = s_reset n0 of counter (pixel, k, 4, 0) before the tick's current.
+ * A digitisation still pending at the end of the window is dropped.
+ * Threshold and ADC decisions compare FP32 roundings of the FP64 operands.
+ * ``tie_tick`` receives the first tick whose decision lies within ``band``
+ * electrons of its threshold (or -1).  Returns the number of hits (may
+ * exceed cap; only cap are written). */
+int64_t ora_electronics(const ora_cfg *c, uint64_t event_id, int32_t pixel, const double *I,
+                        int64_t cap, int32_t *t_cross, int32_t *t_adc, int32_t *adc,
+                        double *qv, double band, int32_t *tie_tick)
+{
+    int T = c->n_ticks;
+    double lsb_e = c->gain * c->lsb_mV;
+    int adc_max = (1 << c->adc_bits) - 1;
+    double q = 0.0;
+    int idle = 1;
+    int64_t last_adc = -(int64_t)1 << 40;
+    int64_t tc = -1, ta = -1;
+    int64_t nh = 0;
+    int32_t tie = -1;
+    for (int k = 0; k < T; ++k) {
+        double n[4];
+        if (c->periodic > 0 && idle && k > 0 && k % c->periodic == 0) {
+            ora_normals(c->seed, event_id, (uint32_t)pixel, (uint32_t)k, 4u, 0u, n);
+            q = c->s_reset * n[0];
+        }
+        q += I[k];
+        ora_normals(c->seed, event_id, (uint32_t)pixel, (uint32_t)k, 2u, 0u, n);
+        if (idle) {
+            double v = q + c->s_unc * n[0];
+            double thr = c->thr + c->s_disc * n[1];
+            if (tie < 0 && fabs(v - thr) < band) tie = k;
+            if ((float)v >= (float)thr) {
+                tc = k;
+                ta = k + c->hold;
+                if (last_adc + c->min_int > ta) ta = last_adc + c->min_int;
+                idle = 0;
+            }
+        }
+        if (!idle && k == ta) {
+            double v = q + c->s_unc * n[0];
+            double r = (double)((float)v / (float)lsb_e);
+            double code = floor(r);
+            if (tie < 0 && fabs(v / lsb_e - floor(v / lsb_e + 0.5)) * lsb_e < band) tie = k;
+            if (code < 0) code = 0;
+            if (code > adc_max) code = adc_max;
+            if (nh < cap) {
+                t_cross[nh] = (int32_t)tc;
+                t_adc[nh] = (int32_t)ta;
+                adc[nh] = (int32_t)code;
+                qv[nh] = v;
+            }
+            ++nh;
+            double m[4];
+            ora_normals(c->seed, event_id, (uint32_t)pixel, (uint32_t)k, 3u, 0u, m);
+            q = c->s_reset * m[0];
+            last_adc = k;
+            idle = 1;
+        }
+    }
+    if (tie_tick) *tie_tick = tie;
+    return nh;
+}

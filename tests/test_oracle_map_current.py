@@ -1,0 +1,315 @@
+"""Pins of the oracle's pixel map (Sec. 3.3.2) and induced current (Eq. (current)).
+
+Exact cases use a geometry whose pitch, bin width, drift velocity and tick
+are binary fractions, so that sample positions and arrival ticks are exact
+and the result must reduce to a table lookup.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synth import params, response
+
+KEYS = ("x0", "y0", "z0", "t0", "x1", "y1", "z1", "t1", "dE")
+
+
+def _seg(rows):
+    a = np.asarray(rows, dtype=np.float32)
+    return {k: np.ascontiguousarray(a[:, i]) for i, k in enumerate(KEYS)}
+
+
+# ---------------------------------------------------------------- pixel map --
+
+def test_cheb_distance_against_dense_sampling():
+    L = oracle.lib()
+    rng = np.random.default_rng(3)
+    t = np.linspace(0.0, 1.0, 200001)
+    for _ in range(60):
+        a = rng.normal(0, 1, 2)
+        b = a + rng.normal(0, 1, 2) * rng.choice([0.0, 1e-3, 1.0])
+        p = rng.normal(0, 1, 2)
+        d = L.ora_cheb_distance(a[0], a[1], b[0], b[1], p[0], p[1])
+        xs = a[0] + t * (b[0] - a[0]) - p[0]
+        ys = a[1] + t * (b[1] - a[1]) - p[1]
+        brute = np.maximum(np.abs(xs), np.abs(ys)).min()
+        assert d <= brute + 1e-12
+        assert brute - d < 2e-5 * (1 + np.hypot(*(b - a)))
+
+
+def _exact_cfg(**over):
+    c = params.tile_config(pitch_cm=0.46875, vdrift_cm_us=0.125, tick_us=0.125,
+                           diff_long_cm2_s=0.0, diff_tran_cm2_s=0.0, n_ticks=128,
+                           lifetime_us=1e9)
+    c.update(over)
+    return c
+
+
+LUT_SMALL = dict(nb=45, nt=64, bins_per_pitch=30, z0_cm=0.1)
+
+
+def test_point_maps_to_3x3():
+    # sigma_T = 0: map radius (45 + 1/2) bins = 1.5167 pitch; pixel centres at
+    # 0 and 1 pitch are inside, 2 pitch outside.
+    o = oracle.Oracle(_exact_cfg(), LUT_SMALL)
+    p = 0.46875
+    xc, yc = 10.5 * p, 20.5 * p
+    seg = _seg([(xc, yc, 1.0 - 2 ** -12, 0, xc, yc, 1.0 + 2 ** -12, 0, 1.0)])
+    d = o.quench_drift(seg)
+    ids, _ = o.map_segment(seg, d, 0)
+    nx = 70
+    exp = sorted((20 + dy) * nx + 10 + dx for dy in (-1, 0, 1) for dx in (-1, 0, 1))
+    assert sorted(ids.tolist()) == exp
+
+
+def test_axis_parallel_segment_maps_4x3():
+    o = oracle.Oracle(_exact_cfg(), LUT_SMALL)
+    p = 0.46875
+    xc, yc = 10.5 * p, 20.5 * p
+    seg = _seg([(xc, yc, 1.0, 0, xc + p, yc, 1.0, 0, 1.0)])
+    d = o.quench_drift(seg)
+    ids, _ = o.map_segment(seg, d, 0)
+    exp = sorted((20 + dy) * 70 + 10 + dx for dy in (-1, 0, 1) for dx in (-1, 0, 1, 2))
+    assert sorted(ids.tolist()) == exp
+
+
+def test_boundary_distance_counts_as_mapped():
+    o = oracle.Oracle(_exact_cfg(), LUT_SMALL)
+    p = 0.46875
+    R = o.map_radius(0.0)
+    assert R == 45.5 * p / 30
+    xc, yc = 10.5 * p, 20.5 * p
+    # a point exactly R to the right of pixel (10, 20): (10,20) mapped, (9,20) not
+    seg = _seg([(xc + R, yc, 1.0 - 2 ** -12, 0, xc + R, yc, 1.0 + 2 ** -12, 0, 1.0)])
+    d = o.quench_drift(seg)
+    ids, mg = o.map_segment(seg, d, 0)
+    pid = 20 * 70 + 10
+    assert pid in ids.tolist()
+    assert mg[ids.tolist().index(pid)] == 0.0
+    assert 20 * 70 + 9 not in ids.tolist()
+
+
+def test_map_contains_every_pixel_with_current():
+    cfg = params.small_config(n_ticks=2000)
+    o = oracle.Oracle(cfg, params.LUT, response.lut_for(cfg, params.LUT))
+    rng = np.random.default_rng(11)
+    rows = []
+    for _ in range(3):
+        x, y, z = 10 + 40 * rng.random(), 10 + 40 * rng.random(), 5 + 50 * rng.random()
+        v = rng.normal(size=3)
+        v *= 0.05 / np.linalg.norm(v)
+        rows.append((x, y, z, 0, x + v[0], y + v[1], z + v[2], 0, 0.1))
+    seg = _seg(rows)
+    d = o.quench_drift(seg)
+    nx = o.npx_x
+    for s in range(len(rows)):
+        ids, _ = o.map_segment(seg, d, s)
+        mapped = set(ids.tolist())
+        g = int(d["anode"][s])
+        base = g * nx * o.npx_y
+        cx = int((seg["x0"][s]) / 0.4434)
+        cy = int((seg["y0"][s]) / 0.4434)
+        for iy in range(cy - 4, cy + 5):
+            for ix in range(cx - 4, cx + 5):
+                pid = base + iy * nx + ix
+                I = o.pixel_current(seg, d, pid, [s])
+                if np.any(I != 0):
+                    assert pid in mapped, (s, ix, iy)
+
+
+# ----------------------------------------------------------- induced current --
+
+def _point(xc, yc, dx, dy, z, t=0.0):
+    x = xc + dx
+    y = yc + dy
+    return (x, y, z - 2 ** -12, t, x, y, z + 2 ** -12, t, 1.0)
+
+
+@pytest.mark.parametrize("bx,by,sx,sy", [(7, 12, 1, 1), (0, 44, -1, 1), (30, 3, 1, -1), (44, 0, -1, -1)])
+def test_point_charge_reads_table_row(bx, by, sx, sy):
+    """sigma = 0, one point at a node offset, integer arrival: I[k] = q R[bx, by, k - A + L - 1]."""
+    cfg = _exact_cfg()
+    rng = np.random.default_rng(bx * 100 + by)
+    lut = rng.random((45, 45, 64))          # any table: checks indexing and orientation
+    o = oracle.Oracle(cfg, LUT_SMALL, lut)
+    p, h = 0.46875, 0.46875 / 30
+    xc, yc = 10.5 * p, 20.5 * p
+    seg = _seg([_point(xc, yc, sx * (bx + 0.5) * h, sy * (by + 0.5) * h, 1.0)])
+    d = o.quench_drift(seg)
+    assert d["n_samples"][0] == 1
+    I = o.pixel_current(seg, d, 20 * 70 + 10, [0])
+    A = 64                                   # 1 cm / 0.125 cm/us / 0.125 us
+    exp = np.zeros(128)
+    for k in range(128):
+        j = k - A + 64 - 1
+        if 0 <= j < 64:
+            exp[k] = d["Qa"][0] * lut[bx, by, j]
+    assert np.array_equal(I, exp)
+
+
+def test_interpolation_is_superposition_of_nodes():
+    """Between nodes and between ticks the current is the weighted sum of node currents."""
+    cfg = _exact_cfg()
+    lut = np.random.default_rng(5).random((45, 45, 64))
+    o = oracle.Oracle(cfg, LUT_SMALL, lut)
+    p, h = 0.46875, 0.46875 / 30
+    xc, yc = 10.5 * p, 20.5 * p
+    pid = 20 * 70 + 10
+
+    def cur(dx, dy, z):
+        seg = _seg([_point(xc, yc, dx, dy, z)])
+        d = o.quench_drift(seg)
+        return o.pixel_current(seg, d, pid, [0]) / d["Qa"][0]   # per unit charge
+
+    # x halfway (1/4 of a bin) between nodes 5 and 6, y on node 9, arrival 64 + 1/4
+    z_int, z_q = 1.0, 1.0 + 0.25 * 0.125 * 0.125
+    got = cur(5.75 * h, 9.5 * h, z_q)
+    base = {}
+    for b in (5, 6):
+        for z, tag in ((z_int, 0), (1.0 + 0.125 * 0.125, 1)):
+            base[(b, tag)] = cur((b + 0.5) * h, 9.5 * h, z)
+    exp = (0.75 * (0.75 * base[(5, 0)] + 0.25 * base[(5, 1)])
+           + 0.25 * (0.75 * base[(6, 0)] + 0.25 * base[(6, 1)]))
+    assert np.allclose(got, exp, rtol=1e-13, atol=1e-15)
+    # inside half a bin of the centre the folded table reads node 0
+    assert np.array_equal(cur(0.25 * h, 9.5 * h, z_int), cur(0.5 * h, 9.5 * h, z_int))
+    assert np.array_equal(cur(-0.25 * h, 9.5 * h, z_int), cur(0.5 * h, 9.5 * h, z_int))
+    # beyond the last node the response vanishes
+    assert not np.any(cur(45.5 * h, 9.5 * h, z_int))
+
+
+def test_time_and_space_shifts():
+    cfg = _exact_cfg(diff_tran_cm2_s=8.8, diff_long_cm2_s=4.0)
+    lut = np.random.default_rng(9).random((45, 45, 64))
+    o = oracle.Oracle(cfg, LUT_SMALL, lut)
+    p = 0.46875
+    row = (5.1, 9.3, 2.0, 0.0, 5.3, 9.2, 2.1, 0.0, 0.4)
+    seg = _seg([row])
+    d = o.quench_drift(seg)
+    pid = int(9.3 / p) * 70 + int(5.1 / p)
+    I0 = o.pixel_current(seg, d, pid, [0])
+    # t0 shifted by 5 ticks: the current moves by exactly 5 ticks
+    r2 = list(row)
+    r2[3] += 5 * 0.125
+    r2[7] += 5 * 0.125
+    seg2 = _seg([r2])
+    I1 = o.pixel_current(seg2, o.quench_drift(seg2), pid, [0])
+    assert np.allclose(I1[5:], I0[:-5], rtol=1e-12, atol=1e-14)
+    # translated by one pitch in x: same current one pixel to the right
+    r3 = list(row)
+    r3[0] += p
+    r3[4] += p
+    seg3 = _seg([r3])
+    I2 = o.pixel_current(seg3, o.quench_drift(seg3), pid + 1, [0])
+    assert np.allclose(I2, I0, rtol=1e-5, atol=1e-12 * np.abs(I0).max())
+
+
+def test_charge_conservation():
+    """Sec. 3.3.1: each response series integrates to one electron, so the
+    current summed over pixels and ticks equals the collected charge."""
+    cfg = params.small_config(n_ticks=4000, t_window0_us=-200.0)
+    lut = response.lut_for(cfg, params.LUT)            # FP64 table
+    o = oracle.Oracle(cfg, params.LUT, lut)
+    rng = np.random.default_rng(21)
+    rows = []
+    for z in (2.0, 14.0, 29.0, 44.0):
+        x, y = 10 + 30 * rng.random(), 10 + 30 * rng.random()
+        v = rng.normal(size=3)
+        v *= 0.2 / np.linalg.norm(v)
+        rows.append((x, y, z, 0, x + v[0], y + v[1], z + v[2], 0, 0.4))
+    seg = _seg(rows)
+    d = o.quench_drift(seg)
+    pix, _, _, _ = o.pixel_map(seg, d)
+    total = sum(o.pixel_current(seg, d, p, s).sum() for p, s in pix.items())
+    assert abs(total / d["Qa"].sum() - 1.0) < 1e-12
+
+
+def _interp_table(tab, h, nb):
+    """Independent bilinear reader of a folded table: node values at +-(b+1/2)h, zero node at nb."""
+    nodes = (np.arange(nb + 1) + 0.5) * h
+    full = np.concatenate([-nodes[::-1], nodes])
+    ext = np.zeros((nb + 1, nb + 1))
+    ext[:nb, :nb] = tab
+    unf = np.block([[ext[::-1, ::-1], ext[::-1, :]], [ext[:, ::-1], ext]])
+    from scipy.interpolate import RegularGridInterpolator
+    return RegularGridInterpolator((full, full), unf, bounds_error=False, fill_value=0.0)
+
+
+def test_monte_carlo_converges_to_convolution():
+    """Eq. (current) approximates the convolution of the response with the
+    diffused charge density at the percent level (Sec. 3.3.2): compare the
+    per-pixel collected charge and mean arrival tick with a quadrature of
+    the continuous integral."""
+    cfg = params.small_config(n_ticks=4000, t_window0_us=-200.0, mc_per_sample=48)
+    lut = response.lut_for(cfg, params.LUT)
+    o = oracle.Oracle(cfg, params.LUT, lut)
+    p = 0.4434
+    h = p / 30
+    row = (20.1, 21.3, 20.0, 0.0, 20.25, 21.45, 20.05, 0.0, 0.5)
+    seg = _seg([row])
+    d = o.quench_drift(seg)
+    sT = d["sigma_T"][0]
+    W = _interp_table(lut.sum(axis=2), h, 45)
+    M1 = _interp_table((lut * np.arange(1950)).sum(axis=2), h, 45)
+    # quadrature: midpoint along the segment x Gauss-Hermite transverse
+    gh, gw = np.polynomial.hermite_e.hermegauss(24)
+    gw = gw / gw.sum()
+    u = (np.arange(400) + 0.5) / 400
+    s = {k: np.float64(seg[k][0]) for k in KEYS}
+    xs = s["x0"] + u * (s["x1"] - s["x0"])
+    ys = s["y0"] + u * (s["y1"] - s["y0"])
+    zs = s["z0"] + u * (s["z1"] - s["z0"])
+    a = ((s["t0"] + zs / cfg["vdrift_cm_us"]) - cfg["t_window0_us"]) / np.float32(0.1)
+    pix, _, _, _ = o.pixel_map(seg, d)
+    Qa = d["Qa"][0]
+    checked = 0
+    for pid, sl in pix.items():
+        iy, ix = divmod(pid % (o.npx_x * o.npx_y), o.npx_x)
+        xc, yc = (ix + 0.5) * np.float32(p), (iy + 0.5) * np.float32(p)
+        X = xs[:, None, None] + sT * gh[None, :, None] - xc
+        Y = ys[:, None, None] + sT * gh[None, None, :] - yc
+        pts = np.stack([np.broadcast_to(X, (400, 24, 24)), np.broadcast_to(Y, (400, 24, 24))], -1)
+        wts = gw[None, :, None] * gw[None, None, :] / 400
+        Wv = W(pts)
+        q_exp = Qa * (wts * Wv).sum()
+        m_exp = Qa * (wts * (Wv * (a[:, None, None] - 1950 + 1) + M1(pts))).sum()
+        I = o.pixel_current(seg, d, pid, sl)
+        if q_exp < 0.02 * Qa:
+            continue
+        checked += 1
+        assert abs(I.sum() / q_exp - 1) < 0.02
+        mean_tick = (np.arange(len(I)) * I).sum() / I.sum()
+        # MC standard error of the mean tick at M = 48 is ~0.05-0.1 tick here
+        assert abs(mean_tick - m_exp / q_exp) < 0.3
+    assert checked >= 3
+
+
+def test_longitudinal_spread_matches_sigma_L():
+    """A point charge drifting 25 cm: the arrival spread of the current adds
+    (sigma_L / (v_d tick))^2 to its variance in ticks (Sec. 3.2)."""
+    cfg = params.tile_config(diff_tran_cm2_s=0.0, n_ticks=4000, t_window0_us=-200.0,
+                             mc_per_sample=4000)
+    lut = response.lut_for(cfg, params.LUT)
+    o = oracle.Oracle(cfg, params.LUT, lut)
+    p = np.float32(0.4434)
+    xc, yc = 20.5 * p, 30.5 * p
+    z = 25.0
+    seg = _seg([(xc + 0.01, yc + 0.02, z - 2 ** -12, 0, xc + 0.01, yc + 0.02, z + 2 ** -12, 0, 1.0)])
+    d = o.quench_drift(seg)
+    pid = 30 * 70 + 20
+    I = o.pixel_current(seg, d, pid, [0])
+    k = np.arange(len(I))
+
+    def var(w):
+        m = (k * w).sum() / w.sum()
+        return ((k - m) ** 2 * w).sum() / w.sum()
+
+    # same point without longitudinal diffusion, arrival smeared uniformly over one tick
+    cfg0 = dict(cfg, diff_long_cm2_s=0.0, mc_per_sample=1)
+    o0 = oracle.Oracle(cfg0, params.LUT, lut)
+    I0 = np.zeros_like(I)
+    for f in (np.arange(64) + 0.5) / 64 - 0.5:
+        zz = z + f * 0.16 * 0.1
+        s0 = _seg([(xc + 0.01, yc + 0.02, zz - 2 ** -12, 0, xc + 0.01, yc + 0.02, zz + 2 ** -12, 0, 1.0)])
+        I0 += o0.pixel_current(s0, o0.quench_drift(s0), pid, [0])
+    sa2 = (d["sigma_L"][0] / (np.float32(0.16) * np.float32(0.1))) ** 2
+    assert abs((var(I) - var(I0)) / (sa2 - 1.0 / 12) - 1) < 0.08

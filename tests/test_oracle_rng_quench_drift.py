@@ -1,0 +1,184 @@
+"""Pins of the oracle's generator and of steps 1-2 (Sec. 3.1, Sec. 3.2).
+
+Each check uses something other than the oracle's own formula: published
+known-answer vectors, numbers printed in the paper, inverted relations and
+invariants that a dropped term, a wrong sign or a swapped constant breaks.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import params
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _gold_values():
+    out = {}
+    for line in open(os.path.join(GOLD, "paper_values.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        name, val, tol = line.split()[:3]
+        out[name] = (float(val), float(tol))
+    return out
+
+
+def test_philox_known_answers():
+    n = 0
+    for line in open(os.path.join(GOLD, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(x, 16) for x in line.split()]
+        out = oracle.philox4x32_10(w[0:4], w[4:6])
+        assert [int(x) for x in out] == w[6:10]
+        n += 1
+    assert n == 3
+
+
+def test_normals_statistics():
+    seed, ev = 12345, 7
+    v = np.array([oracle.normals(seed, ev, i, 3, 2) for i in range(40000)])
+    x = v.reshape(-1)
+    assert abs(x.mean()) < 0.02
+    assert abs(x.std() - 1.0) < 0.02
+    # Box-Muller partners are uncorrelated; 4th moment of a normal is 3
+    assert abs(np.corrcoef(v[:, 0], v[:, 1])[0, 1]) < 0.03
+    assert abs((x ** 4).mean() - 3.0) < 0.15
+    # P(|n| > 2) of a standard normal
+    assert abs((np.abs(x) > 2).mean() - 0.0455) < 0.004
+    # counters and keys select different streams
+    a = oracle.normals(seed, ev, 1, 2, 1)
+    assert not np.allclose(a, oracle.normals(seed, ev + 1, 1, 2, 1))
+    assert not np.allclose(a, oracle.normals(seed, ev, 1, 2, 2))
+
+
+def test_paper_values_consistent_with_config():
+    g = _gold_values()
+    c = params.BASE
+    assert c["pitch_cm"] == g["pixel_pitch_cm"][0]
+    assert abs(c["px_per_tile"] * c["pitch_cm"] - g["tile_size_cm"][0]) < 1e-9
+    assert c["px_per_tile"] ** 2 == g["pixels_per_tile"][0]
+    assert c["gain_e_per_mV"] == g["gain_e_per_mV"][0]
+    assert g["threshold_mV"][0] * c["gain_e_per_mV"] == g["threshold_e"][0]
+    assert abs(c["min_adc_interval_ticks"] * c["tick_us"] - g["min_adc_interval_us"][0]) < 1e-9
+    assert abs(c["hold_ticks"] * c["tick_us"] - g["hold_us"][0]) < 1e-9
+    assert abs(c["sample_step_cm"] * 1e4 - g["sample_step_um"][0]) < 1e-9
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_mip_recombination_around_0p7(model):
+    val, tol = _gold_values()["mip_recomb_factor"]
+    o = oracle.Oracle(params.tile_config(recomb_model=model), params.LUT)
+    assert abs(o.recomb(2.1) - val) < tol
+
+
+def test_birks_inverted_relation():
+    # Eq. (birks) solved for k_b: (A_b / R - 1) / (dE/dx) = k_b / epsilon at every dE/dx
+    cfg = params.tile_config(recomb_model=0)
+    o = oracle.Oracle(cfg, params.LUT)
+    c = o.c
+    eps = c.efield * c.density
+    for dedx in (0.3, 1.0, 2.1, 5.0, 20.0, 48.0):
+        R = o.recomb(dedx)
+        assert 0 < R < c.Ab
+        assert abs((c.Ab / R - 1.0) / dedx - c.kb / eps) < 1e-12
+    assert abs(o.recomb(1e-9) - c.Ab) < 1e-9          # no quenching at vanishing dE/dx
+    assert o.recomb(10.0) < o.recomb(5.0) < o.recomb(2.0)
+
+
+def test_box_inverted_relation():
+    # Eq. (box) solved for alpha: exp(R xi) - xi = alpha, xi = (beta/epsilon) dE/dx
+    cfg = params.tile_config(recomb_model=1)
+    o = oracle.Oracle(cfg, params.LUT)
+    c = o.c
+    eps = c.efield * c.density
+    for dedx in (1.0, 2.1, 5.0, 20.0, 48.0):
+        R = o.recomb(dedx)
+        xi = c.beta / eps * dedx
+        assert abs(math.exp(R * xi) - xi - c.alpha) < 1e-12
+    assert o.recomb(20.0) < o.recomb(5.0) < o.recomb(2.1)
+
+
+def _seg(rows):
+    """Segments from rows (x0,y0,z0,t0,x1,y1,z1,t1,dE)."""
+    a = np.asarray(rows, dtype=np.float32)
+    keys = ("x0", "y0", "z0", "t0", "x1", "y1", "z1", "t1", "dE")
+    return {k: np.ascontiguousarray(a[:, i]) for i, k in enumerate(keys)}
+
+
+def test_quench_drift_invariants():
+    cfg = params.module_config()
+    o = oracle.Oracle(cfg, params.LUT)
+    c = o.c
+    # segments 0.5 cm along x at several heights in both drift volumes
+    zs = [0.0, 3.0, 15.0, 29.5, 30.5, 45.0, 60.0]
+    rows = [(10.0, 20.0, z, 0.0, 10.5, 20.0, z, 0.0, 1.05) for z in zs]
+    d = o.quench_drift(_seg(rows))
+    assert np.all(d["anode"] >= 0)
+    # Q_R = R E / W_ion, R at dE/dx = E / dx
+    dx = d["dx"]
+    assert np.allclose(d["dedx"] * dx, np.float32(1.05), rtol=1e-12)
+    assert np.allclose(d["QR"] * c.w_ion / np.float64(np.float32(1.05)), d["R"], rtol=1e-12)
+    # drift distance: to anode z = 0 in TPC 0 and z = 2D in TPC 1
+    dist = np.array([z if z < 30 else 60.0 - z for z in zs])
+    assert np.allclose(d["t_drift"] * c.vdrift, dist, rtol=1e-12, atol=1e-12)
+    # lifetime: ln(Q_a / Q_R) linear in drift time with slope -1/tau
+    lr = np.log(d["Qa"] / d["QR"])
+    assert np.allclose(lr, -d["t_drift"] / c.lifetime, rtol=1e-12, atol=1e-15)
+    # a charge created on the anode is not attenuated and not diffused
+    assert d["Qa"][0] == d["QR"][0] and d["sigma_T"][0] == 0 and d["sigma_L"][0] == 0
+    # diffusion: sigma^2 / (2 t) = D (cm^2/us) for both directions
+    m = d["t_drift"] > 0
+    assert np.allclose(d["sigma_T"][m] ** 2 / (2 * d["t_drift"][m]), c.DT * 1e-6, rtol=1e-12)
+    assert np.allclose(d["sigma_L"][m] ** 2 / (2 * d["t_drift"][m]), c.DL * 1e-6, rtol=1e-12)
+    # mirror symmetry of the two drift volumes about the cathode
+    assert d["anode"][1] == 0 and d["anode"][5] == 1
+    # full 30 cm drift: attenuation and widths at the cathode
+    full = o.quench_drift(_seg([(10, 20, 30.0 - 1e-4, 0, 10.5, 20, 30.0 - 1e-4, 0, 1.0)]))
+    assert abs(full["t_drift"][0] - 187.5) < 1e-3
+    assert abs(full["Qa"][0] / full["QR"][0] - 0.918304) < 1e-6
+    assert abs(full["sigma_T"][0] - 0.0574456) < 1e-6
+    assert abs(full["sigma_L"][0] - 0.0387298) < 1e-6
+
+
+def test_sample_count_and_activity():
+    cfg = params.module_config()
+    o = oracle.Oracle(cfg, params.LUT)
+    rows = [
+        (10, 20, 5, 0, 10.5, 20, 5, 0, 1.0),          # 0.5 cm
+        (10, 20, 5, 0, 10.0, 20, 5, 0, 1.0),          # zero length: inactive
+        (-1, 20, 5, 0, -0.5, 20, 5, 0, 1.0),          # midpoint outside x
+        (10, 20, 61, 0, 10.5, 20, 61, 0, 1.0),        # beyond the second anode
+        (10, 20, 5, 0, 10.0000, 20.0, 5.0005, 0, 1.0),  # 5 um along z: one point
+        (10, 20, 5, 0, 10.3, 20.4, 5, 0, 1.0),        # 0.5 cm diagonal
+    ]
+    d = o.quench_drift(_seg(rows))
+    assert list(d["anode"][[1, 2, 3]]) == [-1, -1, -1]
+    assert d["Qa"][1] == 0 and d["n_samples"][1] == 0
+    N = d["n_samples"]
+    act = d["anode"] >= 0
+    # N = smallest integer with N * step >= dx (10 um points)
+    assert np.all(N[act] * o.c.step >= d["dx"][act])
+    assert np.all((N[act] - 1) * o.c.step < d["dx"][act])
+    assert N[4] == 1
+    assert abs(N[0] - 500) <= 1 and abs(N[5] - 500) <= 1
+
+
+def test_anode_numbering_across_modules():
+    cfg = params.spill_config()
+    o = oracle.Oracle(cfg, params.LUT)
+    W = 280 * np.float32(0.4434)
+    H = 350 * np.float32(0.4434)
+    rows = []
+    expect = []
+    for (mx, my, tpc) in [(0, 0, 0), (6, 0, 1), (0, 4, 0), (3, 2, 1), (6, 4, 1)]:
+        x = mx * W + 5.0
+        y = my * H + 7.0
+        z = 10.0 if tpc == 0 else 50.0
+        rows.append((x, y, z, 0, x + 0.4, y, z, 0, 1.0))
+        expect.append((my * 7 + mx) * 2 + tpc)
+    d = o.quench_drift(_seg(rows))
+    assert list(d["anode"]) == expect
