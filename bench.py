@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 charge-readout path (arXiv:2212.09807, Sec. 3).
+
+One step = the whole hot path (quench+drift, pixel map, induced current,
+electronics) over one synthetic event resident in HBM.  Default workload: one
+detector module (2 TPCs, 2 anodes of 4x5 tiles of 70x70 pixels) with one
+neutrino-like interaction of ~20k segments.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: replicas only (independent events per rank, no data-path
+collective); the barrier and the max over ranks of the timed region use
+torch.distributed.  ``--impl reference`` times the FP64 CPU oracle (the only
+reference this project has) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import events, params, response  # noqa: E402
+
+KERNELS_PER_STEP = 22     # 1 quench/drift + 14 pixel map + 1 current + 6 electronics
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["module", "tile", "spill"], default="module")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    seed = params.BASE["seed"]
+    if name == "tile":
+        cfg = params.tile_config()
+        seg = events.tile_muon(cfg, seed)
+        desc = "tile_muon_200seg: 1 TPC, 1 tile 70x70 px, one 100 cm muon of 200 x 0.5 cm segments"
+    elif name == "spill":
+        cfg = params.spill_config()
+        seg = events.spill_event(cfg, seed + 2)
+        desc = "spill_35mod: 7x5 modules, 50 interactions + 100 rock muons, t0 ~ U[0,10us]"
+    else:
+        cfg = params.module_config()
+        seg = events.module_event(cfg, seed + 1)
+        desc = ("module_nu_20k: 1 module, 2 TPCs, anodes of 4x5 tiles of 70x70 px (196k px), "
+                "one interaction of ~20k segments (muon + protons + EM cloud)")
+    return cfg, seg, desc
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.lines = []
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "100", "-i", self.gpu_id], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.p = None
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "samples": len(sm),
+                "power_w_max": float(max(power)) if power else None, "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+def stored_traffic(kernel_file: str):
+    """DRAM bytes per launch from a committed ncu summary, if taken on this exact source."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    except OSError:
+        return None
+    src = open(os.path.join(ROOT, "paper_2212_09807_gb300", "csrc", kernel_file), "rb").read()
+    ent = t.get(kernel_file)
+    if not ent or ent.get("src_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    return ent.get("dram_bytes_per_launch_full")
+
+
+# ------------------------------------------------------------------ oracle ---
+
+def oracle_sample(cfg, seg, lut64, rng, n_pix=6):
+    """Times the FP64 oracle on a bounded sample of one event and scales it to
+    the whole event: quench+drift and the (box-restricted brute-force) pixel map
+    of every segment are run in full; current + electronics of ``n_pix`` random
+    active pixels are timed and scaled by the event's active-pixel count.
+    Returns (estimated whole-event seconds, sample description)."""
+    import oracle
+    o = oracle.Oracle(cfg, params.LUT, lut64)
+    t0 = time.perf_counter()
+    d = o.quench_drift(seg)
+    pix, _, _, _ = o.pixel_map(seg, d)
+    t_map = time.perf_counter() - t0
+    keys = np.array(sorted(pix))
+    pick = rng.choice(keys, min(n_pix, len(keys)), replace=False)
+    t0 = time.perf_counter()
+    for p in pick:
+        I = o.pixel_current(seg, d, int(p), pix[int(p)])
+        o.electronics(int(p), I)
+    t_pix = (time.perf_counter() - t0) / len(pick)
+    est = t_map + t_pix * len(keys)
+    desc = (f"oracle, 1 thread: quench+drift and pixel map of all {len(seg['x0'])} segments in full, "
+            f"current+electronics timed on {len(pick)} random active pixels and scaled to all "
+            f"{len(keys)} active pixels")
+    return est, desc
+
+
+def run_reference(args):
+    ws, rank, _ = dist()
+    if rank != 0:
+        return
+    cfg, seg, desc = workload(args.workload)
+    lut64 = response.pad_rows(response.lut_for(cfg, params.LUT))[..., : params.LUT["nt"]].astype(np.float64)
+    S = len(seg["x0"])
+    rng = np.random.default_rng(0)
+    ests = []
+    t_start = time.perf_counter()
+    for i in range(args.warmup + args.steps):
+        est, sdesc = oracle_sample(cfg, seg, lut64, rng, n_pix=3)
+        if i >= args.warmup:
+            ests.append(est)
+    wall = time.perf_counter() - t_start
+    v = S / float(np.mean(ests))
+    print(json.dumps({
+        "impl": "reference", "metric": "segments/s", "value": v, "unit": "segments/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+        "dtype": "f64", "data": "synthetic", "config": {"workload": desc, "segments": S},
+        "cpu_baseline": {"value": v, "unit": "segments/s", "cores": 1, "kind": "oracle", "sample": sdesc},
+        "e2e": {"value": v, "unit": "segments/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall, "vs_baseline": None,
+    }))
+
+
+# --------------------------------------------------------------------- ours ---
+
+def run_ours(args):
+    import torch
+    from paper_2212_09807_gb300 import sim
+
+    world, rank, local = dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=dev)
+        pg = tdist
+    cfg, seg, desc = workload(args.workload)
+    S = len(seg["x0"])
+    T = int(cfg["n_ticks"])
+    lut64 = response.lut_for(cfg, params.LUT)
+    lut_pad = response.pad_rows(lut64)
+    lut = torch.as_tensor(lut_pad, device=dev)
+
+    # capacities: grow until the event fits (one untimed sizing pass)
+    caps = [40 * S, 4 * S, 4 * S]
+    while True:
+        run = sim.EventRunner(cfg, lut, params.LUT["nt"], params.LUT["bins_per_pitch"], S, *caps, device=dev)
+        segs = sim.Segments.from_numpy(seg, event_id=rank, device=dev)
+        run.enqueue(segs)
+        torch.cuda.synchronize()
+        n_pairs, n_pix, n_hits, status = run.counts()
+        if status == 0:
+            break
+        caps = [max(caps[0], 2 * n_pairs), max(caps[1], 2 * n_pix), max(caps[2], 2 * n_hits)]
+        del run
+        torch.cuda.empty_cache()
+
+    # the same entry points sim_event calls, one by one, so that each step is timed
+    v = run.view(S)
+    A = sim._alias
+    dr = sim.Drifted.wrap(v.dr)
+    seg_pix_off = A(v.seg_pix_off, S + 1, torch.int32, dev)
+    seg_pix_ids = A(v.seg_pix_ids, run.max_pairs, torch.int32, dev)
+    active = A(v.active_pixels, run.max_pixels, torch.int32, dev)
+    pix_seg_off = A(v.pix_seg_off, run.max_pixels + 1, torch.int32, dev)
+    pix_seg_ids = A(v.pix_seg_ids, run.max_pairs, torch.int32, dev)
+    current = A(v.current, run.max_pixels * T, torch.float32, dev).view(run.max_pixels, T)
+    counts = run.ws[:4]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)   # 256 MB > L2
+
+    def step(evs):
+        evs[0].record()
+        sim.sim_quench_drift(run.cfg, segs, dr)
+        evs[1].record()
+        sim.sim_pixel_map(run.cfg, segs, dr, run.resp, seg_pix_off, seg_pix_ids, active, pix_seg_off,
+                          pix_seg_ids, run.ws)
+        evs[2].record()
+        sim.sim_induced_current(run.cfg, segs, dr, run.resp, active, pix_seg_off, pix_seg_ids, counts, current)
+        evs[3].record()
+        sim.sim_electronics(run.cfg, segs.event_id, active, current, counts, run.hits, run.ws)
+        evs[4].record()
+
+    mk = lambda: [torch.cuda.Event(enable_timing=True) for _ in range(5)]  # noqa: E731
+    for _ in range(args.warmup):
+        flush.zero_()
+        step(mk())
+    torch.cuda.synchronize()
+    n_pairs, n_pix, n_hits, status = run.counts()
+    assert status == 0
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = str(getattr(props, "uuid", local))
+    if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) > 8:
+        gpu_id = "GPU-" + gpu_id
+    clk = ClockSampler(gpu_id)
+    clk.start()
+    time.sleep(0.15)
+    all_evs = []
+    for _ in range(args.steps):
+        flush.zero_()                  # outside the timed intervals: every step starts with a cold L2
+        e = mk()
+        step(e)
+        all_evs.append(e)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    per = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in all_evs])   # ms
+    step_ms = per.sum(axis=1)
+    total_ms = float(step_ms.sum())
+    if pg:
+        t = torch.tensor([total_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * S * args.steps / (total_ms / 1e3)
+    a45_ms = float(per[:, 2:].sum())
+    pix_ticks = world * n_pix * T * args.steps / (a45_ms / 1e3)
+
+    # roofline of the dominant kernel (induced current)
+    dn = run.view(S)
+    ns = A(dn.dr.n_samples, S, torch.int32, dev).cpu().numpy().astype(np.int64)
+    an = A(dn.dr.anode, S, torch.int32, dev).cpu().numpy()
+    samples = int(ns[an >= 0].sum()) * int(cfg["mc_per_sample"])
+    L = params.LUT["nt"]
+    w_alg = 2.0 * 9 * L * samples                       # flop per launch (9 pixels per point)
+    a4_s = float(per[:, 2].mean()) / 1e3
+    achieved = w_alg / a4_s / 1e12
+    sm_mhz = clocks.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": stored_traffic("induced_current.cu"), "kernel": "k_induced_current",
+                "peak_note": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz",
+                "work_note": "2 flop x 9 pixels x 1950 table ticks per (point, perturbation)"}
+
+    # end to end through the public API: pinned host segments in, hits out
+    io = sim.EventIO(run)
+    host = {k: torch.as_tensor(np.ascontiguousarray(seg[k], dtype=np.float32)).pin_memory() for k in seg}
+    for _ in range(max(1, args.warmup)):
+        io.simulate(host, S, rank)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    t0 = time.perf_counter()
+    h2d = d2h = 0
+    for _ in range(args.steps):
+        _, _, hb, db = io.simulate(host, S, rank)
+        h2d, d2h = hb, db
+    e2e_s = time.perf_counter() - t0
+    if pg:
+        t = torch.tensor([e2e_s], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * S * args.steps / e2e_s, "unit": "segments/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        lut_or = lut_pad[..., :L].astype(np.float64)
+        est, sdesc = oracle_sample(cfg, seg, lut_or, np.random.default_rng(0), n_pix=8)
+        cpu = {"value": S / est, "unit": "segments/s", "cores": 1, "kind": "oracle", "sample": sdesc}
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": "segments/s", "value": value, "unit": "segments/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": desc, "segments": S, "active_pixels": n_pix, "pairs": n_pairs,
+                       "hits": n_hits, "n_ticks": T, "points": samples, "parallelism": f"replicas{world}",
+                       "l2": "flushed (256 MB write) before every timed step"},
+            "pixel_ticks_per_s": pix_ticks,
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+            "step_breakdown_ms": {"quench_drift": float(per[:, 0].mean()), "pixel_map": float(per[:, 1].mean()),
+                                  "induced_current": float(per[:, 2].mean()),
+                                  "electronics": float(per[:, 3].mean())},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clocks,
+        }))
+    if pg:
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,222 @@
+/*
+ * sim.h -- C ABI of the GB300 charge-readout simulation of a pixelated LArTPC
+ * (arXiv:2212.09807, "Highly-parallelized simulation of a pixelated LArTPC on
+ * a GPU", Sec. 3).
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers are DEVICE pointers unless marked (host).  The caller owns every
+ *    buffer; the library allocates nothing on the device.
+ *  - Every call is asynchronous on the caller's CUDA stream (`stream` is a
+ *    cudaStream_t passed as void*; NULL = the legacy default stream).  No call
+ *    synchronises the host.
+ *  - Host-side argument checks run before any launch; a failed check returns
+ *    SIM_ERR_INVALID_ARG and enqueues nothing.
+ *  - Counts that only the device knows (pairs, active pixels, hits) are written
+ *    to device int64 words.  When a count exceeds the caller's capacity the
+ *    kernels skip the writes that would overflow, store the required size and
+ *    set a bit in the status word (see SIM_STATUS_*); the caller reads the
+ *    counts after synchronising, grows its buffers and calls again.
+ *  - Units: cm, us, MeV, electrons.  Pixel ids are global int32:
+ *      anode = (my * n_mod_x + mx) * n_tpc + tpc,
+ *      pixel = anode * (npx_x * npx_y) + iy * npx_x + ix,
+ *    npx_x = tiles_x * px_per_tile, npx_y = tiles_y * px_per_tile.
+ *  - Results depend only on (config, segments, event_id, seed), not on thread
+ *    order or batch composition (the paper's requirement that a result must
+ *    not depend on the order of execution of the threads, Sec. 2).
+ */
+#ifndef LARPIX_GB300_SIM_H
+#define LARPIX_GB300_SIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define SIM_OK 0
+#define SIM_ERR_INVALID_ARG (-1) /* null pointer, negative size, bad config: nothing enqueued */
+#define SIM_ERR_CAPACITY (-2)    /* a host-known size exceeds a buffer or the workspace */
+#define SIM_ERR_CUDA (-3)        /* a CUDA launch or copy failed; see sim_last_cuda_error() */
+#define SIM_ERR_TIMEOUT (-4)     /* reserved: a bounded device-side wait gave up */
+
+/* Bits of the device status word (workspace counts block, index 3). */
+#define SIM_STATUS_PAIR_OVERFLOW 1
+#define SIM_STATUS_PIXEL_OVERFLOW 2
+#define SIM_STATUS_HIT_OVERFLOW 4
+#define SIM_STATUS_TICK_RANGE 8
+
+/* Simulation parameters (host struct, copied at each call).  Floating-point
+ * fields are FP32.  Citations: recombination Sec. 3.1 Eq. (birks)/(box);
+ * drift Sec. 3.2; sampling Sec. 3.3.2; front end Sec. 3.4; geometry Sec. 6. */
+typedef struct sim_config {
+    /* geometry: modules tile x-y; TPC 0 anode at z=0, cathode at z=drift_len,
+     * TPC 1 anode at z=2*drift_len */
+    int32_t n_mod_x, n_mod_y, n_tpc, tiles_x, tiles_y, px_per_tile;
+    float pitch_cm, drift_len_cm;
+    /* recombination: 0 = Birks, 1 = modified Box */
+    int32_t recomb_model;
+    float birks_Ab, birks_kb, box_alpha, box_beta, efield_kV_cm, lar_density_g_cm3, w_ion_MeV;
+    /* drift */
+    float vdrift_cm_us, lifetime_us, diff_long_cm2_s, diff_tran_cm2_s;
+    /* sampling of Eq. (current): point spacing, perturbations per point, clip (sigmas) */
+    float sample_step_cm;
+    int32_t mc_per_sample;
+    float diff_clip_sigma;
+    /* readout window: tick length, number of ticks, start time */
+    float tick_us;
+    int32_t n_ticks;
+    float t_window0_us;
+    /* front end */
+    float thr_e, sigma_reset_e, sigma_disc_e, sigma_unc_e, gain_e_per_mV, adc_lsb_mV;
+    int32_t hold_ticks, min_adc_interval_ticks, periodic_reset_ticks, adc_bits;
+    /* counter-based RNG seed (Philox4x32-10 key = seed ^ event_id) */
+    uint64_t seed;
+    /* arithmetic form of the induced-current step: 0 = FP32 direct */
+    int32_t precision;
+    int32_t reserved;
+} sim_config;
+
+/* Energy-deposit segments S_i = (r_s, r_e, E) of one event (Sec. 2), as
+ * structure-of-arrays FP32 device columns of length n: start (x0,y0,z0,t0),
+ * end (x1,y1,z1,t1), deposited energy dE.  Segment index i (0..n-1) keys the
+ * diffusion random numbers together with event_id. */
+typedef struct sim_segments {
+    const float *x0, *y0, *z0, *t0, *x1, *y1, *z1, *t1, *dE;
+    int64_t n;
+    uint64_t event_id;
+} sim_segments;
+
+/* Field-response table I_pixel[x, y, t] (Sec. 3.3.1): FP32 device array
+ * [nb][nb][ld], series of nt ticks (electrons per tick for one electron; row
+ * nt-1 is the last tick before arrival) at folded offsets
+ * (b + 1/2) * pitch / bins_per_pitch, b = 0..nb-1.  ld >= nt, ld % 4 == 0,
+ * the row tail [nt, ld) is ignored. */
+typedef struct sim_response {
+    const float *lut;
+    int32_t nb, nt, ld, bins_per_pitch;
+} sim_response;
+
+/* Per-segment results of sim_quench_drift (device arrays of length n):
+ * Q_a (electrons at the anode), t_drift (us), sigma_T, sigma_L (cm), anode
+ * (-1 = inactive segment), n_samples (points N along the segment), and
+ * `anchors`: SIM_ANCHOR_BYTES per segment, 16-byte aligned, an opaque
+ * sampling record read by sim_pixel_map and sim_induced_current. */
+#define SIM_ANCHOR_BYTES 64
+typedef struct sim_drifted {
+    float *Qa, *t_drift, *sigma_T, *sigma_L;
+    int32_t *anode, *n_samples;
+    void *anchors;
+} sim_drifted;
+
+/* Hit list written by sim_electronics / sim_event, ordered by active-pixel
+ * index then tick: pixel id, threshold-crossing tick, ADC tick, 8-bit ADC
+ * code and the digitised CSA charge (electrons).  n_out (device int64)
+ * receives the number of hits (which may exceed capacity: see status). */
+typedef struct sim_hits {
+    int32_t *pixel, *t_cross, *t_adc;
+    uint8_t *adc;
+    float *q;
+    int64_t capacity;
+    int64_t *n_out;
+} sim_hits;
+
+/* Human-readable text of a return code (static string). */
+const char *sim_strerror(int code);
+
+/* The cudaError_t of the last SIM_ERR_CUDA return of this host thread. */
+int sim_last_cuda_error(void);
+
+/* Sizes of the ABI structs as compiled (for binding checks): writes
+ * sizeof(sim_config), sizeof(sim_segments), sizeof(sim_response),
+ * sizeof(sim_drifted), sizeof(sim_hits) to sizes[0..4] (host). */
+void sim_abi_sizes(int64_t sizes[5]);
+
+/* Workspace bytes sim_event needs for up to max_segments segments, max_pairs
+ * (segment, pixel) pairs and max_pixels active pixels; the same size serves
+ * sim_pixel_map and sim_electronics, which use only the scratch region after
+ * the counts block.  Writes *bytes (host).  The first 256 bytes of any
+ * workspace hold the counts block: int64 [0] pairs, [1] active pixels,
+ * [2] hits, [3] status bits (SIM_STATUS_*). */
+int sim_workspace_size(const sim_config *cfg, int64_t max_segments, int64_t max_pairs,
+                       int64_t max_pixels, size_t *bytes);
+
+/* Device address of the counts block inside a workspace. */
+const int64_t *sim_workspace_counts(const void *ws);
+
+/* Steps 1-2 (Sec. 3.1 Eq. (birks)/(box); Sec. 3.2 Eq. (drift), Eq. (lifetime),
+ * sigma = sqrt(2 D t_drift)): one pass over the segments.
+ *   R   = A_b / (1 + k_b/eps dE/dx)            (Birks, default)
+ *       = ln(alpha + xi) / xi, xi = beta/eps dE/dx  (modified Box)
+ *   Q_a = R (dE / W_ion) exp(-t_drift / tau), t_drift = |z_mid - z_anode| / v_drift
+ * Segments whose midpoint is outside every drift volume, or shorter than
+ * 1e-6 cm, get anode = -1 and Q_a = 0. */
+int sim_quench_drift(const sim_config *cfg, const sim_segments *seg, const sim_drifted *out,
+                     void *stream);
+
+/* Step 3 (Sec. 3.3.2, pixels a segment can induce on).  Pixel p of the
+ * segment's anode is mapped iff the segment's x-y projection comes within
+ * Chebyshev distance (nb + 1/2) pitch/bins_per_pitch + clip * sigma_T of its
+ * centre (nb and bins_per_pitch from `resp`; its table is not read).  Outputs:
+ *   seg_pix_off [n+1], seg_pix_ids [pair_cap]   segment -> pixel ids (CSR)
+ *   active_pixels [pix_cap]                      mapped pixel ids, increasing
+ *   pix_seg_off [pix_cap+1], pix_seg_ids [pair_cap]  pixel -> segments (CSR,
+ *                                                segment indices increasing)
+ * Counts go to the workspace counts block ([0] pairs, [1] pixels, [3] status);
+ * on overflow the required sizes are stored and the CSR fill is skipped.
+ * Workspace: sim_workspace_size(cfg, n, pair_cap, pix_cap). */
+int sim_pixel_map(const sim_config *cfg, const sim_segments *seg, const sim_drifted *dr,
+                  const sim_response *resp, int32_t *seg_pix_off, int32_t *seg_pix_ids, int64_t pair_cap,
+                  int32_t *active_pixels, int32_t *pix_seg_off, int32_t *pix_seg_ids,
+                  int64_t pix_cap, void *ws, size_t ws_bytes, void *stream);
+
+/* Step 4 (Sec. 3.3.2, charge density rho and Eq. (current)):
+ *   I[p, k] = sum over segments s mapped to p, points mu < N_s, perturbations
+ *             nu < M of q_s * Rt(x - x_p, y - y_p, k - a),  q_s = Q_a/(N_s M),
+ * the table read bilinearly at the folded transverse offset and linearly at
+ * the fractional arrival tick a; summed over segments in increasing index
+ * order.  current: FP32 [pix_cap][n_ticks]; rows [0, counts[1]) are written.
+ * counts: device int64[4] counts block as written by sim_pixel_map ([1] =
+ * active pixels, [3] = status); nothing is computed when the status word is
+ * nonzero or counts[1] > pix_cap. */
+int sim_induced_current(const sim_config *cfg, const sim_segments *seg, const sim_drifted *dr,
+                        const sim_response *resp, const int32_t *active_pixels,
+                        const int32_t *pix_seg_off, const int32_t *pix_seg_ids,
+                        const int64_t *counts, int64_t pix_cap, float *current, void *stream);
+
+/* Step 5 (Sec. 3.4): per active pixel, tick by tick, charge integration,
+ * discriminator with uncorrelated and threshold noise, hold, 8-bit ADC and
+ * reset with pedestal noise (Philox counters keyed by pixel id and tick).
+ * Reads counts[1] (active pixels) and counts[3] (status; nothing is done when
+ * nonzero); writes the hit list `out`, *out->n_out and counts[2] (hits).
+ * Workspace (scratch, from byte 256 on): sim_workspace_size(cfg, 0, 0, pix_cap). */
+int sim_electronics(const sim_config *cfg, uint64_t event_id, const int32_t *active_pixels,
+                    const float *current, int64_t *counts, int64_t pix_cap,
+                    const sim_hits *out, void *ws, size_t ws_bytes, void *stream);
+
+/* Steps 1-5 for one event, enqueued on one stream with no host
+ * synchronisation; every intermediate lives in the workspace, sized by
+ * sim_workspace_size(cfg, seg->n, max_pairs, max_pixels). */
+int sim_event(const sim_config *cfg, const sim_segments *seg, const sim_response *resp,
+              int64_t max_pairs, int64_t max_pixels, const sim_hits *out, void *ws,
+              size_t ws_bytes, void *stream);
+
+/* Device addresses of sim_event's intermediates inside its workspace (for
+ * inspection after the stream has run): per-segment results, both CSR maps,
+ * the active-pixel list, the induced current [max_pixels][n_ticks] and the
+ * counts block. */
+typedef struct sim_event_view {
+    sim_drifted dr;
+    int32_t *seg_pix_off, *seg_pix_ids, *active_pixels, *pix_seg_off, *pix_seg_ids;
+    float *current;
+    int64_t *counts;
+} sim_event_view;
+
+int sim_event_view_of(const sim_config *cfg, int64_t n_segments, int64_t max_pairs,
+                      int64_t max_pixels, void *ws, size_t ws_bytes, sim_event_view *view);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LARPIX_GB300_SIM_H */

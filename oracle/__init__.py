@@ -73,6 +73,8 @@ def lib():
         L.ora_map_segment.argtypes = [P(_Cfg), C.c_float, C.c_float, C.c_float, C.c_float,
                                       C.c_double, C.c_int32, i32p, f64p, C.c_int64]
         L.ora_map_segment.restype = C.c_int64
+        L.ora_map_segment_box.argtypes = L.ora_map_segment.argtypes
+        L.ora_map_segment_box.restype = C.c_int64
         L.ora_pair_margin.argtypes = [P(_Cfg), C.c_float, C.c_float, C.c_float, C.c_float,
                                       C.c_double, C.c_int32, C.c_int32]
         L.ora_pair_margin.restype = C.c_double
@@ -176,13 +178,15 @@ class Oracle:
     def map_radius(self, sigma_T: float) -> float:
         return self.L.ora_map_radius(C.byref(self.c), float(sigma_T))
 
-    def map_segment(self, seg: dict, dr: dict, s: int):
-        """(ids, margins) of the pixels segment s is mapped to (brute force)."""
+    def map_segment(self, seg: dict, dr: dict, s: int, box: bool = True):
+        """(ids, margins) of the pixels segment s is mapped to (brute force over
+        the whole anode, or over the segment's widened bounding box)."""
+        fn = self.L.ora_map_segment_box if box else self.L.ora_map_segment
         cap = 4096
         while True:
             ids = np.zeros(cap, dtype=np.int32)
             mg = np.zeros(cap)
-            n = self.L.ora_map_segment(C.byref(self.c), float(seg["x0"][s]), float(seg["y0"][s]),
+            n = fn(C.byref(self.c), float(seg["x0"][s]), float(seg["y0"][s]),
                                        float(seg["x1"][s]), float(seg["y1"][s]),
                                        float(dr["sigma_T"][s]), int(dr["anode"][s]),
                                        _p(ids, C.c_int32), _p(mg, C.c_double), cap)

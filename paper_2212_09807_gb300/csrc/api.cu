@@ -1,0 +1,244 @@
+// api.cu -- the C ABI of include/sim.h: host-side argument checks, workspace
+// layout and the asynchronous enqueue of the path's kernels on the caller's
+// stream.  Nothing here allocates device memory or synchronises the host.
+#include <string.h>
+
+#include "sim_internal.cuh"
+
+using namespace larsim;
+
+namespace {
+
+thread_local int g_last_cuda = 0;
+
+int cuda_fail(cudaError_t e)
+{
+    g_last_cuda = (int)e;
+    return SIM_ERR_CUDA;
+}
+
+bool cfg_ok(const sim_config *c)
+{
+    if (!c) return false;
+    if (c->n_mod_x < 1 || c->n_mod_y < 1 || (c->n_tpc != 1 && c->n_tpc != 2)) return false;
+    if (c->tiles_x < 1 || c->tiles_y < 1 || c->px_per_tile < 1) return false;
+    const int64_t npx = (int64_t)c->n_mod_x * c->n_mod_y * c->n_tpc * c->tiles_x * c->px_per_tile *
+                        c->tiles_y * c->px_per_tile;
+    if (npx >= ((int64_t)1 << 31)) return false;
+    if (!(c->pitch_cm > 0.f) || !(c->drift_len_cm > 0.f) || !(c->vdrift_cm_us > 0.f)) return false;
+    if (!(c->tick_us > 0.f) || c->n_ticks < 1 || !(c->sample_step_cm > 0.f)) return false;
+    if (c->mc_per_sample < 1 || !(c->diff_clip_sigma >= 0.f) || !(c->lifetime_us > 0.f)) return false;
+    if (c->recomb_model != 0 && c->recomb_model != 1) return false;
+    if (c->adc_bits < 1 || c->adc_bits > 16 || c->hold_ticks < 0 || c->min_adc_interval_ticks < 0) return false;
+    if (c->periodic_reset_ticks < 0 || c->precision != 0) return false;
+    return true;
+}
+
+bool seg_ok(const sim_segments *s)
+{
+    if (!s || s->n < 0 || s->n >= ((int64_t)1 << 31)) return false;
+    if (s->n == 0) return true;
+    return s->x0 && s->y0 && s->z0 && s->t0 && s->x1 && s->y1 && s->z1 && s->t1 && s->dE;
+}
+
+bool resp_ok(const sim_response *r, bool need_table)
+{
+    if (!r || r->nb < 1 || r->nt < 1 || r->ld < r->nt || (r->ld % 4) != 0 || r->bins_per_pitch < 1) return false;
+    if (need_table && (!r->lut || (reinterpret_cast<uintptr_t>(r->lut) & 15) != 0)) return false;
+    return true;
+}
+
+bool drifted_ok(const sim_drifted *d)
+{
+    return d && d->Qa && d->t_drift && d->sigma_T && d->sigma_L && d->anode && d->n_samples && d->anchors &&
+           (reinterpret_cast<uintptr_t>(d->anchors) & 15) == 0;
+}
+
+bool hits_ok(const sim_hits *h)
+{
+    return h && h->capacity >= 0 && (h->capacity == 0 || (h->pixel && h->t_cross && h->t_adc && h->adc && h->q));
+}
+
+// Layout of sim_event's workspace.
+struct Layout {
+    size_t counts, scratch, Qa, td, sT, sL, anode, ns, anch;
+    size_t seg_off, seg_ids, active, pix_off, pix_ids, current, total;
+};
+
+Layout layout(const sim_config &c, int64_t n, int64_t pairs, int64_t pixels)
+{
+    Layout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o += align256(bytes);
+        return at;
+    };
+    L.counts = take(256);
+    const size_t ms = map_scratch_bytes(c, n), es = elec_scratch_bytes(c, pixels);
+    L.scratch = take(ms > es ? ms : es);
+    L.Qa = take(4 * (size_t)n);
+    L.td = take(4 * (size_t)n);
+    L.sT = take(4 * (size_t)n);
+    L.sL = take(4 * (size_t)n);
+    L.anode = take(4 * (size_t)n);
+    L.ns = take(4 * (size_t)n);
+    L.anch = take(SIM_ANCHOR_BYTES * (size_t)n);
+    L.seg_off = take(4 * (size_t)(n + 1));
+    L.seg_ids = take(4 * (size_t)pairs);
+    L.active = take(4 * (size_t)pixels);
+    L.pix_off = take(4 * (size_t)(pixels + 1));
+    L.pix_ids = take(4 * (size_t)pairs);
+    L.current = take(4 * (size_t)pixels * (size_t)c.n_ticks);
+    L.total = o;
+    return L;
+}
+
+void fill_view(const Layout &L, char *w, sim_event_view *v)
+{
+    v->dr.Qa = reinterpret_cast<float *>(w + L.Qa);
+    v->dr.t_drift = reinterpret_cast<float *>(w + L.td);
+    v->dr.sigma_T = reinterpret_cast<float *>(w + L.sT);
+    v->dr.sigma_L = reinterpret_cast<float *>(w + L.sL);
+    v->dr.anode = reinterpret_cast<int32_t *>(w + L.anode);
+    v->dr.n_samples = reinterpret_cast<int32_t *>(w + L.ns);
+    v->dr.anchors = w + L.anch;
+    v->seg_pix_off = reinterpret_cast<int32_t *>(w + L.seg_off);
+    v->seg_pix_ids = reinterpret_cast<int32_t *>(w + L.seg_ids);
+    v->active_pixels = reinterpret_cast<int32_t *>(w + L.active);
+    v->pix_seg_off = reinterpret_cast<int32_t *>(w + L.pix_off);
+    v->pix_seg_ids = reinterpret_cast<int32_t *>(w + L.pix_ids);
+    v->current = reinterpret_cast<float *>(w + L.current);
+    v->counts = reinterpret_cast<int64_t *>(w + L.counts);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sim_strerror(int code)
+{
+    switch (code) {
+    case SIM_OK: return "ok";
+    case SIM_ERR_INVALID_ARG: return "invalid argument";
+    case SIM_ERR_CAPACITY: return "capacity or workspace too small";
+    case SIM_ERR_CUDA: return "CUDA error (see sim_last_cuda_error)";
+    case SIM_ERR_TIMEOUT: return "device-side wait timed out";
+    default: return "unknown error";
+    }
+}
+
+int sim_last_cuda_error(void) { return g_last_cuda; }
+
+void sim_abi_sizes(int64_t sizes[5])
+{
+    sizes[0] = sizeof(sim_config);
+    sizes[1] = sizeof(sim_segments);
+    sizes[2] = sizeof(sim_response);
+    sizes[3] = sizeof(sim_drifted);
+    sizes[4] = sizeof(sim_hits);
+}
+
+int sim_workspace_size(const sim_config *cfg, int64_t max_segments, int64_t max_pairs, int64_t max_pixels,
+                       size_t *bytes)
+{
+    if (!cfg_ok(cfg) || !bytes || max_segments < 0 || max_pairs < 0 || max_pixels < 0) return SIM_ERR_INVALID_ARG;
+    *bytes = layout(*cfg, max_segments, max_pairs, max_pixels).total;
+    return SIM_OK;
+}
+
+const int64_t *sim_workspace_counts(const void *ws) { return reinterpret_cast<const int64_t *>(ws); }
+
+int sim_quench_drift(const sim_config *cfg, const sim_segments *seg, const sim_drifted *out, void *stream)
+{
+    if (!cfg_ok(cfg) || !seg_ok(seg) || (seg->n > 0 && !drifted_ok(out))) return SIM_ERR_INVALID_ARG;
+    const cudaError_t e = launch_quench_drift(*cfg, *seg, *out, (cudaStream_t)stream);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e);
+}
+
+int sim_pixel_map(const sim_config *cfg, const sim_segments *seg, const sim_drifted *dr,
+                  const sim_response *resp, int32_t *seg_pix_off, int32_t *seg_pix_ids, int64_t pair_cap,
+                  int32_t *active_pixels, int32_t *pix_seg_off, int32_t *pix_seg_ids, int64_t pix_cap,
+                  void *ws, size_t ws_bytes, void *stream)
+{
+    if (!cfg_ok(cfg) || !seg_ok(seg) || !resp_ok(resp, false) || pair_cap < 0 || pix_cap < 0 || !ws)
+        return SIM_ERR_INVALID_ARG;
+    if (seg->n > 0 && (!drifted_ok(dr) || !seg_pix_off)) return SIM_ERR_INVALID_ARG;
+    if (!seg_pix_off || (pair_cap > 0 && (!seg_pix_ids || !pix_seg_ids)) ||
+        (pix_cap > 0 && (!active_pixels || !pix_seg_off)) || (pix_cap == 0 && !pix_seg_off))
+        return SIM_ERR_INVALID_ARG;
+    if (ws_bytes < 256 + map_scratch_bytes(*cfg, seg->n)) return SIM_ERR_CAPACITY;
+    char *w = reinterpret_cast<char *>(ws);
+    const sim_drifted d0 = dr ? *dr : sim_drifted{};
+    const cudaError_t e = launch_pixel_map(*cfg, *seg, d0, resp->nb, resp->bins_per_pitch, seg_pix_off,
+                                           seg_pix_ids, pair_cap, active_pixels, pix_seg_off, pix_seg_ids,
+                                           pix_cap, reinterpret_cast<int64_t *>(w), w + 256,
+                                           (cudaStream_t)stream);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e);
+}
+
+int sim_induced_current(const sim_config *cfg, const sim_segments *seg, const sim_drifted *dr,
+                        const sim_response *resp, const int32_t *active_pixels, const int32_t *pix_seg_off,
+                        const int32_t *pix_seg_ids, const int64_t *counts, int64_t pix_cap, float *current,
+                        void *stream)
+{
+    if (!cfg_ok(cfg) || !seg_ok(seg) || !resp_ok(resp, true) || !counts || pix_cap < 0) return SIM_ERR_INVALID_ARG;
+    if (pix_cap > 0 && (!active_pixels || !pix_seg_off || !pix_seg_ids || !current || !drifted_ok(dr)))
+        return SIM_ERR_INVALID_ARG;
+    if (pix_cap == 0) return SIM_OK;
+    const cudaError_t e = launch_induced_current(*cfg, *seg, *dr, *resp, active_pixels, pix_seg_off, pix_seg_ids,
+                                                 counts, pix_cap, current, (cudaStream_t)stream);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e);
+}
+
+int sim_electronics(const sim_config *cfg, uint64_t event_id, const int32_t *active_pixels, const float *current,
+                    int64_t *counts, int64_t pix_cap, const sim_hits *out, void *ws, size_t ws_bytes,
+                    void *stream)
+{
+    if (!cfg_ok(cfg) || !counts || pix_cap < 0 || !hits_ok(out) || !ws) return SIM_ERR_INVALID_ARG;
+    if (pix_cap > 0 && (!active_pixels || !current)) return SIM_ERR_INVALID_ARG;
+    if (ws_bytes < 256 + elec_scratch_bytes(*cfg, pix_cap)) return SIM_ERR_CAPACITY;
+    const cudaError_t e = launch_electronics(*cfg, event_id, active_pixels, current, counts, pix_cap, *out,
+                                             reinterpret_cast<char *>(ws) + 256, (cudaStream_t)stream);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e);
+}
+
+int sim_event_view_of(const sim_config *cfg, int64_t n_segments, int64_t max_pairs, int64_t max_pixels, void *ws,
+                      size_t ws_bytes, sim_event_view *view)
+{
+    if (!cfg_ok(cfg) || n_segments < 0 || max_pairs < 0 || max_pixels < 0 || !ws || !view)
+        return SIM_ERR_INVALID_ARG;
+    const Layout L = layout(*cfg, n_segments, max_pairs, max_pixels);
+    if (ws_bytes < L.total) return SIM_ERR_CAPACITY;
+    fill_view(L, reinterpret_cast<char *>(ws), view);
+    return SIM_OK;
+}
+
+int sim_event(const sim_config *cfg, const sim_segments *seg, const sim_response *resp, int64_t max_pairs,
+              int64_t max_pixels, const sim_hits *out, void *ws, size_t ws_bytes, void *stream)
+{
+    if (!cfg_ok(cfg) || !seg_ok(seg) || !resp_ok(resp, true) || max_pairs < 0 || max_pixels < 0 ||
+        !hits_ok(out) || !ws)
+        return SIM_ERR_INVALID_ARG;
+    const Layout L = layout(*cfg, seg->n, max_pairs, max_pixels);
+    if (ws_bytes < L.total) return SIM_ERR_CAPACITY;
+    char *w = reinterpret_cast<char *>(ws);
+    sim_event_view v;
+    fill_view(L, w, &v);
+    const cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = launch_quench_drift(*cfg, *seg, v.dr, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = launch_pixel_map(*cfg, *seg, v.dr, resp->nb, resp->bins_per_pitch, v.seg_pix_off, v.seg_pix_ids,
+                         max_pairs, v.active_pixels, v.pix_seg_off, v.pix_seg_ids, max_pixels, v.counts,
+                         w + L.scratch, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = launch_induced_current(*cfg, *seg, v.dr, *resp, v.active_pixels, v.pix_seg_off, v.pix_seg_ids, v.counts,
+                               max_pixels, v.current, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = launch_electronics(*cfg, seg->event_id, v.active_pixels, v.current, v.counts, max_pixels, *out,
+                           w + L.scratch, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return SIM_OK;
+}
+
+}  // extern "C"

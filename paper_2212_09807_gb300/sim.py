@@ -1,0 +1,409 @@
+"""Python binding of the C ABI in include/sim.h (argument marshalling only).
+
+Torch provides device memory and streams; every step of the simulation runs
+in the sm_103a kernels of ``libsim.so``.  The functions keep the C names
+(``sim_quench_drift``, ``sim_pixel_map``, ``sim_induced_current``,
+``sim_electronics``, ``sim_event``) and take torch CUDA tensors.  If the
+library has not been built, :func:`lib` raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsim.so")
+
+SIM_OK = 0
+SIM_STATUS_PAIR_OVERFLOW = 1
+SIM_STATUS_PIXEL_OVERFLOW = 2
+SIM_STATUS_HIT_OVERFLOW = 4
+ANCHOR_BYTES = 64
+
+_lib = None
+
+
+class SimError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = lib().sim_strerror(code).decode()
+        if code == -3:
+            msg += f" (cudaError {lib().sim_last_cuda_error()})"
+        super().__init__(f"{where}: {msg} [{code}]")
+        self.code = code
+
+
+class SimConfig(C.Structure):
+    _fields_ = [
+        ("n_mod_x", C.c_int32), ("n_mod_y", C.c_int32), ("n_tpc", C.c_int32),
+        ("tiles_x", C.c_int32), ("tiles_y", C.c_int32), ("px_per_tile", C.c_int32),
+        ("pitch_cm", C.c_float), ("drift_len_cm", C.c_float),
+        ("recomb_model", C.c_int32),
+        ("birks_Ab", C.c_float), ("birks_kb", C.c_float), ("box_alpha", C.c_float),
+        ("box_beta", C.c_float), ("efield_kV_cm", C.c_float), ("lar_density_g_cm3", C.c_float),
+        ("w_ion_MeV", C.c_float),
+        ("vdrift_cm_us", C.c_float), ("lifetime_us", C.c_float), ("diff_long_cm2_s", C.c_float),
+        ("diff_tran_cm2_s", C.c_float),
+        ("sample_step_cm", C.c_float), ("mc_per_sample", C.c_int32), ("diff_clip_sigma", C.c_float),
+        ("tick_us", C.c_float), ("n_ticks", C.c_int32), ("t_window0_us", C.c_float),
+        ("thr_e", C.c_float), ("sigma_reset_e", C.c_float), ("sigma_disc_e", C.c_float),
+        ("sigma_unc_e", C.c_float), ("gain_e_per_mV", C.c_float), ("adc_lsb_mV", C.c_float),
+        ("hold_ticks", C.c_int32), ("min_adc_interval_ticks", C.c_int32),
+        ("periodic_reset_ticks", C.c_int32), ("adc_bits", C.c_int32),
+        ("seed", C.c_uint64),
+        ("precision", C.c_int32), ("reserved", C.c_int32),
+    ]
+
+
+_P = C.c_void_p
+
+
+class SimSegments(C.Structure):
+    _fields_ = [(k, _P) for k in ("x0", "y0", "z0", "t0", "x1", "y1", "z1", "t1", "dE")] + [
+        ("n", C.c_int64), ("event_id", C.c_uint64)]
+
+
+class SimResponse(C.Structure):
+    _fields_ = [("lut", _P), ("nb", C.c_int32), ("nt", C.c_int32), ("ld", C.c_int32),
+                ("bins_per_pitch", C.c_int32)]
+
+
+class SimDrifted(C.Structure):
+    _fields_ = [(k, _P) for k in ("Qa", "t_drift", "sigma_T", "sigma_L", "anode", "n_samples", "anchors")]
+
+
+class SimHits(C.Structure):
+    _fields_ = [(k, _P) for k in ("pixel", "t_cross", "t_adc", "adc", "q")] + [
+        ("capacity", C.c_int64), ("n_out", _P)]
+
+
+class SimEventView(C.Structure):
+    _fields_ = [("dr", SimDrifted)] + [(k, _P) for k in (
+        "seg_pix_off", "seg_pix_ids", "active_pixels", "pix_seg_off", "pix_seg_ids", "current", "counts")]
+
+
+def lib():
+    """The compiled library; raises when it is missing (build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        cp = C.POINTER
+        L.sim_strerror.restype = C.c_char_p
+        L.sim_strerror.argtypes = [C.c_int]
+        L.sim_last_cuda_error.restype = C.c_int
+        L.sim_abi_sizes.argtypes = [cp(C.c_int64)]
+        L.sim_workspace_size.argtypes = [cp(SimConfig), C.c_int64, C.c_int64, C.c_int64, cp(C.c_size_t)]
+        L.sim_workspace_counts.restype = C.c_void_p
+        L.sim_workspace_counts.argtypes = [_P]
+        L.sim_quench_drift.argtypes = [cp(SimConfig), cp(SimSegments), cp(SimDrifted), _P]
+        L.sim_pixel_map.argtypes = [cp(SimConfig), cp(SimSegments), cp(SimDrifted), cp(SimResponse),
+                                    _P, _P, C.c_int64, _P, _P, _P, C.c_int64, _P, C.c_size_t, _P]
+        L.sim_induced_current.argtypes = [cp(SimConfig), cp(SimSegments), cp(SimDrifted), cp(SimResponse),
+                                          _P, _P, _P, _P, C.c_int64, _P, _P]
+        L.sim_electronics.argtypes = [cp(SimConfig), C.c_uint64, _P, _P, _P, C.c_int64, cp(SimHits),
+                                      _P, C.c_size_t, _P]
+        L.sim_event.argtypes = [cp(SimConfig), cp(SimSegments), cp(SimResponse), C.c_int64, C.c_int64,
+                                cp(SimHits), _P, C.c_size_t, _P]
+        L.sim_event_view_of.argtypes = [cp(SimConfig), C.c_int64, C.c_int64, C.c_int64, _P, C.c_size_t,
+                                        cp(SimEventView)]
+        for f in ("sim_workspace_size", "sim_quench_drift", "sim_pixel_map", "sim_induced_current",
+                  "sim_electronics", "sim_event", "sim_event_view_of"):
+            getattr(L, f).restype = C.c_int
+        sizes = (C.c_int64 * 5)()
+        L.sim_abi_sizes(sizes)
+        exp = [C.sizeof(SimConfig), C.sizeof(SimSegments), C.sizeof(SimResponse), C.sizeof(SimDrifted),
+               C.sizeof(SimHits)]
+        if list(sizes) != exp:
+            raise RuntimeError(f"ABI struct size mismatch: library {list(sizes)} vs binding {exp}")
+        _lib = L
+    return _lib
+
+
+def _check(code: int, where: str):
+    if code != SIM_OK:
+        raise SimError(code, where)
+
+
+def make_config(cfg: dict) -> SimConfig:
+    """sim_config from a parameter dict (floats rounded to FP32 by ctypes)."""
+    c = SimConfig()
+    for name, ct in SimConfig._fields_:
+        if name == "reserved":
+            continue
+        v = cfg[name]
+        setattr(c, name, int(v) & 0xFFFFFFFFFFFFFFFF if name == "seed" else (float(v) if ct is C.c_float else int(v)))
+    return c
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+class Segments:
+    """Segment columns as FP32 CUDA tensors (x0, y0, z0, t0, x1, y1, z1, t1, dE)."""
+
+    KEYS = ("x0", "y0", "z0", "t0", "x1", "y1", "z1", "t1", "dE")
+
+    def __init__(self, cols: dict, event_id: int = 0):
+        self.cols = cols
+        self.n = int(cols["x0"].numel())
+        self.event_id = int(event_id)
+
+    @classmethod
+    def from_numpy(cls, seg: dict, event_id: int = 0, device="cuda"):
+        import torch
+        return cls({k: torch.as_tensor(np.ascontiguousarray(seg[k], dtype=np.float32), device=device)
+                    for k in cls.KEYS}, event_id)
+
+    def struct(self) -> SimSegments:
+        s = SimSegments()
+        for k in self.KEYS:
+            setattr(s, k, _ptr(self.cols[k]))
+        s.n = self.n
+        s.event_id = self.event_id
+        return s
+
+
+class Response:
+    """Response table as a CUDA FP32 tensor [nb][nb][ld]."""
+
+    def __init__(self, lut_padded, nt: int, bins_per_pitch: int):
+        self.t = lut_padded
+        self.nb = int(lut_padded.shape[0])
+        self.ld = int(lut_padded.shape[2])
+        self.nt = int(nt)
+        self.bpp = int(bins_per_pitch)
+
+    def struct(self) -> SimResponse:
+        r = SimResponse()
+        r.lut = _ptr(self.t)
+        r.nb, r.nt, r.ld, r.bins_per_pitch = self.nb, self.nt, self.ld, self.bpp
+        return r
+
+
+class Drifted:
+    """Outputs of sim_quench_drift."""
+
+    def __init__(self, n: int, device="cuda"):
+        import torch
+        f = dict(dtype=torch.float32, device=device)
+        i = dict(dtype=torch.int32, device=device)
+        m = max(n, 1)                      # never a null pointer, even for an empty event
+        self.Qa, self.t_drift = torch.empty(m, **f)[:n], torch.empty(m, **f)[:n]
+        self.sigma_T, self.sigma_L = torch.empty(m, **f)[:n], torch.empty(m, **f)[:n]
+        self.anode, self.n_samples = torch.empty(m, **i)[:n], torch.empty(m, **i)[:n]
+        self.anchors = torch.empty(m * ANCHOR_BYTES // 4, **f)
+
+    @classmethod
+    def wrap(cls, sd: SimDrifted):
+        d = cls.__new__(cls)
+        d._s = sd
+        return d
+
+    def struct(self) -> SimDrifted:
+        if hasattr(self, "_s"):
+            return self._s
+        d = SimDrifted()
+        for k in ("Qa", "t_drift", "sigma_T", "sigma_L", "anode", "n_samples", "anchors"):
+            setattr(d, k, _ptr(getattr(self, k)))
+        return d
+
+
+class Hits:
+    """Hit list buffers of a given capacity."""
+
+    def __init__(self, capacity: int, device="cuda"):
+        import torch
+        self.capacity = int(capacity)
+        n = max(self.capacity, 1)
+        self.pixel = torch.empty(n, dtype=torch.int32, device=device)
+        self.t_cross = torch.empty(n, dtype=torch.int32, device=device)
+        self.t_adc = torch.empty(n, dtype=torch.int32, device=device)
+        self.adc = torch.empty(n, dtype=torch.uint8, device=device)
+        self.q = torch.empty(n, dtype=torch.float32, device=device)
+        self.n_out = torch.zeros(1, dtype=torch.int64, device=device)
+
+    def struct(self) -> SimHits:
+        h = SimHits()
+        for k in ("pixel", "t_cross", "t_adc", "adc", "q"):
+            setattr(h, k, _ptr(getattr(self, k)))
+        h.capacity = self.capacity
+        h.n_out = _ptr(self.n_out)
+        return h
+
+    def to_numpy(self, n: int) -> dict:
+        return {k: getattr(self, k)[:n].cpu().numpy() for k in ("pixel", "t_cross", "t_adc", "adc", "q")}
+
+
+def workspace_size(cfg: SimConfig, max_segments: int, max_pairs: int, max_pixels: int) -> int:
+    b = C.c_size_t()
+    _check(lib().sim_workspace_size(C.byref(cfg), max_segments, max_pairs, max_pixels, C.byref(b)),
+           "sim_workspace_size")
+    return int(b.value)
+
+
+# ------------------------------------------------------------ C entry points --
+
+def sim_quench_drift(cfg: SimConfig, seg: Segments, out: Drifted, stream=None):
+    s, d = seg.struct(), out.struct()
+    _check(lib().sim_quench_drift(C.byref(cfg), C.byref(s), C.byref(d), _stream(stream)), "sim_quench_drift")
+
+
+def sim_pixel_map(cfg: SimConfig, seg: Segments, dr: Drifted, resp: Response, seg_pix_off, seg_pix_ids,
+                  active_pixels, pix_seg_off, pix_seg_ids, ws, stream=None):
+    s, d, r = seg.struct(), dr.struct(), resp.struct()
+    _check(lib().sim_pixel_map(C.byref(cfg), C.byref(s), C.byref(d), C.byref(r), _ptr(seg_pix_off),
+                               _ptr(seg_pix_ids), int(seg_pix_ids.numel()), _ptr(active_pixels),
+                               _ptr(pix_seg_off), _ptr(pix_seg_ids), int(active_pixels.numel()),
+                               _ptr(ws), int(ws.numel() * ws.element_size()), _stream(stream)),
+           "sim_pixel_map")
+
+
+def sim_induced_current(cfg: SimConfig, seg: Segments, dr: Drifted, resp: Response, active_pixels,
+                        pix_seg_off, pix_seg_ids, counts, current, stream=None):
+    s, d, r = seg.struct(), dr.struct(), resp.struct()
+    pix_cap = int(current.shape[0])
+    _check(lib().sim_induced_current(C.byref(cfg), C.byref(s), C.byref(d), C.byref(r), _ptr(active_pixels),
+                                     _ptr(pix_seg_off), _ptr(pix_seg_ids), _ptr(counts), pix_cap,
+                                     _ptr(current), _stream(stream)), "sim_induced_current")
+
+
+def sim_electronics(cfg: SimConfig, event_id: int, active_pixels, current, counts, hits: Hits, ws,
+                    stream=None):
+    h = hits.struct()
+    pix_cap = int(current.shape[0])
+    _check(lib().sim_electronics(C.byref(cfg), int(event_id), _ptr(active_pixels), _ptr(current), _ptr(counts),
+                                 pix_cap, C.byref(h), _ptr(ws), int(ws.numel() * ws.element_size()),
+                                 _stream(stream)), "sim_electronics")
+
+
+def sim_event(cfg: SimConfig, seg: Segments, resp: Response, max_pairs: int, max_pixels: int, hits: Hits, ws,
+              stream=None):
+    s, r, h = seg.struct(), resp.struct(), hits.struct()
+    _check(lib().sim_event(C.byref(cfg), C.byref(s), C.byref(r), int(max_pairs), int(max_pixels), C.byref(h),
+                           _ptr(ws), int(ws.numel() * ws.element_size()), _stream(stream)), "sim_event")
+
+
+def sim_event_view_of(cfg: SimConfig, n_segments: int, max_pairs: int, max_pixels: int, ws) -> SimEventView:
+    v = SimEventView()
+    _check(lib().sim_event_view_of(C.byref(cfg), int(n_segments), int(max_pairs), int(max_pixels), _ptr(ws),
+                                   int(ws.numel() * ws.element_size()), C.byref(v)), "sim_event_view_of")
+    return v
+
+
+# ------------------------------------------------------------ convenience --
+
+def _alias(ptr, n, dtype, device):
+    """A torch tensor aliasing ``n`` elements of device memory at ``ptr`` (no copy)."""
+    import torch
+    elem = torch.tensor([], dtype=dtype).element_size()
+    typestr = {torch.float32: "<f4", torch.int32: "<i4", torch.int64: "<i8", torch.uint8: "|u1"}[dtype]
+
+    class _CAI:
+        __cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr), False),
+                                    "version": 2, "strides": None}
+
+    if n == 0:
+        return torch.empty(0, dtype=dtype, device=device)
+    t = torch.as_tensor(_CAI(), device=device)
+    assert t.element_size() == elem
+    return t
+
+
+class EventRunner:
+    """Allocates the workspace and hit buffers once and runs sim_event on events.
+
+    ``max_pairs`` / ``max_pixels`` / ``max_hits`` bound one event; on a
+    capacity overflow ``run`` reports it (status bits) and the caller grows
+    the runner.
+    """
+
+    def __init__(self, cfg: dict, lut_padded, lut_nt: int, bins_per_pitch: int, max_segments: int,
+                 max_pairs: int, max_pixels: int, max_hits: int, device="cuda"):
+        import torch
+        self.cfg_dict = cfg
+        self.cfg = make_config(cfg)
+        self.resp = Response(lut_padded, lut_nt, bins_per_pitch)
+        self.max_segments, self.max_pairs, self.max_pixels = int(max_segments), int(max_pairs), int(max_pixels)
+        self.ws_bytes = workspace_size(self.cfg, self.max_segments, self.max_pairs, self.max_pixels)
+        self.ws = torch.empty((self.ws_bytes + 7) // 8, dtype=torch.int64, device=device)
+        self.hits = Hits(max_hits, device)
+        self.device = device
+
+    def view(self, n_segments: int) -> SimEventView:
+        return sim_event_view_of(self.cfg, n_segments, self.max_pairs, self.max_pixels, self.ws)
+
+    def enqueue(self, seg: Segments, stream=None):
+        if seg.n > self.max_segments:
+            raise ValueError("event larger than the runner's max_segments")
+        sim_event(self.cfg, seg, self.resp, self.max_pairs, self.max_pixels, self.hits, self.ws, stream)
+
+    def counts(self):
+        """(pairs, pixels, hits, status) after the stream has run."""
+        return [int(x) for x in self.ws[:4].cpu().tolist()]
+
+    def current(self, n_segments: int, n_pixels: int):
+        import torch
+        v = self.view(n_segments)
+        T = int(self.cfg.n_ticks)
+        return _alias(v.current, n_pixels * T, torch.float32, self.ws.device).view(n_pixels, T)
+
+    def active_pixels(self, n_segments: int, n_pixels: int):
+        import torch
+        v = self.view(n_segments)
+        return _alias(v.active_pixels, n_pixels, torch.int32, self.ws.device)
+
+    def csr(self, n_segments: int, n_pixels: int, n_pairs: int):
+        import torch
+        v = self.view(n_segments)
+        off = _alias(v.pix_seg_off, n_pixels + 1, torch.int32, self.ws.device)
+        ids = _alias(v.pix_seg_ids, n_pairs, torch.int32, self.ws.device)
+        return off, ids
+
+
+class EventIO:
+    """End-to-end use of :class:`EventRunner`: pinned host segments in, hits out.
+
+    ``simulate`` copies one event's segment columns from pinned host memory
+    to the device, runs sim_event and reads the hit list back to the host.
+    """
+
+    def __init__(self, runner: EventRunner):
+        import torch
+        self.r = runner
+        n = runner.max_segments
+        self.dev_cols = {k: torch.empty(n, dtype=torch.float32, device=runner.device) for k in Segments.KEYS}
+        self.host_counts = torch.zeros(4, dtype=torch.int64).pin_memory()
+        cap = runner.hits.capacity
+        self.host_hits = {k: torch.empty(max(cap, 1), dtype=getattr(runner.hits, k).dtype).pin_memory()
+                          for k in ("pixel", "t_cross", "t_adc", "adc", "q")}
+
+    def simulate(self, host_cols: dict, n: int, event_id: int = 0, stream=None):
+        """Returns (hits dict of host tensors, counts, h2d_bytes, d2h_bytes)."""
+        import torch
+        for k in Segments.KEYS:
+            self.dev_cols[k][:n].copy_(host_cols[k][:n], non_blocking=True)
+        seg = Segments({k: self.dev_cols[k][:n] for k in Segments.KEYS}, event_id)
+        self.r.enqueue(seg, stream)
+        self.host_counts.copy_(self.r.ws[:4], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        counts = [int(x) for x in self.host_counts.tolist()]
+        nh = min(counts[2], self.r.hits.capacity)
+        d2h = 32
+        out = {}
+        for k, t in self.host_hits.items():
+            src = getattr(self.r.hits, k)[:nh]
+            t[:nh].copy_(src, non_blocking=True)
+            out[k] = t[:nh]
+            d2h += nh * src.element_size()
+        torch.cuda.current_stream().synchronize()
+        return out, counts, 9 * 4 * n, d2h

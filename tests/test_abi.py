@@ -1,0 +1,81 @@
+"""CPU checks of the C ABI: the library loads, exports every declared entry
+point, agrees with the binding's struct layouts, and rejects bad arguments on
+the host before any launch (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2212_09807_gb300 import build, sim
+    build.build()
+    return sim.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "sim.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sim_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_path_entry_points():
+    names = declared_functions()
+    for f in ("sim_quench_drift", "sim_pixel_map", "sim_induced_current", "sim_electronics", "sim_event"):
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    import subprocess
+    from paper_2212_09807_gb300 import sim
+    out = subprocess.run(["nm", "-D", "--defined-only", sim.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (sim_[a-z_0-9]+)", out))
+    missing = [f for f in declared_functions() if f not in exported]
+    assert not missing, missing
+    for f in declared_functions():
+        assert hasattr(L, f)
+
+
+def test_struct_sizes_match_binding(L):
+    from paper_2212_09807_gb300 import sim
+    sizes = (C.c_int64 * 5)()
+    L.sim_abi_sizes(sizes)
+    assert list(sizes) == [C.sizeof(sim.SimConfig), C.sizeof(sim.SimSegments), C.sizeof(sim.SimResponse),
+                           C.sizeof(sim.SimDrifted), C.sizeof(sim.SimHits)]
+
+
+def test_strerror(L):
+    assert L.sim_strerror(0) == b"ok"
+    assert b"invalid" in L.sim_strerror(-1)
+
+
+def test_host_argument_checks_reject_before_launch(L):
+    from paper_2212_09807_gb300 import sim
+    from synth import params
+    cfg = sim.make_config(params.module_config())
+    b = C.c_size_t()
+    assert L.sim_workspace_size(C.byref(cfg), 100, 1000, 100, C.byref(b)) == 0 and b.value > 0
+    assert L.sim_workspace_size(C.byref(cfg), -1, 1000, 100, C.byref(b)) == -1
+    bad = sim.make_config(params.module_config(n_ticks=0))
+    assert L.sim_workspace_size(C.byref(bad), 1, 1, 1, C.byref(b)) == -1
+    seg = sim.SimSegments()
+    seg.n = 5                                   # null columns
+    d = sim.SimDrifted()
+    assert L.sim_quench_drift(C.byref(cfg), C.byref(seg), C.byref(d), None) == -1
+    r = sim.SimResponse()
+    r.nb, r.nt, r.ld, r.bins_per_pitch = 45, 1950, 1950, 30   # ld not a multiple of 4
+    h = sim.SimHits()
+    assert L.sim_event(C.byref(cfg), C.byref(seg), C.byref(r), 10, 10, C.byref(h), None, 0, None) == -1
+
+
+def test_workspace_grows_with_capacities(L):
+    from paper_2212_09807_gb300 import sim
+    from synth import params
+    cfg = sim.make_config(params.module_config())
+    a = sim.workspace_size(cfg, 1000, 10000, 1000)
+    b = sim.workspace_size(cfg, 1000, 10000, 2000)
+    assert b - a >= 1000 * 2000 * 4      # the current array [pixels][ticks] is inside

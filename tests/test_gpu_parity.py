@@ -1,0 +1,315 @@
+"""GPU parity of every step of the CUDA path against the FP64 oracle, called
+through the C ABI.
+
+Tolerances (stated once, used below):
+  * Q_a, t_drift, sigma_T, sigma_L: FP32 evaluation of closed forms, rtol 2e-6;
+    anode and point count N: exact (decided in FP64 on both sides);
+  * pixel map: set-equal, except pairs whose oracle distance margin is within
+    1e-5 cm of the map radius (FP32 geometry on the GPU);
+  * current (FP32 direct gather): per pixel ||I_gpu - I_ref||_inf <= 1e-4 ||I_ref||_inf
+    (hard) with the median <= 1e-5, and integrated charge per pixel <= 1e-5;
+  * hits: bit-exact pixel, t_cross, t_adc and ADC code up to the oracle's first
+    tie (a threshold or ADC decision within BAND electrons), with at most 1% of
+    hit-bearing pixels cut by a tie.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2212_09807_gb300 import sim
+from synth import events, params, response
+
+from gpu_harness import Steps, compare_pixel_hits, current_errors, hits_of_pixel, lut_pair
+
+pytestmark = pytest.mark.gpu
+
+MAP_BAND = 1e-5
+CUR_HARD, CUR_MED, Q_TOL = 1e-4, 1e-5, 1e-5
+
+
+def _edge_segments(cfg):
+    """Degenerate cases appended to the random events: zero length, midpoint
+    outside, on the cathode, exactly 10 um long, a long diagonal, near a tile
+    corner and on the detector edge."""
+    g = params.geometry(cfg)
+    D = g["drift"]
+    rows = [
+        (5.0, 5.0, 10.0, 0.0, 5.0, 5.0, 10.0, 0.0, 1.0),
+        (-3.0, 5.0, 10.0, 0.0, -2.5, 5.0, 10.0, 0.0, 1.0),
+        (8.0, 9.0, D - 0.05, 0.0, 8.2, 9.1, D + 0.05, 0.0, 0.3),
+        (12.0, 13.0, 20.0, 0.0, 12.001, 13.0, 20.0, 0.0, 0.002),
+        (10.0, 10.0, 5.0, 0.0, 10.7, 10.6, 6.0, 0.0, 2.5),
+        (31.0, 31.0, 40.0, 1.0, 31.1, 31.05, 40.3, 1.0, 0.5),
+        (0.05, 0.1, 3.0, 0.0, 0.4, 0.2, 3.2, 0.0, 0.6),
+    ]
+    a = np.asarray(rows, dtype=np.float32)
+    return {k: a[:, i] for i, k in enumerate(events.COLS)}
+
+
+def _event(cfg, seed, n, max_len=0.6, t_range=(0.0, 0.0)):
+    seg = events.scatter_event(cfg, seed, n, max_len=max_len, t_range=t_range)
+    e = _edge_segments(cfg)
+    return {k: np.concatenate([seg[k], e[k]]).astype(np.float32) for k in events.COLS}
+
+
+@pytest.fixture(scope="module")
+def small():
+    cfg = params.small_config()
+    seg = _event(cfg, 101, 60)
+    lut_dev, lut64 = lut_pair(cfg)
+    st = Steps(cfg, seg, lut_dev, event_id=5).all()
+    o = oracle.Oracle(cfg, params.LUT, lut64)
+    return dict(cfg=cfg, seg=seg, st=st, o=o, d=o.quench_drift(seg), lut_dev=lut_dev, lut64=lut64)
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_quench_drift(model):
+    cfg = params.small_config(recomb_model=model)
+    seg = _event(cfg, 7 + model, 300)
+    lut_dev, _ = lut_pair(cfg)
+    st = Steps(cfg, seg, lut_dev).quench_drift()
+    g = st.drifted_np()
+    d = oracle.Oracle(cfg, params.LUT).quench_drift(seg)
+    assert np.array_equal(g["anode"], d["anode"])
+    assert np.array_equal(g["n_samples"], d["n_samples"])
+    for k in ("Qa", "t_drift", "sigma_T", "sigma_L"):
+        np.testing.assert_allclose(g[k], d[k], rtol=2e-6, atol=1e-30, err_msg=k)
+    assert (d["anode"] < 0).sum() >= 2   # degenerate segments present and inactive
+
+
+def test_pixel_map(small):
+    st, o, seg, d = small["st"], small["o"], small["seg"], small["d"]
+    m = st.maps_np()
+    n = len(seg["x0"])
+    seen_ties = 0
+    for s in range(n):
+        gpu = set(m["seg_ids"][m["seg_off"][s]:m["seg_off"][s + 1]].tolist())
+        ids, mg = o.map_segment(seg, d, s)
+        ref = set(ids.tolist())
+        for p in ref - gpu:
+            assert mg[list(ids).index(p)] < MAP_BAND, (s, p)
+            seen_ties += 1
+        for p in gpu - ref:
+            assert o.pair_margin(seg, d, s, p) > -MAP_BAND, (s, p)
+            seen_ties += 1
+    assert seen_ties <= 2
+    act = m["active"]
+    assert np.all(np.diff(act) > 0)                         # increasing pixel ids
+    assert set(act.tolist()) == set(m["seg_ids"].tolist())
+    for i, p in enumerate(act):
+        lst = m["pix_ids"][m["pix_off"][i]:m["pix_off"][i + 1]]
+        assert np.all(np.diff(lst) > 0)                     # segment order fixed
+        assert all(p in m["seg_ids"][m["seg_off"][s]:m["seg_off"][s + 1]] for s in lst)
+
+
+def _current_parity(cfg, seg, lut_dev, lut64, event_id=0, lut_par=None, frac=1.0):
+    lut_par = lut_par or params.LUT
+    st = Steps(cfg, seg, lut_dev, event_id=event_id, lut_par=lut_par).quench_drift().pixel_map().induced_current()
+    m = st.maps_np()
+    cur = st.current_np()
+    o = oracle.Oracle(cfg, lut_par, lut64)
+    d = o.quench_drift(seg)
+    idx = np.arange(len(m["active"]))
+    if frac < 1.0:
+        idx = np.random.default_rng(0).choice(idx, max(8, int(frac * len(idx))), replace=False)
+    refs = []
+    for i in idx:
+        segs = m["pix_ids"][m["pix_off"][i]:m["pix_off"][i + 1]]
+        refs.append(o.pixel_current(seg, d, int(m["active"][i]), segs, event_id=event_id))
+    ref = np.array(refs)
+    rel, qrel = current_errors(cur[idx], ref)
+    big = np.abs(ref).max(axis=1) > 0
+    return rel[big], qrel[big], ref
+
+
+def test_induced_current_all_pixels(small):
+    rel, qrel, ref = _current_parity(small["cfg"], small["seg"], small["lut_dev"], small["lut64"], event_id=5)
+    assert len(rel) > 200
+    assert rel.max() <= CUR_HARD, rel.max()
+    assert np.median(rel) <= CUR_MED, np.median(rel)
+    assert np.quantile(qrel, 0.99) <= Q_TOL and qrel.max() <= 10 * Q_TOL
+
+
+@pytest.mark.parametrize("case", ["M4", "ragged_window", "box_shifted", "bipolar"])
+def test_induced_current_variants(case):
+    over, lut_kw, tr = {}, {}, (0.0, 0.0)
+    if case == "M4":
+        over = dict(mc_per_sample=4)
+    elif case == "ragged_window":
+        over = dict(n_ticks=2500, t_window0_us=-37.3)           # two tick chunks, ragged tail
+    elif case == "box_shifted":
+        over = dict(recomb_model=1, t_window0_us=3.05)
+        tr = (0.0, 9.0)
+    elif case == "bipolar":
+        lut_kw = dict(bipolar=0.5)
+    cfg = params.small_config(**over)
+    seg = _event(cfg, 300 + len(case), 25, t_range=tr)
+    lut_dev, lut64 = lut_pair(cfg, **lut_kw)
+    rel, qrel, _ = _current_parity(cfg, seg, lut_dev, lut64, event_id=11)
+    assert rel.max() <= CUR_HARD, rel.max()
+    assert np.median(rel) <= CUR_MED
+    if case != "bipolar":                  # bipolar pixels can integrate to ~0
+        assert qrel.max() <= 10 * Q_TOL
+
+
+def test_electronics_bit_exact_on_same_current(small):
+    """Same FP32 current into both front ends: hits must agree up to ties."""
+    st, o, cfg = small["st"], small["o"], small["cfg"]
+    m = st.maps_np()
+    cur = st.current_np()
+    h = st.hits_np()
+    band = 0.05                        # electrons; FP32 scan vs FP64 sum differ by ~1e-3 e-
+    n_hit_pix, n_tied, n_cmp = 0, 0, 0
+    for i, p in enumerate(m["active"]):
+        ref = o.electronics(int(p), cur[i].astype(np.float64), event_id=5, band=band)
+        g = hits_of_pixel(h, int(p))
+        if len(ref["t_cross"]) or len(g["t_cross"]):
+            n_hit_pix += 1
+        if ref["tie_tick"] >= 0:
+            n_tied += 1
+        ok, nc = compare_pixel_hits(g, ref, 976.5625)
+        assert ok, (p, ref, g)
+        n_cmp += nc
+        mref = ref["t_adc"] < (ref["tie_tick"] if ref["tie_tick"] >= 0 else 1 << 30)
+        np.testing.assert_allclose(g["q"][: mref.sum()], ref["q"][mref], rtol=1e-5, atol=0.05)
+    assert n_cmp > 20
+    assert n_tied <= max(1, 0.01 * n_hit_pix)
+
+
+def test_electronics_closed_form_gpu():
+    """Noise off, constant current per pixel: first crossing, ADC code and period."""
+    cfg = params.small_config(sigma_reset_e=0.0, sigma_disc_e=0.0, sigma_unc_e=0.0, n_ticks=1000)
+    c = sim.make_config(cfg)
+    dev = torch.device("cuda:0")
+    iv = np.array([37.0, 333.0, 1250.5, 4999.0, 7000.0, 10.0], dtype=np.float32)
+    P = len(iv)
+    cur = torch.as_tensor(np.repeat(iv[:, None], 1000, axis=1), device=dev)
+    active = torch.arange(P, dtype=torch.int32, device=dev) * 7
+    hits = sim.Hits(10000, dev)
+    ws = torch.zeros((sim.workspace_size(c, 0, 0, P) + 7) // 8, dtype=torch.int64, device=dev)
+    counts = ws[:4]
+    counts[1] = P
+    sim.sim_electronics(c, 0, active, cur, counts, hits, ws)
+    torch.cuda.synchronize()
+    n = int(counts[2])
+    h = hits.to_numpy(n)
+    for j, i in enumerate(iv):
+        g = hits_of_pixel(h, 7 * j)
+        n_up = int(np.ceil(np.float32(5000.0) / i))
+        t1 = n_up - 1
+        if t1 + 16 >= 1000:
+            assert len(g["t_cross"]) == 0
+            continue
+        assert g["t_cross"][0] == t1 and g["t_adc"][0] == t1 + 16
+        assert g["adc"][0] == min(255, int(np.floor(np.float32((t1 + 17) * i) / np.float32(976.5625))))
+        assert np.all(np.diff(g["t_cross"]) == 16 + n_up)
+
+
+def test_event_matches_steps_and_is_deterministic(small):
+    cfg, seg, lut_dev = small["cfg"], small["seg"], small["lut_dev"]
+    st = small["st"]
+    run = sim.EventRunner(cfg, lut_dev, params.LUT["nt"], params.LUT["bins_per_pitch"], len(seg["x0"]),
+                          st.pair_cap, st.pix_cap, st.hit_cap)
+    S = sim.Segments.from_numpy(seg, 5)
+    outs = []
+    for _ in range(2):
+        run.enqueue(S)
+        torch.cuda.synchronize()
+        n_pairs, n_pix, n_hits, status = run.counts()
+        assert status == 0
+        outs.append((run.current(S.n, n_pix).cpu().numpy().copy(), run.hits.to_numpy(n_hits)))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    for k in outs[0][1]:
+        assert np.array_equal(outs[0][1][k], outs[1][1][k])
+    assert np.array_equal(outs[0][0], st.current_np())
+    hs = st.hits_np()
+    for k in hs:
+        assert np.array_equal(hs[k], outs[0][1][k])
+
+
+def test_event_hits_against_oracle_end_to_end(small):
+    """Oracle current (FP64) into the oracle front end vs the GPU event."""
+    st, o, seg, d = small["st"], small["o"], small["seg"], small["d"]
+    m = st.maps_np()
+    h = st.hits_np()
+    band = 1e-4 * 5000.0               # currents differ by up to 1e-5 relative
+    n_hit_pix = n_tied = n_cmp = 0
+    for i, p in enumerate(m["active"]):
+        segs = m["pix_ids"][m["pix_off"][i]:m["pix_off"][i + 1]]
+        I = o.pixel_current(seg, d, int(p), segs, event_id=5)
+        ref = o.electronics(int(p), I, event_id=5, band=band)
+        g = hits_of_pixel(h, int(p))
+        if len(ref["t_cross"]) or len(g["t_cross"]):
+            n_hit_pix += 1
+        if ref["tie_tick"] >= 0:
+            n_tied += 1
+        ok, nc = compare_pixel_hits(g, ref, 976.5625)
+        assert ok, (p, ref, g)
+        n_cmp += nc
+    assert n_cmp > 20
+    assert n_tied <= max(1, 0.01 * n_hit_pix)
+
+
+def test_capacity_overflow_then_retry():
+    cfg = params.small_config()
+    seg = _event(cfg, 77, 40)
+    lut_dev, _ = lut_pair(cfg)
+    st = Steps(cfg, seg, lut_dev, pair_cap=50, pix_cap=2000, hit_cap=5).all()
+    n_pairs, n_pix, n_hits, status = st.count_values()
+    assert status & sim.SIM_STATUS_PAIR_OVERFLOW and n_pairs > 50
+    st2 = Steps(cfg, seg, lut_dev, pair_cap=n_pairs, pix_cap=10, hit_cap=5).all()
+    _, n_pix2, _, status2 = st2.count_values()
+    assert status2 & sim.SIM_STATUS_PIXEL_OVERFLOW and n_pix2 > 10
+    st3 = Steps(cfg, seg, lut_dev, pair_cap=n_pairs, pix_cap=n_pix2, hit_cap=5).all()
+    _, _, n_hits3, status3 = st3.count_values()
+    assert status3 == (sim.SIM_STATUS_HIT_OVERFLOW if n_hits3 > 5 else 0)
+    st4 = Steps(cfg, seg, lut_dev, pair_cap=n_pairs, pix_cap=n_pix2, hit_cap=max(n_hits3, 1)).all()
+    assert st4.count_values()[3] == 0
+    assert st4.count_values()[2] == n_hits3
+
+
+def test_empty_and_all_inactive_events():
+    cfg = params.small_config()
+    lut_dev, _ = lut_pair(cfg)
+    empty = {k: np.zeros(0, np.float32) for k in events.COLS}
+    st = Steps(cfg, empty, lut_dev, pair_cap=16, pix_cap=16).all()
+    assert st.count_values() == [0, 0, 0, 0]
+    outside = _edge_segments(cfg)
+    outside = {k: v[:2] for k, v in outside.items()}          # zero length + outside
+    st = Steps(cfg, outside, lut_dev, pair_cap=16, pix_cap=16).all()
+    assert st.count_values() == [0, 0, 0, 0]
+
+
+def test_module_event_sampled_pixels():
+    """The ~20k-segment module event at full size through sim_event (the
+    benchmark's launch configuration): sampled pixels against the oracle,
+    including the oracle's own brute-force segment list per pixel."""
+    cfg = params.module_config()
+    seg = events.module_event(cfg, seed=params.BASE["seed"] + 1)
+    lut_dev, lut64 = lut_pair(cfg)
+    n = len(seg["x0"])
+    run = sim.EventRunner(cfg, lut_dev, params.LUT["nt"], params.LUT["bins_per_pitch"], n, 40 * n, 4 * n, 4 * n)
+    S = sim.Segments.from_numpy(seg, 1)
+    run.enqueue(S)
+    torch.cuda.synchronize()
+    n_pairs, n_pix, n_hits, status = run.counts()
+    assert status == 0 and n_pix > 1000 and n_hits > 100
+    act = run.active_pixels(n, n_pix).cpu().numpy()
+    off, ids = run.csr(n, n_pix, n_pairs)
+    off, ids = off.cpu().numpy(), ids.cpu().numpy()
+    cur = run.current(n, n_pix)
+    o = oracle.Oracle(cfg, params.LUT, lut64)
+    d = o.quench_drift(seg)
+    rng = np.random.default_rng(1)
+    for i in rng.choice(n_pix, 10, replace=False):
+        p = int(act[i])
+        segs, mg = o.segments_for_pixel(seg, d, p)
+        gl = ids[off[i]:off[i + 1]]
+        diff = set(segs.tolist()) ^ set(gl.tolist())
+        for s in diff:
+            assert abs(o.pair_margin(seg, d, s, p)) < MAP_BAND
+        ref = o.pixel_current(seg, d, p, gl, event_id=1)
+        g = cur[i].cpu().numpy()
+        err = np.abs(g - ref).max() / max(np.abs(ref).max(), 1e-300)
+        assert err <= CUR_HARD, (p, err)

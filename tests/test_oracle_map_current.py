@@ -55,7 +55,7 @@ def test_point_maps_to_3x3():
     xc, yc = 10.5 * p, 20.5 * p
     seg = _seg([(xc, yc, 1.0 - 2 ** -12, 0, xc, yc, 1.0 + 2 ** -12, 0, 1.0)])
     d = o.quench_drift(seg)
-    ids, _ = o.map_segment(seg, d, 0)
+    ids, _ = o.map_segment(seg, d, 0, box=False)
     nx = 70
     exp = sorted((20 + dy) * nx + 10 + dx for dy in (-1, 0, 1) for dx in (-1, 0, 1))
     assert sorted(ids.tolist()) == exp
@@ -86,6 +86,18 @@ def test_boundary_distance_counts_as_mapped():
     assert pid in ids.tolist()
     assert mg[ids.tolist().index(pid)] == 0.0
     assert 20 * 70 + 9 not in ids.tolist()
+
+
+def test_box_restricted_map_equals_full_brute_force():
+    cfg = params.small_config()
+    o = oracle.Oracle(cfg, params.LUT)
+    from synth import events
+    seg = events.scatter_event(cfg, 5, 120, max_len=1.0)
+    d = o.quench_drift(seg)
+    for s in range(len(seg["x0"])):
+        a, ma = o.map_segment(seg, d, s, box=False)
+        b, mb = o.map_segment(seg, d, s, box=True)
+        assert np.array_equal(a, b) and np.array_equal(ma, mb)
 
 
 def test_map_contains_every_pixel_with_current():
