@@ -183,10 +183,11 @@ int sim_induced_current(const sim_config *cfg, const sim_segments *seg, const si
                         void *stream)
 {
     if (!cfg_ok(cfg) || !seg_ok(seg) || !resp_ok(resp, true) || !counts || pix_cap < 0) return SIM_ERR_INVALID_ARG;
-    if (pix_cap > 0 && (!active_pixels || !pix_seg_off || !pix_seg_ids || !current || !drifted_ok(dr)))
-        return SIM_ERR_INVALID_ARG;
+    if (pix_cap > 0 && (!active_pixels || !pix_seg_off || !pix_seg_ids || !current)) return SIM_ERR_INVALID_ARG;
+    if (pix_cap > 0 && seg->n > 0 && !drifted_ok(dr)) return SIM_ERR_INVALID_ARG;
     if (pix_cap == 0) return SIM_OK;
-    const cudaError_t e = launch_induced_current(*cfg, *seg, *dr, *resp, active_pixels, pix_seg_off, pix_seg_ids,
+    const sim_drifted d0 = dr ? *dr : sim_drifted{};
+    const cudaError_t e = launch_induced_current(*cfg, *seg, d0, *resp, active_pixels, pix_seg_off, pix_seg_ids,
                                                  counts, pix_cap, current, (cudaStream_t)stream);
     return e == cudaSuccess ? SIM_OK : cuda_fail(e);
 }

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(kThreads) k_induced_current(CurArgs a)
     __shared__ int q_A[kThreads];       // integer arrival tick
     __shared__ float4 q_w[kThreads];    // q-scaled bilinear weights (00, 10, 01, 11)
     __shared__ float q_f[kThreads];     // fractional arrival
-    __shared__ int q_n;
+    __shared__ int warp_n[kThreads / 32];
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int T = a.c.n_ticks, L = a.nt, M = a.c.mc_per_sample;
@@ -75,8 +75,6 @@ __global__ void __launch_bounds__(kThreads) k_induced_current(CurArgs a)
                 const int total = A.N * M;
                 const float invN = 1.0f / (float)A.N;
                 for (int base = 0; base < total; base += kThreads) {
-                    if (tid == 0) q_n = 0;
-                    __syncthreads();
                     const int idx = base + tid;
                     bool ok = false;
                     int row = 0, Ai = 0;
@@ -113,10 +111,19 @@ __global__ void __launch_bounds__(kThreads) k_induced_current(CurArgs a)
                                             q * (1.f - wx) * wy1, q * wx1 * wy1);
                         }
                     }
+                    // queue order = point order (warp prefix of ballot counts), so the
+                    // FP32 sum is formed in the same order on every run
                     const unsigned m = __ballot_sync(0xffffffffu, ok);
-                    int wbase = 0;
-                    if (lane == 0 && m) wbase = atomicAdd(&q_n, __popc(m));
-                    wbase = __shfl_sync(0xffffffffu, wbase, 0);
+                    const int warp = tid >> 5;
+                    if (lane == 0) warp_n[warp] = __popc(m);
+                    __syncthreads();
+                    int wbase = 0, nq = 0;
+#pragma unroll
+                    for (int w2 = 0; w2 < kThreads / 32; ++w2) {
+                        const int c2 = warp_n[w2];
+                        wbase += (w2 < warp) ? c2 : 0;
+                        nq += c2;
+                    }
                     if (ok) {
                         const int slot = wbase + __popc(m & ((1u << lane) - 1u));
                         q_row[slot] = row;
@@ -125,7 +132,6 @@ __global__ void __launch_bounds__(kThreads) k_induced_current(CurArgs a)
                         q_f[slot] = f;
                     }
                     __syncthreads();
-                    const int nq = q_n;
                     for (int r = 0; r < nq; ++r) {
                         const int b0 = q_row[r];
                         const float4 wr = q_w[r];
