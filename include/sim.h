@@ -202,6 +202,29 @@ int sim_event(const sim_config *cfg, const sim_segments *seg, const sim_response
               int64_t max_pairs, int64_t max_pixels, const sim_hits *out, void *ws,
               size_t ws_bytes, void *stream);
 
+/* Allocation-free pixel map.  The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc when they map an event, such
+ * as services that fix their device-memory budget at start-up and must not
+ * allocate in their event loop, or code embedded in a framework whose
+ * allocator owns all device memory.  Same inputs, outputs and results as
+ * sim_pixel_map, with the counts block (device int64[4], written as by
+ * sim_pixel_map) passed explicitly; its scratch lives in a file-scope device
+ * array of SIM_NOALLOC_SCRATCH_BYTES that every device loading this library
+ * holds until the process exits.  The call allocates nothing.
+ *  - Returns SIM_ERR_CAPACITY, with nothing enqueued, when the event needs more
+ *    scratch than that: 2 x 4 x (total pixels + 1) bytes plus the scan's tile
+ *    sums, i.e. detectors of up to about two million pixels.
+ *  - The first call on a device looks up the array's device address (a host
+ *    call, cudaGetSymbolAddress); make that first call before any stream
+ *    capture.
+ *  - All calls share the array: calls whose work overlaps on the GPU race and
+ *    must be ordered by the caller (one stream, or events between streams). */
+#define SIM_NOALLOC_SCRATCH_BYTES (16u << 20)
+int sim_pixel_map_noalloc(const sim_config *cfg, const sim_segments *seg, const sim_drifted *dr,
+                          const sim_response *resp, int32_t *seg_pix_off, int32_t *seg_pix_ids,
+                          int64_t pair_cap, int32_t *active_pixels, int32_t *pix_seg_off,
+                          int32_t *pix_seg_ids, int64_t pix_cap, int64_t *counts, void *stream);
+
 /* Device addresses of sim_event's intermediates inside its workspace (for
  * inspection after the stream has run): per-segment results, both CSR maps,
  * the active-pixel list, the induced current [max_pixels][n_ticks] and the

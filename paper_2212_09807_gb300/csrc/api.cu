@@ -114,6 +114,14 @@ void fill_view(const Layout &L, char *w, sim_event_view *v)
 
 }  // namespace
 
+namespace larsim {
+// argument checks and error recording shared with pixel_map_static.cu
+bool abi_config_ok(const sim_config *c) { return cfg_ok(c); }
+bool abi_segments_ok(const sim_segments *s) { return seg_ok(s); }
+bool abi_drifted_ok(const sim_drifted *d) { return drifted_ok(d); }
+int abi_cuda_fail(cudaError_t e) { return cuda_fail(e); }
+}  // namespace larsim
+
 extern "C" {
 
 const char *sim_strerror(int code)

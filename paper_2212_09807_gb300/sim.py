@@ -109,8 +109,10 @@ def lib():
                                 cp(SimHits), _P, C.c_size_t, _P]
         L.sim_event_view_of.argtypes = [cp(SimConfig), C.c_int64, C.c_int64, C.c_int64, _P, C.c_size_t,
                                         cp(SimEventView)]
+        L.sim_pixel_map_noalloc.argtypes = [cp(SimConfig), cp(SimSegments), cp(SimDrifted), cp(SimResponse),
+                                            _P, _P, C.c_int64, _P, _P, _P, C.c_int64, _P, _P]
         for f in ("sim_workspace_size", "sim_quench_drift", "sim_pixel_map", "sim_induced_current",
-                  "sim_electronics", "sim_event", "sim_event_view_of"):
+                  "sim_electronics", "sim_event", "sim_event_view_of", "sim_pixel_map_noalloc"):
             getattr(L, f).restype = C.c_int
         sizes = (C.c_int64 * 5)()
         L.sim_abi_sizes(sizes)
@@ -266,6 +268,17 @@ def sim_pixel_map(cfg: SimConfig, seg: Segments, dr: Drifted, resp: Response, se
                                _ptr(pix_seg_off), _ptr(pix_seg_ids), int(active_pixels.numel()),
                                _ptr(ws), int(ws.numel() * ws.element_size()), _stream(stream)),
            "sim_pixel_map")
+
+
+def sim_pixel_map_noalloc(cfg: SimConfig, seg: Segments, dr: Drifted, resp: Response, seg_pix_off, seg_pix_ids,
+                          active_pixels, pix_seg_off, pix_seg_ids, counts, stream=None):
+    """sim_pixel_map without a workspace: for callers that cannot allocate
+    device memory when they map an event (scratch lives in the library)."""
+    s, d, r = seg.struct(), dr.struct(), resp.struct()
+    _check(lib().sim_pixel_map_noalloc(C.byref(cfg), C.byref(s), C.byref(d), C.byref(r), _ptr(seg_pix_off),
+                                       _ptr(seg_pix_ids), int(seg_pix_ids.numel()), _ptr(active_pixels),
+                                       _ptr(pix_seg_off), _ptr(pix_seg_ids), int(active_pixels.numel()),
+                                       _ptr(counts), _stream(stream)), "sim_pixel_map_noalloc")
 
 
 def sim_induced_current(cfg: SimConfig, seg: Segments, dr: Drifted, resp: Response, active_pixels,
