@@ -256,7 +256,8 @@ def run_ours(args):
         sim.sim_pixel_map(run.cfg, segs, dr, run.resp, seg_pix_off, seg_pix_ids, active, pix_seg_off,
                           pix_seg_ids, run.ws)
         evs[2].record()
-        sim.sim_induced_current(run.cfg, segs, dr, run.resp, active, pix_seg_off, pix_seg_ids, counts, current)
+        sim.sim_induced_current(run.cfg, segs, dr, run.resp, active, pix_seg_off, pix_seg_ids, counts, current,
+                                run.ws)
         evs[3].record()
         sim.sim_electronics(run.cfg, segs.event_id, active, current, counts, run.hits, run.ws)
         evs[4].record()

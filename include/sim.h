@@ -179,11 +179,14 @@ int sim_pixel_map(const sim_config *cfg, const sim_segments *seg, const sim_drif
  * order.  current: FP32 [pix_cap][n_ticks]; rows [0, counts[1]) are written.
  * counts: device int64[4] counts block as written by sim_pixel_map ([1] =
  * active pixels, [3] = status); nothing is computed when the status word is
- * nonzero or counts[1] > pix_cap. */
+ * nonzero or counts[1] > pix_cap.  Workspace (scratch from byte 256 on):
+ * sim_workspace_size(cfg, 0, 0, pix_cap) bytes, sized for the current device
+ * (a per-CTA record buffer).  Table limits: nb * nb <= 2048, nt <= 2048. */
 int sim_induced_current(const sim_config *cfg, const sim_segments *seg, const sim_drifted *dr,
                         const sim_response *resp, const int32_t *active_pixels,
                         const int32_t *pix_seg_off, const int32_t *pix_seg_ids,
-                        const int64_t *counts, int64_t pix_cap, float *current, void *stream);
+                        const int64_t *counts, int64_t pix_cap, float *current, void *ws,
+                        size_t ws_bytes, void *stream);
 
 /* Step 5 (Sec. 3.4): per active pixel, tick by tick, charge integration,
  * discriminator with uncorrelated and threshold noise, hold, 8-bit ADC and

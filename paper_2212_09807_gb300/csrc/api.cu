@@ -44,6 +44,7 @@ bool seg_ok(const sim_segments *s)
 bool resp_ok(const sim_response *r, bool need_table)
 {
     if (!r || r->nb < 1 || r->nt < 1 || r->ld < r->nt || (r->ld % 4) != 0 || r->bins_per_pitch < 1) return false;
+    if (!current_table_ok(r->nb, r->nt)) return false;
     if (need_table && (!r->lut || (reinterpret_cast<uintptr_t>(r->lut) & 15) != 0)) return false;
     return true;
 }
@@ -75,8 +76,11 @@ Layout layout(const sim_config &c, int64_t n, int64_t pairs, int64_t pixels)
         return at;
     };
     L.counts = take(256);
-    const size_t ms = map_scratch_bytes(c, n), es = elec_scratch_bytes(c, pixels);
-    L.scratch = take(ms > es ? ms : es);
+    size_t sc = map_scratch_bytes(c, n);
+    const size_t es = elec_scratch_bytes(c, pixels), cs = current_scratch_bytes(pixels);
+    if (es > sc) sc = es;
+    if (cs > sc) sc = cs;
+    L.scratch = take(sc);
     L.Qa = take(4 * (size_t)n);
     L.td = take(4 * (size_t)n);
     L.sT = take(4 * (size_t)n);
@@ -188,15 +192,18 @@ int sim_pixel_map(const sim_config *cfg, const sim_segments *seg, const sim_drif
 int sim_induced_current(const sim_config *cfg, const sim_segments *seg, const sim_drifted *dr,
                         const sim_response *resp, const int32_t *active_pixels, const int32_t *pix_seg_off,
                         const int32_t *pix_seg_ids, const int64_t *counts, int64_t pix_cap, float *current,
-                        void *stream)
+                        void *ws, size_t ws_bytes, void *stream)
 {
-    if (!cfg_ok(cfg) || !seg_ok(seg) || !resp_ok(resp, true) || !counts || pix_cap < 0) return SIM_ERR_INVALID_ARG;
+    if (!cfg_ok(cfg) || !seg_ok(seg) || !resp_ok(resp, true) || !counts || pix_cap < 0 || !ws)
+        return SIM_ERR_INVALID_ARG;
     if (pix_cap > 0 && (!active_pixels || !pix_seg_off || !pix_seg_ids || !current)) return SIM_ERR_INVALID_ARG;
     if (pix_cap > 0 && seg->n > 0 && !drifted_ok(dr)) return SIM_ERR_INVALID_ARG;
     if (pix_cap == 0) return SIM_OK;
+    if (ws_bytes < 256 + current_scratch_bytes(pix_cap)) return SIM_ERR_CAPACITY;
     const sim_drifted d0 = dr ? *dr : sim_drifted{};
     const cudaError_t e = launch_induced_current(*cfg, *seg, d0, *resp, active_pixels, pix_seg_off, pix_seg_ids,
-                                                 counts, pix_cap, current, (cudaStream_t)stream);
+                                                 counts, pix_cap, current, reinterpret_cast<char *>(ws) + 256,
+                                                 (cudaStream_t)stream);
     return e == cudaSuccess ? SIM_OK : cuda_fail(e);
 }
 
@@ -242,7 +249,7 @@ int sim_event(const sim_config *cfg, const sim_segments *seg, const sim_response
                          w + L.scratch, st);
     if (e != cudaSuccess) return cuda_fail(e);
     e = launch_induced_current(*cfg, *seg, v.dr, *resp, v.active_pixels, v.pix_seg_off, v.pix_seg_ids, v.counts,
-                               max_pixels, v.current, st);
+                               max_pixels, v.current, w + L.scratch, st);
     if (e != cudaSuccess) return cuda_fail(e);
     e = launch_electronics(*cfg, seg->event_id, v.active_pixels, v.current, v.counts, max_pixels, *out,
                            w + L.scratch, st);

@@ -102,7 +102,7 @@ def lib():
         L.sim_pixel_map.argtypes = [cp(SimConfig), cp(SimSegments), cp(SimDrifted), cp(SimResponse),
                                     _P, _P, C.c_int64, _P, _P, _P, C.c_int64, _P, C.c_size_t, _P]
         L.sim_induced_current.argtypes = [cp(SimConfig), cp(SimSegments), cp(SimDrifted), cp(SimResponse),
-                                          _P, _P, _P, _P, C.c_int64, _P, _P]
+                                          _P, _P, _P, _P, C.c_int64, _P, _P, C.c_size_t, _P]
         L.sim_electronics.argtypes = [cp(SimConfig), C.c_uint64, _P, _P, _P, C.c_int64, cp(SimHits),
                                       _P, C.c_size_t, _P]
         L.sim_event.argtypes = [cp(SimConfig), cp(SimSegments), cp(SimResponse), C.c_int64, C.c_int64,
@@ -282,12 +282,13 @@ def sim_pixel_map_noalloc(cfg: SimConfig, seg: Segments, dr: Drifted, resp: Resp
 
 
 def sim_induced_current(cfg: SimConfig, seg: Segments, dr: Drifted, resp: Response, active_pixels,
-                        pix_seg_off, pix_seg_ids, counts, current, stream=None):
+                        pix_seg_off, pix_seg_ids, counts, current, ws, stream=None):
     s, d, r = seg.struct(), dr.struct(), resp.struct()
     pix_cap = int(current.shape[0])
     _check(lib().sim_induced_current(C.byref(cfg), C.byref(s), C.byref(d), C.byref(r), _ptr(active_pixels),
                                      _ptr(pix_seg_off), _ptr(pix_seg_ids), _ptr(counts), pix_cap,
-                                     _ptr(current), _stream(stream)), "sim_induced_current")
+                                     _ptr(current), _ptr(ws), int(ws.numel() * ws.element_size()),
+                                     _stream(stream)), "sim_induced_current")
 
 
 def sim_electronics(cfg: SimConfig, event_id: int, active_pixels, current, counts, hits: Hits, ws,

@@ -63,7 +63,7 @@ class Steps:
 
     def induced_current(self):
         sim.sim_induced_current(self.cfg, self.seg, self.dr, self.resp, self.active, self.pix_seg_off,
-                                self.pix_seg_ids, self.counts, self.current[: self.pix_cap])
+                                self.pix_seg_ids, self.counts, self.current[: self.pix_cap], self.ws)
         return self
 
     def electronics(self):
