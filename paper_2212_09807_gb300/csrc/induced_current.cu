@@ -9,9 +9,13 @@
 //   v(j) = sum_c w_c R[b_c][j],   I[k] += (1 - f) v(k - A + L - 1) + f v(k - A + L - 2)
 // (w_c include the point charge q = Q_a / (N M)).
 //
-// Design: one CTA of 512 threads per active pixel (grid-stride, two CTAs per
-// SM), output stationary: 2048 ticks per pass, lane l of warp w owning ticks
-// 128 w + 4 l .. + 3 in registers.
+// Design: one CTA of 256 threads per active pixel (grid-stride, three CTAs per
+// SM), output stationary: 2048 ticks per pass.  Warp w owns a low block of
+// 128 ticks (128 w ..) and its mirror (2048 - 128 (w + 1) ..); in each block
+// lane l owns ticks l, 32 + l, 64 + l, 96 + l, in registers.  A record's ticks
+// form one interval, which for drifting charge usually starts at the window
+// start, so pairing each low block with a high one keeps the warps evenly
+// loaded while warps skip the blocks a record does not reach.
 //  1. records: the CTA regenerates every perturbed point of the pixel's
 //     segments (Philox keyed by segment and point), keeps those within the
 //     table's reach of this pixel as records {A, b0, f, w[4]} in its scratch
@@ -19,11 +23,12 @@
 //  2. stable counting sort by bin (one warp computes destinations with
 //     match_any ranks from the bins in shared memory; the CTA moves the records);
 //  3. per distinct bin: the four table rows are staged once in shared memory
-//     (16-byte global reads issued one bin ahead into registers) in a padded
-//     layout, address p + p/4, under which the lanes' stride-4 reads hit 32
-//     distinct banks for any start; every record of the bin is then applied
-//     with 5 shared reads per row per lane (both time taps of 4 ticks), the
-//     read offsets being immediates selected by the record's (p mod 4).
+//     (read one bin ahead into registers), interleaved so that each position
+//     holds the four corner values as one 16-byte quad, with zero quads beyond
+//     both ends of the row.  A record then costs a lane one 16-byte shared
+//     read and a 4-term dot product per tick for v(j); v(j - 1) is the
+//     neighbouring lane's v(j) (warp shuffle).  Consecutive lanes read
+//     consecutive quads: no bank conflicts.
 // A pixel's records fall on ~1000 of the 2025 bins, ~7 records per bin, so the
 // table is read from L2 once per (pixel, bin) instead of once per record.
 // Summation order is fixed (chunks in point order, bins increasing, records
@@ -33,15 +38,17 @@
 namespace larsim {
 
 namespace {
-constexpr int kThreads = 512;
+constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kTPL = 4;                         // consecutive ticks per lane
-constexpr int kPass = kThreads * kTPL;          // ticks per pass
+constexpr int kTPL = 4;                         // consecutive ticks per lane and block
+constexpr int kHalf = 32 * kTPL;                // ticks per block
+constexpr int kPass = 2 * kThreads * kTPL;      // ticks per pass (two blocks per warp)
 constexpr int kRecCap = 8192;                   // records per chunk (per-CTA scratch)
 constexpr int kMaxBins = 2048;                  // nb * nb <= kMaxBins
 constexpr int kMaxRow = 2048;                   // staged row length (>= nt rounded to 4)
-constexpr int kRowPad = kMaxRow + kMaxRow / 4;  // padded row: position p at p + p / 4
-constexpr int kF4PerRowThread = 4;              // 128 threads x 4 float4 = 512 float4 = kMaxRow / 4
+constexpr int kEdge = kHalf + 8;                // zero quads before position 0 and after L - 1
+constexpr int kQuads = kMaxRow + 2 * kEdge;     // staged quads (position p at p + kEdge)
+constexpr int kPosPerThread = kMaxRow / kThreads;   // positions staged per thread
 
 struct __align__(16) Rec {
     int A, b0;
@@ -66,11 +73,11 @@ struct CurArgs {
 };
 
 struct Smem {
-    float rows[4][kRowPad];
-    int hist[kMaxBins];
-    int cur[kMaxBins];
-    int glist[kMaxBins];
-    unsigned short rbin[kRecCap];
+    float4 quad[kQuads];                        // (R00, R10, R01, R11) at each table position
+    int hist[kMaxBins];                         // bin counts, then scatter cursors
+    unsigned short glist[kMaxBins];             // bins present, increasing
+    unsigned short gstart[kMaxBins + 1];        // start of each present bin in bin order
+    unsigned short rbin[kRecCap];               // bin of record i, then its destination
     int warp_n[kWarps];
     int scan_tmp[kWarps + 1];
     int n_groups;
@@ -107,64 +114,72 @@ __device__ __forceinline__ int block_scan(int v, Smem *s, int *tot)
     return r;
 }
 
-// Rows are staged by 128 threads each: thread t handles row t >> 7 and the
-// float4 indices (t & 127) + 128 i.  Corners outside the table read row b0
+// Table row of corner c of bin b0; corners outside the table read row b0
 // (their weight is zero).  b0 / nb is formed in FP32: exact, since
 // (b0 + 1/2) / nb stays >= 1/(2 nb) away from an integer.
-__device__ __forceinline__ void load_rows(const CurArgs &a, int b0, float4 (&r)[kF4PerRowThread])
+__device__ __forceinline__ const float *corner_row(const CurArgs &a, int b0, int c)
 {
-    const int c = threadIdx.x >> 7, q = threadIdx.x & 127;
     const int bx = (int)(((float)b0 + 0.5f) * a.inv_nb), by = b0 - bx * a.nb;
     const int dx = c & 1, dy = c >> 1;
     const int row = (bx + dx < a.nb && by + dy < a.nb) ? b0 + dx * a.nb + dy : b0;
-    const float4 *src = reinterpret_cast<const float4 *>(a.lut + (size_t)row * a.ld);
-    const int n4 = a.lp >> 2;
-#pragma unroll
-    for (int i = 0; i < kF4PerRowThread; ++i) {
-        const int qi = q + 128 * i;
-        if (qi < n4) r[i] = __ldg(src + qi);
-    }
+    return a.lut + (size_t)row * a.ld;
 }
 
-__device__ __forceinline__ void store_rows(const CurArgs &a, Smem *s, const float4 (&r)[kF4PerRowThread])
+// Thread t stages positions t + 256 i (i < 8) of the four rows: coalesced
+// 4-byte global reads into registers, one bin ahead.
+struct RowRegs {
+    float v[4][kPosPerThread];
+};
+
+__device__ __forceinline__ void load_rows(const CurArgs &a, int b0, RowRegs &r)
 {
-    const int c = threadIdx.x >> 7, q = threadIdx.x & 127;
-    const int n4 = a.lp >> 2;
-    float *dst = s->rows[c];
 #pragma unroll
-    for (int i = 0; i < kF4PerRowThread; ++i) {
-        const int qi = q + 128 * i;
-        if (qi < n4) {
-            const int j = 4 * qi;               // positions j..j+3 live at 5 qi .. 5 qi + 3
-            float *d = dst + 5 * qi;
-            d[0] = (j + 0 < a.nt) ? r[i].x : 0.f;
-            d[1] = (j + 1 < a.nt) ? r[i].y : 0.f;
-            d[2] = (j + 2 < a.nt) ? r[i].z : 0.f;
-            d[3] = (j + 3 < a.nt) ? r[i].w : 0.f;
+    for (int c = 0; c < 4; ++c) {
+        const float *row = corner_row(a, b0, c);
+#pragma unroll
+        for (int i = 0; i < kPosPerThread; ++i) {
+            const int j = threadIdx.x + kThreads * i;
+            r.v[c][i] = (j < a.nt) ? __ldg(row + j) : 0.f;
         }
     }
 }
 
-// v at padded address `ad` of the four staged rows.
-__device__ __forceinline__ float vrow(const Smem *s, int ad, const float4 &w)
+__device__ __forceinline__ void store_rows(Smem *s, const RowRegs &r)
 {
-    return w.x * s->rows[0][ad] + w.y * s->rows[1][ad] + w.z * s->rows[2][ad] + w.w * s->rows[3][ad];
+#pragma unroll
+    for (int i = 0; i < kPosPerThread; ++i)
+        s->quad[threadIdx.x + kThreads * i + kEdge] = make_float4(r.v[0][i], r.v[1][i], r.v[2][i], r.v[3][i]);
 }
 
-// One record, all positions of the warp inside the row: positions p0 + m,
-// m = 0..4, with p0 = 4 q + R live at 5 q + R + m + ((R + m) >> 2); R is the
-// same for every lane of the CTA, so each case uses immediate offsets only.
-template <int R>
-__device__ __forceinline__ void apply_fast(const Smem *s, int ad5q, const float4 &w, float f, float (&acc)[kTPL])
+__device__ __forceinline__ float dot4(const float4 &w, const float4 &q)
 {
-    float v[kTPL + 1];
-#pragma unroll
-    for (int m = 0; m <= kTPL; ++m) v[m] = vrow(s, ad5q + R + m + ((R + m) >> 2), w);
-#pragma unroll
-    for (int i = 0; i < kTPL; ++i) acc[i] += (1.f - f) * v[i + 1] + f * v[i];
+    return w.x * q.x + w.y * q.y + w.z * q.z + w.w * q.w;
 }
 
-__global__ void __launch_bounds__(kThreads, 2) k_induced_current(CurArgs a)
+// One record on one block of a warp.  p1 is the position of v(j) at the
+// block's first tick; lane l at iteration i handles tick 32 i + l, reading
+// v(j) at p1 + 32 i + l and taking v(j - 1) from lane l - 1 (lane 0: from
+// lane 31 of the previous iteration, or read directly at i = 0).
+__device__ __forceinline__ void apply_block(const Smem *s, int p1, int L, int lane, const float4 &w, float f,
+                                            float (&acc)[kTPL])
+{
+    if (p1 + kHalf - 1 < 0 || p1 - 1 > L - 1) return;     // block outside the row
+    const float4 *q = s->quad + kEdge + p1 + lane;
+    float carry = 0.f;
+    if (lane == 0) carry = dot4(w, q[-1]);
+    const float g = 1.f - f;
+#pragma unroll
+    for (int i = 0; i < kTPL; ++i) {
+        const float v = dot4(w, q[32 * i]);
+        float vm = __shfl_up_sync(0xffffffffu, v, 1);
+        if (lane == 0) vm = carry;
+        carry = __shfl_sync(0xffffffffu, v, 31);
+        acc[i] = fmaf(g, v, acc[i]);
+        acc[i] = fmaf(f, vm, acc[i]);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a)
 {
     if (a.counts[3] != 0) return;
     const int64_t npix = a.counts[1];
@@ -179,7 +194,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_induced_current(CurArgs a)
     const int npx = a.g.npx_x * a.g.npx_y;
     Rec *recs = a.recs + (size_t)blockIdx.x * kRecCap;
     Rec *sorted = a.sorted + (size_t)blockIdx.x * kRecCap;
-    const int lane_tick = warp * (32 * kTPL) + lane * kTPL;       // first tick of this lane in a pass
+    for (int i = tid; i < kQuads; i += kThreads) s->quad[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int blo_tick = kHalf * warp;                            // first tick of my low block
+    const int bhi_tick = kPass - kHalf * (warp + 1);              // first tick of my high block
 
     for (int64_t pi = blockIdx.x; pi < npix; pi += gridDim.x) {
         const int32_t pid = a.active[pi];
@@ -188,9 +205,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_induced_current(CurArgs a)
         const int iy = rem / a.g.npx_x, ix = rem - iy * a.g.npx_x;
         const int e0 = a.off[pi], e1 = a.off[pi + 1];
         for (int k0 = 0; k0 < T; k0 += kPass) {
-            float acc[kTPL];
+            float acc_lo[kTPL], acc_hi[kTPL];
 #pragma unroll
-            for (int i = 0; i < kTPL; ++i) acc[i] = 0.f;
+            for (int i = 0; i < kTPL; ++i) acc_lo[i] = acc_hi[i] = 0.f;
             int e = e0, base = 0;                                     // generation cursor
             while (e < e1) {
                 // ---- 1. records of this chunk -------------------------------------
@@ -265,10 +282,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_induced_current(CurArgs a)
                 if (nrec == 0) continue;
                 // ---- 2. bin offsets, bin list, stable move to bin order -----------
                 {
-                    int v[4], fl[4], sv = 0, sf = 0;
+                    constexpr int kB = kMaxBins / kThreads;
+                    int v[kB], fl[kB], sv = 0, sf = 0;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int b = tid * 4 + i;
+                    for (int i = 0; i < kB; ++i) {
+                        const int b = tid * kB + i;
                         v[i] = (b < nb2) ? s->hist[b] : 0;
                         fl[i] = v[i] > 0 ? 1 : 0;
                         sv += v[i];
@@ -278,16 +296,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_induced_current(CurArgs a)
                     int pv = block_scan(sv, s, &tv);
                     int pf = block_scan(sf, s, &tf);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int b = tid * 4 + i;
+                    for (int i = 0; i < kB; ++i) {
+                        const int b = tid * kB + i;
                         if (b < nb2) {
-                            s->cur[b] = pv;
-                            if (fl[i]) s->glist[pf] = b;
+                            s->hist[b] = pv;             // scatter cursor
+                            if (fl[i]) {
+                                s->glist[pf] = (unsigned short)b;
+                                s->gstart[pf] = (unsigned short)pv;
+                            }
                         }
                         pv += v[i];
                         pf += fl[i];
                     }
-                    if (tid == 0) s->n_groups = tf;
+                    if (tid == 0) {
+                        s->n_groups = tf;
+                        s->gstart[tf] = (unsigned short)tv;
+                    }
                 }
                 __syncthreads();
                 if (warp == 0) {
@@ -298,10 +322,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_induced_current(CurArgs a)
                         const int bin = v ? (int)s->rbin[i] : -1 - lane;
                         const unsigned peers = __match_any_sync(0xffffffffu, bin);
                         const int rank = __popc(peers & ((1u << lane) - 1u));
-                        const int pos = v ? s->cur[bin] : 0;
+                        const int pos = v ? s->hist[bin] : 0;
                         __syncwarp();
                         if (v) {
-                            if (lane == __ffs(peers) - 1) s->cur[bin] = pos + __popc(peers);
+                            if (lane == __ffs(peers) - 1) s->hist[bin] = pos + __popc(peers);
                             s->rbin[i] = (unsigned short)(pos + rank);
                         }
                         __syncwarp();
@@ -310,60 +334,36 @@ __global__ void __launch_bounds__(kThreads, 2) k_induced_current(CurArgs a)
                 __syncthreads();
                 for (int i = tid; i < nrec; i += kThreads) sorted[s->rbin[i]] = recs[i];
                 __syncthreads();
-                // cur[b] is now the end offset of bin b; its start is end - hist[b]
                 // ---- 3. per bin: stage rows, apply records ------------------------
                 const int ng = s->n_groups;
-                const int Pbase = k0 + L - 2;            // position of v(j-1) at tick k0 is Pbase - A
-                float4 nxt[kF4PerRowThread];
+                const int Pbase = k0 + L - 1;            // position of v(j) at tick k0 is Pbase - A
+                RowRegs nxt;
                 load_rows(a, s->glist[0], nxt);
                 for (int g = 0; g < ng; ++g) {
-                    const int b0 = s->glist[g];
-                    const int gend = s->cur[b0], gbeg = gend - s->hist[b0];
+                    const int gbeg = s->gstart[g], gend = s->gstart[g + 1];
                     __syncthreads();                     // previous bin's rows no longer read
-                    store_rows(a, s, nxt);
+                    store_rows(s, nxt);
                     if (g + 1 < ng) load_rows(a, s->glist[g + 1], nxt);
                     __syncthreads();
                     Rec rn = sorted[gbeg];
                     for (int ri = gbeg; ri < gend; ++ri) {
                         const Rec rc = rn;
                         if (ri + 1 < gend) rn = sorted[ri + 1];         // prefetch the next record
-                        const int wlo = Pbase - rc.A + warp * (32 * kTPL);   // warp's positions [wlo, wlo + 128]
-                        if (wlo + 32 * kTPL < 0 || wlo >= L) continue;
-                        const float f = rc.f;
-                        const int p0 = wlo + lane * kTPL;
-                        if (wlo >= 0 && wlo + 32 * kTPL < L) {
-                            const int ad5q = 5 * (p0 >> 2);
-                            switch (p0 & 3) {
-                            case 0: apply_fast<0>(s, ad5q, rc.w, f, acc); break;
-                            case 1: apply_fast<1>(s, ad5q, rc.w, f, acc); break;
-                            case 2: apply_fast<2>(s, ad5q, rc.w, f, acc); break;
-                            default: apply_fast<3>(s, ad5q, rc.w, f, acc); break;
-                            }
-                        } else {
-                            float v[kTPL + 1];
-#pragma unroll
-                            for (int m2 = 0; m2 <= kTPL; ++m2) {
-                                const int p = p0 + m2;
-                                const bool in = (unsigned)p < (unsigned)L;
-                                const int pc = in ? p : 0;
-                                const float t = vrow(s, pc + (pc >> 2), rc.w);
-                                v[m2] = in ? t : 0.f;
-                            }
-#pragma unroll
-                            for (int i = 0; i < kTPL; ++i) acc[i] += (1.f - f) * v[i + 1] + f * v[i];
-                        }
+                        const int P = Pbase - rc.A;
+                        apply_block(s, P + blo_tick, L, lane, rc.w, rc.f, acc_lo);
+                        apply_block(s, P + bhi_tick, L, lane, rc.w, rc.f, acc_hi);
                     }
                 }
                 __syncthreads();
             }
-            const int kw = k0 + lane_tick;
             float *out = a.current + (size_t)pi * T;
-            if (kw + kTPL <= T && (((size_t)pi * T + kw) & 3) == 0) {
-                *reinterpret_cast<float4 *>(out + kw) = make_float4(acc[0], acc[1], acc[2], acc[3]);
-            } else {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int kb = k0 + (h ? bhi_tick : blo_tick) + lane;
+                const float *ac = h ? acc_hi : acc_lo;
 #pragma unroll
                 for (int i = 0; i < kTPL; ++i)
-                    if (kw + i < T) out[kw + i] = acc[i];
+                    if (kb + 32 * i < T) out[kb + 32 * i] = ac[i];
             }
         }
     }
@@ -374,7 +374,7 @@ int grid_for(int64_t pix_cap)
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int64_t g = (int64_t)sms * 2;
+    int64_t g = (int64_t)sms * 3;
     if (g > pix_cap) g = pix_cap;
     return (int)(g < 1 ? 1 : g);
 }
