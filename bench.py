@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["module", "tile", "spill"], default="module")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
 
@@ -203,6 +204,49 @@ def run_reference(args):
 
 # --------------------------------------------------------------------- ours ---
 
+def batched_vs_plain(cfg, lut, dev, n_events=32, lo=1.0e3, hi=1.0e4, reps=2):
+    """The same events run one sim_event call each (plain) and as one batch;
+    segments/s of both and the per-event latencies of the plain form (each
+    event's own device time) against the batch's completion time."""
+    import torch
+    from paper_2212_09807_gb300 import sim
+    evs = events.batch_events(cfg, params.BASE["seed"] + 4, n_events, lo, hi)
+    sizes = [len(e["x0"]) for e in evs]
+    total, big = sum(sizes), max(sizes)
+    ids = list(range(1000, 1000 + n_events))
+    plain = sim.EventRunner(cfg, lut, params.LUT["nt"], params.LUT["bins_per_pitch"], big, 40 * big, 4 * big,
+                            4 * big, device=dev)
+    batch_run = sim.EventRunner(cfg, lut, params.LUT["nt"], params.LUT["bins_per_pitch"], total, 40 * total,
+                                4 * total, 4 * total, device=dev, max_events=n_events)
+    singles = [sim.Segments.from_numpy(e, i, dev) for e, i in zip(evs, ids)]
+    batch = sim.Segments.batch_from_numpy(evs, ids, dev)
+    best_plain, best_batch, lat = None, None, None
+    for _ in range(reps):
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(n_events + 1)]
+        marks[0].record()
+        for k, sg in enumerate(singles):
+            plain.enqueue(sg)
+            marks[k + 1].record()
+        torch.cuda.synchronize()
+        t_plain = marks[0].elapsed_time(marks[-1])
+        per = [marks[k].elapsed_time(marks[k + 1]) for k in range(n_events)]
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record()
+        batch_run.enqueue(batch)
+        b1.record()
+        torch.cuda.synchronize()
+        t_batch = b0.elapsed_time(b1)
+        if best_plain is None or t_plain < best_plain:
+            best_plain, lat = t_plain, per
+        best_batch = t_batch if best_batch is None else min(best_batch, t_batch)
+    assert batch_run.counts()[3] == 0
+    return {"events": n_events, "segments": total, "sizes": f"log-uniform [{lo:.0f}, {hi:.0f}] segments",
+            "plain_segments_per_s": total / (best_plain / 1e3), "batched_segments_per_s": total / (best_batch / 1e3),
+            "plain_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "batched_completion_ms": best_batch}
+
+
+
 def run_ours(args):
     import torch
     from paper_2212_09807_gb300 import sim
@@ -259,7 +303,7 @@ def run_ours(args):
         sim.sim_induced_current(run.cfg, segs, dr, run.resp, active, pix_seg_off, pix_seg_ids, counts, current,
                                 run.ws)
         evs[3].record()
-        sim.sim_electronics(run.cfg, segs.event_id, active, current, counts, run.hits, run.ws)
+        sim.sim_electronics(run.cfg, segs, active, current, counts, run.hits, run.ws)
         evs[4].record()
 
     mk = lambda: [torch.cuda.Event(enable_timing=True) for _ in range(5)]  # noqa: E731
@@ -335,6 +379,8 @@ def run_ours(args):
     e2e = {"value": world * S * args.steps / e2e_s, "unit": "segments/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
 
+    batched = batched_vs_plain(cfg, lut, dev) if not args.no_batched else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         lut_or = lut_pad[..., :L].astype(np.float64)
@@ -355,7 +401,7 @@ def run_ours(args):
             "step_breakdown_ms": {"quench_drift": float(per[:, 0].mean()), "pixel_map": float(per[:, 1].mean()),
                                   "induced_current": float(per[:, 2].mean()),
                                   "electronics": float(per[:, 3].mean())},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,
             "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clocks,
         }))
     if pg:

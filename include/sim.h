@@ -78,14 +78,25 @@ typedef struct sim_config {
     int32_t reserved;
 } sim_config;
 
-/* Energy-deposit segments S_i = (r_s, r_e, E) of one event (Sec. 2), as
- * structure-of-arrays FP32 device columns of length n: start (x0,y0,z0,t0),
- * end (x1,y1,z1,t1), deposited energy dE.  Segment index i (0..n-1) keys the
- * diffusion random numbers together with event_id. */
+/* Energy-deposit segments S_i = (r_s, r_e, E) (Sec. 2), as structure-of-arrays
+ * FP32 device columns of length n: start (x0,y0,z0,t0), end (x1,y1,z1,t1),
+ * deposited energy dE.
+ *  - n_events == 0: one event with id event_id; segment index i keys the
+ *    diffusion random numbers together with event_id.
+ *  - n_events >= 1 (a batch): event slot e owns segments
+ *    [event_offsets[e], event_offsets[e+1]) and has id event_ids[e]
+ *    (device arrays of n_events + 1 and n_events entries, offsets increasing,
+ *    event_offsets[0] = 0, event_offsets[n_events] = n); its random numbers use
+ *    the event-local segment index, so every event's results are identical alone
+ *    and in a batch.  Pixel ids then refer to a virtual detector with one copy of
+ *    the geometry per slot: virtual id = slot * n_detector_pixels + pixel id. */
 typedef struct sim_segments {
     const float *x0, *y0, *z0, *t0, *x1, *y1, *z1, *t1, *dE;
     int64_t n;
     uint64_t event_id;
+    const int64_t *event_offsets;
+    const uint64_t *event_ids;
+    int64_t n_events;
 } sim_segments;
 
 /* Field-response table I_pixel[x, y, t] (Sec. 3.3.1): FP32 device array
@@ -133,14 +144,15 @@ int sim_last_cuda_error(void);
  * sizeof(sim_drifted), sizeof(sim_hits) to sizes[0..4] (host). */
 void sim_abi_sizes(int64_t sizes[5]);
 
-/* Workspace bytes sim_event needs for up to max_segments segments, max_pairs
- * (segment, pixel) pairs and max_pixels active pixels; the same size serves
- * sim_pixel_map and sim_electronics, which use only the scratch region after
- * the counts block.  Writes *bytes (host).  The first 256 bytes of any
- * workspace hold the counts block: int64 [0] pairs, [1] active pixels,
- * [2] hits, [3] status bits (SIM_STATUS_*). */
-int sim_workspace_size(const sim_config *cfg, int64_t max_segments, int64_t max_pairs,
-                       int64_t max_pixels, size_t *bytes);
+/* Workspace bytes sim_event needs for batches of up to max_events events
+ * (0 or 1 for a single event), max_segments segments, max_pairs (segment,
+ * pixel) pairs and max_pixels active pixels, on the current device; the same
+ * size serves sim_pixel_map, sim_induced_current and sim_electronics, which use
+ * only the scratch region after the counts block.  Writes *bytes (host).  The
+ * first 256 bytes of any workspace hold the counts block: int64 [0] pairs,
+ * [1] active pixels, [2] hits, [3] status bits (SIM_STATUS_*). */
+int sim_workspace_size(const sim_config *cfg, int64_t max_events, int64_t max_segments,
+                       int64_t max_pairs, int64_t max_pixels, size_t *bytes);
 
 /* Device address of the counts block inside a workspace. */
 const int64_t *sim_workspace_counts(const void *ws);
@@ -165,7 +177,7 @@ int sim_quench_drift(const sim_config *cfg, const sim_segments *seg, const sim_d
  *                                                segment indices increasing)
  * Counts go to the workspace counts block ([0] pairs, [1] pixels, [3] status);
  * on overflow the required sizes are stored and the CSR fill is skipped.
- * Workspace: sim_workspace_size(cfg, n, pair_cap, pix_cap). */
+ * Workspace: sim_workspace_size(cfg, n_events, n, pair_cap, pix_cap). */
 int sim_pixel_map(const sim_config *cfg, const sim_segments *seg, const sim_drifted *dr,
                   const sim_response *resp, int32_t *seg_pix_off, int32_t *seg_pix_ids, int64_t pair_cap,
                   int32_t *active_pixels, int32_t *pix_seg_off, int32_t *pix_seg_ids,
@@ -180,7 +192,7 @@ int sim_pixel_map(const sim_config *cfg, const sim_segments *seg, const sim_drif
  * counts: device int64[4] counts block as written by sim_pixel_map ([1] =
  * active pixels, [3] = status); nothing is computed when the status word is
  * nonzero or counts[1] > pix_cap.  Workspace (scratch from byte 256 on):
- * sim_workspace_size(cfg, 0, 0, pix_cap) bytes, sized for the current device
+ * sim_workspace_size(cfg, 0, 0, 0, pix_cap) bytes, sized for the current device
  * (a per-CTA record buffer).  Table limits: nb * nb <= 2048, nt <= 2048. */
 int sim_induced_current(const sim_config *cfg, const sim_segments *seg, const sim_drifted *dr,
                         const sim_response *resp, const int32_t *active_pixels,
@@ -193,14 +205,17 @@ int sim_induced_current(const sim_config *cfg, const sim_segments *seg, const si
  * reset with pedestal noise (Philox counters keyed by pixel id and tick).
  * Reads counts[1] (active pixels) and counts[3] (status; nothing is done when
  * nonzero); writes the hit list `out`, *out->n_out and counts[2] (hits).
- * Workspace (scratch, from byte 256 on): sim_workspace_size(cfg, 0, 0, pix_cap). */
-int sim_electronics(const sim_config *cfg, uint64_t event_id, const int32_t *active_pixels,
+ * `events` supplies the event ids only (event_id, or event_ids/n_events of a
+ * batch; its segment columns are not read).
+ * Workspace (scratch, from byte 256 on): sim_workspace_size(cfg, 0, 0, 0, pix_cap). */
+int sim_electronics(const sim_config *cfg, const sim_segments *events, const int32_t *active_pixels,
                     const float *current, int64_t *counts, int64_t pix_cap,
                     const sim_hits *out, void *ws, size_t ws_bytes, void *stream);
 
-/* Steps 1-5 for one event, enqueued on one stream with no host
- * synchronisation; every intermediate lives in the workspace, sized by
- * sim_workspace_size(cfg, seg->n, max_pairs, max_pixels). */
+/* Steps 1-5 for one event or a batch of events (see sim_segments), enqueued
+ * on one stream with no host synchronisation; every intermediate lives in the
+ * workspace, sized by sim_workspace_size(cfg, seg->n_events, seg->n, max_pairs,
+ * max_pixels). */
 int sim_event(const sim_config *cfg, const sim_segments *seg, const sim_response *resp,
               int64_t max_pairs, int64_t max_pixels, const sim_hits *out, void *ws,
               size_t ws_bytes, void *stream);
@@ -239,8 +254,9 @@ typedef struct sim_event_view {
     int64_t *counts;
 } sim_event_view;
 
-int sim_event_view_of(const sim_config *cfg, int64_t n_segments, int64_t max_pairs,
-                      int64_t max_pixels, void *ws, size_t ws_bytes, sim_event_view *view);
+int sim_event_view_of(const sim_config *cfg, int64_t max_events, int64_t n_segments,
+                      int64_t max_pairs, int64_t max_pixels, void *ws, size_t ws_bytes,
+                      sim_event_view *view);
 
 #ifdef __cplusplus
 }

@@ -34,9 +34,18 @@ bool cfg_ok(const sim_config *c)
     return true;
 }
 
+bool events_ok(const sim_config *c, const sim_segments *s)
+{
+    if (!s || s->n_events < 0) return false;
+    if (s->n_events > 0 && (!s->event_offsets || !s->event_ids)) return false;
+    const int64_t slots = s->n_events > 0 ? s->n_events : 1;
+    return detector_pixels(geo_of(*c)) * slots < ((int64_t)1 << 31);
+}
+
 bool seg_ok(const sim_segments *s)
 {
     if (!s || s->n < 0 || s->n >= ((int64_t)1 << 31)) return false;
+    if (s->n_events < 0 || (s->n_events > 0 && (!s->event_offsets || !s->event_ids))) return false;
     if (s->n == 0) return true;
     return s->x0 && s->y0 && s->z0 && s->t0 && s->x1 && s->y1 && s->z1 && s->t1 && s->dE;
 }
@@ -66,7 +75,7 @@ struct Layout {
     size_t seg_off, seg_ids, active, pix_off, pix_ids, current, total;
 };
 
-Layout layout(const sim_config &c, int64_t n, int64_t pairs, int64_t pixels)
+Layout layout(const sim_config &c, int64_t slots, int64_t n, int64_t pairs, int64_t pixels)
 {
     Layout L;
     size_t o = 0;
@@ -76,7 +85,7 @@ Layout layout(const sim_config &c, int64_t n, int64_t pairs, int64_t pixels)
         return at;
     };
     L.counts = take(256);
-    size_t sc = map_scratch_bytes(c, n);
+    size_t sc = map_scratch_bytes(c, n, slots);
     const size_t es = elec_scratch_bytes(c, pixels), cs = current_scratch_bytes(pixels);
     if (es > sc) sc = es;
     if (cs > sc) sc = cs;
@@ -122,6 +131,7 @@ namespace larsim {
 // argument checks and error recording shared with pixel_map_static.cu
 bool abi_config_ok(const sim_config *c) { return cfg_ok(c); }
 bool abi_segments_ok(const sim_segments *s) { return seg_ok(s); }
+bool abi_events_ok(const sim_config *c, const sim_segments *s) { return events_ok(c, s); }
 bool abi_drifted_ok(const sim_drifted *d) { return drifted_ok(d); }
 int abi_cuda_fail(cudaError_t e) { return cuda_fail(e); }
 }  // namespace larsim
@@ -151,11 +161,14 @@ void sim_abi_sizes(int64_t sizes[5])
     sizes[4] = sizeof(sim_hits);
 }
 
-int sim_workspace_size(const sim_config *cfg, int64_t max_segments, int64_t max_pairs, int64_t max_pixels,
-                       size_t *bytes)
+int sim_workspace_size(const sim_config *cfg, int64_t max_events, int64_t max_segments, int64_t max_pairs,
+                       int64_t max_pixels, size_t *bytes)
 {
-    if (!cfg_ok(cfg) || !bytes || max_segments < 0 || max_pairs < 0 || max_pixels < 0) return SIM_ERR_INVALID_ARG;
-    *bytes = layout(*cfg, max_segments, max_pairs, max_pixels).total;
+    if (!cfg_ok(cfg) || !bytes || max_events < 0 || max_segments < 0 || max_pairs < 0 || max_pixels < 0)
+        return SIM_ERR_INVALID_ARG;
+    const int64_t slots = max_events > 0 ? max_events : 1;
+    if (detector_pixels(geo_of(*cfg)) * slots >= ((int64_t)1 << 31)) return SIM_ERR_INVALID_ARG;
+    *bytes = layout(*cfg, slots, max_segments, max_pairs, max_pixels).total;
     return SIM_OK;
 }
 
@@ -173,13 +186,14 @@ int sim_pixel_map(const sim_config *cfg, const sim_segments *seg, const sim_drif
                   int32_t *active_pixels, int32_t *pix_seg_off, int32_t *pix_seg_ids, int64_t pix_cap,
                   void *ws, size_t ws_bytes, void *stream)
 {
-    if (!cfg_ok(cfg) || !seg_ok(seg) || !resp_ok(resp, false) || pair_cap < 0 || pix_cap < 0 || !ws)
+    if (!cfg_ok(cfg) || !seg_ok(seg) || !events_ok(cfg, seg) || !resp_ok(resp, false) || pair_cap < 0 ||
+        pix_cap < 0 || !ws)
         return SIM_ERR_INVALID_ARG;
     if (seg->n > 0 && (!drifted_ok(dr) || !seg_pix_off)) return SIM_ERR_INVALID_ARG;
     if (!seg_pix_off || (pair_cap > 0 && (!seg_pix_ids || !pix_seg_ids)) ||
         (pix_cap > 0 && (!active_pixels || !pix_seg_off)) || (pix_cap == 0 && !pix_seg_off))
         return SIM_ERR_INVALID_ARG;
-    if (ws_bytes < 256 + map_scratch_bytes(*cfg, seg->n)) return SIM_ERR_CAPACITY;
+    if (ws_bytes < 256 + map_scratch_bytes(*cfg, seg->n, n_slots(events_of(*seg)))) return SIM_ERR_CAPACITY;
     char *w = reinterpret_cast<char *>(ws);
     const sim_drifted d0 = dr ? *dr : sim_drifted{};
     const cudaError_t e = launch_pixel_map(*cfg, *seg, d0, resp->nb, resp->bins_per_pitch, seg_pix_off,
@@ -194,7 +208,8 @@ int sim_induced_current(const sim_config *cfg, const sim_segments *seg, const si
                         const int32_t *pix_seg_ids, const int64_t *counts, int64_t pix_cap, float *current,
                         void *ws, size_t ws_bytes, void *stream)
 {
-    if (!cfg_ok(cfg) || !seg_ok(seg) || !resp_ok(resp, true) || !counts || pix_cap < 0 || !ws)
+    if (!cfg_ok(cfg) || !seg_ok(seg) || !events_ok(cfg, seg) || !resp_ok(resp, true) || !counts || pix_cap < 0 ||
+        !ws)
         return SIM_ERR_INVALID_ARG;
     if (pix_cap > 0 && (!active_pixels || !pix_seg_off || !pix_seg_ids || !current)) return SIM_ERR_INVALID_ARG;
     if (pix_cap > 0 && seg->n > 0 && !drifted_ok(dr)) return SIM_ERR_INVALID_ARG;
@@ -207,24 +222,25 @@ int sim_induced_current(const sim_config *cfg, const sim_segments *seg, const si
     return e == cudaSuccess ? SIM_OK : cuda_fail(e);
 }
 
-int sim_electronics(const sim_config *cfg, uint64_t event_id, const int32_t *active_pixels, const float *current,
-                    int64_t *counts, int64_t pix_cap, const sim_hits *out, void *ws, size_t ws_bytes,
-                    void *stream)
+int sim_electronics(const sim_config *cfg, const sim_segments *events, const int32_t *active_pixels,
+                    const float *current, int64_t *counts, int64_t pix_cap, const sim_hits *out, void *ws,
+                    size_t ws_bytes, void *stream)
 {
-    if (!cfg_ok(cfg) || !counts || pix_cap < 0 || !hits_ok(out) || !ws) return SIM_ERR_INVALID_ARG;
+    if (!cfg_ok(cfg) || !events_ok(cfg, events) || !counts || pix_cap < 0 || !hits_ok(out) || !ws)
+        return SIM_ERR_INVALID_ARG;
     if (pix_cap > 0 && (!active_pixels || !current)) return SIM_ERR_INVALID_ARG;
     if (ws_bytes < 256 + elec_scratch_bytes(*cfg, pix_cap)) return SIM_ERR_CAPACITY;
-    const cudaError_t e = launch_electronics(*cfg, event_id, active_pixels, current, counts, pix_cap, *out,
+    const cudaError_t e = launch_electronics(*cfg, events_of(*events), active_pixels, current, counts, pix_cap, *out,
                                              reinterpret_cast<char *>(ws) + 256, (cudaStream_t)stream);
     return e == cudaSuccess ? SIM_OK : cuda_fail(e);
 }
 
-int sim_event_view_of(const sim_config *cfg, int64_t n_segments, int64_t max_pairs, int64_t max_pixels, void *ws,
-                      size_t ws_bytes, sim_event_view *view)
+int sim_event_view_of(const sim_config *cfg, int64_t max_events, int64_t n_segments, int64_t max_pairs,
+                      int64_t max_pixels, void *ws, size_t ws_bytes, sim_event_view *view)
 {
-    if (!cfg_ok(cfg) || n_segments < 0 || max_pairs < 0 || max_pixels < 0 || !ws || !view)
+    if (!cfg_ok(cfg) || max_events < 0 || n_segments < 0 || max_pairs < 0 || max_pixels < 0 || !ws || !view)
         return SIM_ERR_INVALID_ARG;
-    const Layout L = layout(*cfg, n_segments, max_pairs, max_pixels);
+    const Layout L = layout(*cfg, max_events > 0 ? max_events : 1, n_segments, max_pairs, max_pixels);
     if (ws_bytes < L.total) return SIM_ERR_CAPACITY;
     fill_view(L, reinterpret_cast<char *>(ws), view);
     return SIM_OK;
@@ -233,10 +249,10 @@ int sim_event_view_of(const sim_config *cfg, int64_t n_segments, int64_t max_pai
 int sim_event(const sim_config *cfg, const sim_segments *seg, const sim_response *resp, int64_t max_pairs,
               int64_t max_pixels, const sim_hits *out, void *ws, size_t ws_bytes, void *stream)
 {
-    if (!cfg_ok(cfg) || !seg_ok(seg) || !resp_ok(resp, true) || max_pairs < 0 || max_pixels < 0 ||
-        !hits_ok(out) || !ws)
+    if (!cfg_ok(cfg) || !seg_ok(seg) || !events_ok(cfg, seg) || !resp_ok(resp, true) || max_pairs < 0 ||
+        max_pixels < 0 || !hits_ok(out) || !ws)
         return SIM_ERR_INVALID_ARG;
-    const Layout L = layout(*cfg, seg->n, max_pairs, max_pixels);
+    const Layout L = layout(*cfg, n_slots(events_of(*seg)), seg->n, max_pairs, max_pixels);
     if (ws_bytes < L.total) return SIM_ERR_CAPACITY;
     char *w = reinterpret_cast<char *>(ws);
     sim_event_view v;
@@ -251,7 +267,7 @@ int sim_event(const sim_config *cfg, const sim_segments *seg, const sim_response
     e = launch_induced_current(*cfg, *seg, v.dr, *resp, v.active_pixels, v.pix_seg_off, v.pix_seg_ids, v.counts,
                                max_pixels, v.current, w + L.scratch, st);
     if (e != cudaSuccess) return cuda_fail(e);
-    e = launch_electronics(*cfg, seg->event_id, v.active_pixels, v.current, v.counts, max_pixels, *out,
+    e = launch_electronics(*cfg, events_of(*seg), v.active_pixels, v.current, v.counts, max_pixels, *out,
                            w + L.scratch, st);
     if (e != cudaSuccess) return cuda_fail(e);
     return SIM_OK;

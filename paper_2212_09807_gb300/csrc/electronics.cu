@@ -35,7 +35,8 @@ __host__ __device__ inline int max_hits_per_pixel(const sim_config &c)
 
 struct ElArgs {
     sim_config c;
-    uint64_t key;
+    EventInfo ev;
+    int64_t det_px;                             // pixels of one detector copy
     const int32_t *active;
     const float *current;
     const int64_t *counts;
@@ -70,7 +71,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_electronics(ElArgs a)
     const int per = c.periodic_reset_ticks;
 
     for (int64_t pi = wg; pi < npix; pi += nw) {
-        const uint32_t pid = (uint32_t)a.active[pi];
+        // virtual pixel -> event slot (Philox key) and detector pixel id (counter)
+        const int32_t vpid = a.active[pi];
+        const int slot = (int)(vpid / a.det_px);
+        const uint32_t pid = (uint32_t)(vpid - slot * a.det_px);
+        const uint64_t key = slot_key(a.c.seed, a.ev, slot);
         const float *I = a.current + (size_t)pi * T;
         HitRec *st = a.stage + (size_t)pi * a.hmax;
         float qoff = 0.f;         // CSA charge before this chunk's first tick
@@ -95,7 +100,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_electronics(ElArgs a)
                     }
                     bool cross = false;
                     if (lane >= pos && lane < lim) {
-                        const float2 n = normals2(a.key, pid, (uint32_t)k, 2u);
+                        const float2 n = normals2(key, pid, (uint32_t)k, 2u);
                         const float v = qoff + sc + c.sigma_unc_e * n.x;
                         const float thr = c.thr_e + c.sigma_disc_e * n.y;
                         cross = v >= thr;
@@ -108,7 +113,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_electronics(ElArgs a)
                         idle = false;
                         pos = cl;
                     } else if (lim < nl) {
-                        const float r = c.sigma_reset_e * normals2(a.key, pid, (uint32_t)(k0 + lim), 4u).x;
+                        const float r = c.sigma_reset_e * normals2(key, pid, (uint32_t)(k0 + lim), 4u).x;
                         const float sprev = __shfl_sync(0xffffffffu, sc, max(lim - 1, 0));
                         qoff = r - (lim > 0 ? sprev : 0.f);
                         per_done = k0 + lim;
@@ -120,12 +125,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_electronics(ElArgs a)
                     if (t_adc < k0 + nl) {
                         const int l = t_adc - k0;
                         const float sl = __shfl_sync(0xffffffffu, sc, l);
-                        const float nu = normals2(a.key, pid, (uint32_t)t_adc, 2u).x;
+                        const float nu = normals2(key, pid, (uint32_t)t_adc, 2u).x;
                         const float v = qoff + sl + c.sigma_unc_e * nu;
                         const float code = fminf(fmaxf(floorf(v / lsb_e), 0.f), adc_max);
                         if (lane == 0 && nh < a.hmax) st[nh] = HitRec{t_cross, t_adc, (int32_t)code, v};
                         ++nh;
-                        const float r = c.sigma_reset_e * normals2(a.key, pid, (uint32_t)t_adc, 3u).x;
+                        const float r = c.sigma_reset_e * normals2(key, pid, (uint32_t)t_adc, 3u).x;
                         qoff = r - sl;
                         last_adc = t_adc;
                         idle = true;
@@ -185,7 +190,7 @@ size_t elec_scratch_bytes(const sim_config &c, int64_t pix_cap)
            align256(sizeof(int32_t) * (size_t)(pix_cap + 1)) + scan_scratch_bytes(pix_cap + 1);
 }
 
-cudaError_t launch_electronics(const sim_config &c, uint64_t event_id, const int32_t *active,
+cudaError_t launch_electronics(const sim_config &c, const EventInfo &ev, const int32_t *active,
                                const float *current, int64_t *counts, int64_t pix_cap,
                                const sim_hits &out, void *scratch, cudaStream_t st)
 {
@@ -208,7 +213,8 @@ cudaError_t launch_electronics(const sim_config &c, uint64_t event_id, const int
     if (e != cudaSuccess) return e;
     ElArgs a;
     a.c = c;
-    a.key = c.seed ^ event_id;
+    a.ev = ev;
+    a.det_px = detector_pixels(geo_of(c));
     a.active = active;
     a.current = current;
     a.counts = counts;

@@ -66,7 +66,8 @@ struct CurArgs {
     const int64_t *counts;
     int64_t pix_cap;
     float *current;
-    uint64_t key;
+    uint64_t seed;
+    EventInfo ev;
     Geo g;
     Rec *recs;                                  // [grid][kRecCap], point order
     Rec *sorted;                                // [grid][kRecCap], bin order
@@ -203,6 +204,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a)
         const int an = pid / npx;
         const int rem = pid - an * npx;
         const int iy = rem / a.g.npx_x, ix = rem - iy * a.g.npx_x;
+        // event of this (virtual) pixel: key and first segment of its slot
+        const int slot = an / a.g.n_anodes;
+        const uint64_t key = slot_key(a.seed, a.ev, slot);
+        const int64_t seg0 = slot_first(a.ev, slot);
         const int e0 = a.off[pi], e1 = a.off[pi + 1];
         for (int k0 = 0; k0 < T; k0 += kPass) {
             float acc_lo[kTPL], acc_hi[kTPL];
@@ -230,7 +235,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a)
                     Rec r;
                     if (idx < total) {
                         const int mu = (M == 1) ? idx : idx / M;
-                        float3 n = normals3(a.key, (uint32_t)sg, (uint32_t)idx, 1u);
+                        float3 n = normals3(key, (uint32_t)(sg - seg0), (uint32_t)idx, 1u);
                         n.x = fminf(fmaxf(n.x, -clip), clip);
                         n.y = fminf(fmaxf(n.y, -clip), clip);
                         n.z = fminf(fmaxf(n.z, -clip), clip);
@@ -411,7 +416,8 @@ cudaError_t launch_induced_current(const sim_config &c, const sim_segments &s, c
     a.counts = counts;
     a.pix_cap = pix_cap;
     a.current = current;
-    a.key = c.seed ^ s.event_id;
+    a.seed = c.seed;
+    a.ev = events_of(s);
     a.g = geo_of(c);
     const int grid = grid_for(pix_cap);
     char *p = reinterpret_cast<char *>(scratch);

@@ -143,15 +143,15 @@ __global__ void __launch_bounds__(256) k_map_sort(const int64_t *counts, const i
 
 }  // namespace
 
-static int64_t n_total_pixels(const sim_config &c)
+// Pixel ids of the (virtual) detector: one copy of the geometry per event slot.
+static int64_t n_total_pixels(const sim_config &c, int64_t slots)
 {
-    const Geo g = geo_of(c);
-    return (int64_t)g.n_anodes * g.npx_x * g.npx_y;
+    return detector_pixels(geo_of(c)) * slots;
 }
 
-size_t map_scratch_bytes(const sim_config &c, int64_t n_seg)
+size_t map_scratch_bytes(const sim_config &c, int64_t n_seg, int64_t slots)
 {
-    const int64_t nt = n_total_pixels(c);
+    const int64_t nt = n_total_pixels(c, slots);
     const int64_t big = nt > n_seg ? nt : n_seg;
     return 2 * align256(sizeof(int32_t) * (size_t)(nt + 1)) + scan_scratch_bytes(big + 1);
 }
@@ -162,7 +162,7 @@ cudaError_t launch_pixel_map(const sim_config &c, const sim_segments &s, const s
                              int32_t *pix_seg_ids, int64_t pix_cap, int64_t *counts, void *scratch,
                              cudaStream_t st)
 {
-    const int64_t nt = n_total_pixels(c);
+    const int64_t nt = n_total_pixels(c, n_slots(events_of(s)));
     char *p = reinterpret_cast<char *>(scratch);
     int32_t *hist = reinterpret_cast<int32_t *>(p);
     p += align256(sizeof(int32_t) * (size_t)(nt + 1));

@@ -23,6 +23,7 @@ namespace larsim {
 // defined in api.cu
 bool abi_config_ok(const sim_config *c);
 bool abi_segments_ok(const sim_segments *s);
+bool abi_events_ok(const sim_config *c, const sim_segments *s);
 bool abi_drifted_ok(const sim_drifted *d);
 int abi_cuda_fail(cudaError_t e);
 }  // namespace larsim
@@ -64,14 +65,15 @@ extern "C" int sim_pixel_map_noalloc(const sim_config *cfg, const sim_segments *
                                      int64_t pair_cap, int32_t *active_pixels, int32_t *pix_seg_off,
                                      int32_t *pix_seg_ids, int64_t pix_cap, int64_t *counts, void *stream)
 {
-    if (!abi_config_ok(cfg) || !abi_segments_ok(seg) || !resp || resp->nb < 1 || resp->bins_per_pitch < 1 ||
+    if (!abi_config_ok(cfg) || !abi_segments_ok(seg) || !abi_events_ok(cfg, seg) || !resp || resp->nb < 1 ||
+        resp->bins_per_pitch < 1 ||
         pair_cap < 0 || pix_cap < 0 || !counts)
         return SIM_ERR_INVALID_ARG;
     if (seg->n > 0 && !abi_drifted_ok(dr)) return SIM_ERR_INVALID_ARG;
     if (!seg_pix_off || (pair_cap > 0 && (!seg_pix_ids || !pix_seg_ids)) || !pix_seg_off ||
         (pix_cap > 0 && !active_pixels))
         return SIM_ERR_INVALID_ARG;
-    if (map_scratch_bytes(*cfg, seg->n) > SIM_NOALLOC_SCRATCH_BYTES) return SIM_ERR_CAPACITY;
+    if (map_scratch_bytes(*cfg, seg->n, n_slots(events_of(*seg))) > SIM_NOALLOC_SCRATCH_BYTES) return SIM_ERR_CAPACITY;
     void *scratch = nullptr;
     const int rc = scratch_for_current_device(&scratch);
     if (rc != SIM_OK) return rc;

@@ -42,7 +42,7 @@ __device__ __forceinline__ Loc locate(const sim_config &c, double x, double y, d
     return L;
 }
 
-__global__ void __launch_bounds__(256) k_quench_drift(sim_config c, sim_segments s, sim_drifted o)
+__global__ void __launch_bounds__(256) k_quench_drift(sim_config c, sim_segments s, sim_drifted o, EventInfo ev)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.n) return;
@@ -97,7 +97,9 @@ __global__ void __launch_bounds__(256) k_quench_drift(sim_config c, sim_segments
     o.t_drift[i] = td;
     o.sigma_T[i] = sT;
     o.sigma_L[i] = sL;
-    o.anode[i] = L.anode;
+    // in a batch, event slot e owns virtual anodes e * n_anodes ..
+    const int slot = slot_of_segment(ev, i);
+    o.anode[i] = slot * (c.n_mod_x * c.n_mod_y * c.n_tpc) + L.anode;
     o.n_samples[i] = N;
 
     // ---- anchor: FP64 start point, FP32 small offsets ----
@@ -138,7 +140,7 @@ cudaError_t launch_quench_drift(const sim_config &c, const sim_segments &s, cons
     if (s.n == 0) return cudaSuccess;
     const int threads = 256;
     const int64_t blocks = (s.n + threads - 1) / threads;
-    k_quench_drift<<<(unsigned)blocks, threads, 0, st>>>(c, s, o);
+    k_quench_drift<<<(unsigned)blocks, threads, 0, st>>>(c, s, o, events_of(s));
     return cudaGetLastError();
 }
 

@@ -102,6 +102,51 @@ __host__ __device__ inline Geo geo_of(const sim_config &c)
     return g;
 }
 
+// Events of a call: one event (n == 0, id `single`) or a batch of n event
+// slots with device offsets [n + 1] and ids [n].  Slot s owns virtual anodes
+// s * n_anodes .. and virtual pixels s * detector_pixels ...
+struct EventInfo {
+    const int64_t *off;
+    const uint64_t *ids;
+    int64_t n;
+    uint64_t single;
+};
+
+inline EventInfo events_of(const sim_segments &s)
+{
+    EventInfo e;
+    e.off = s.event_offsets;
+    e.ids = s.event_ids;
+    e.n = s.n_events;
+    e.single = s.event_id;
+    return e;
+}
+
+inline int64_t n_slots(const EventInfo &e) { return e.n > 0 ? e.n : 1; }
+
+__host__ __device__ inline int64_t detector_pixels(const Geo &g) { return (int64_t)g.n_anodes * g.npx_x * g.npx_y; }
+
+// Philox key of an event slot.
+__device__ __forceinline__ uint64_t slot_key(uint64_t seed, const EventInfo &e, int slot)
+{
+    return seed ^ (e.n > 0 ? e.ids[slot] : e.single);
+}
+
+// First segment index of an event slot (0 for a single event).
+__device__ __forceinline__ int64_t slot_first(const EventInfo &e, int slot) { return e.n > 0 ? e.off[slot] : 0; }
+
+// Slot owning segment i: largest e with off[e] <= i.
+__device__ __forceinline__ int slot_of_segment(const EventInfo &e, int64_t i)
+{
+    if (e.n <= 0) return 0;
+    int lo = 0, hi = (int)e.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (e.off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Map half-width in pitch units: table reach (nb + 1/2) bins plus the clip.
 __device__ __forceinline__ float map_radius_pitch(int nb, int bpp, float clip, float sTp)
 {
@@ -113,7 +158,7 @@ __device__ __forceinline__ float map_radius_pitch(int nb, int bpp, float clip, f
 cudaError_t launch_quench_drift(const sim_config &c, const sim_segments &s, const sim_drifted &o,
                                 cudaStream_t st);
 
-size_t map_scratch_bytes(const sim_config &c, int64_t n_seg);
+size_t map_scratch_bytes(const sim_config &c, int64_t n_seg, int64_t slots);
 cudaError_t launch_pixel_map(const sim_config &c, const sim_segments &s, const sim_drifted &d,
                              int nb, int bins_per_pitch, int32_t *seg_pix_off, int32_t *seg_pix_ids,
                              int64_t pair_cap, int32_t *active, int32_t *pix_seg_off,
@@ -129,7 +174,7 @@ cudaError_t launch_induced_current(const sim_config &c, const sim_segments &s, c
                                    cudaStream_t st);
 
 size_t elec_scratch_bytes(const sim_config &c, int64_t pix_cap);
-cudaError_t launch_electronics(const sim_config &c, uint64_t event_id, const int32_t *active,
+cudaError_t launch_electronics(const sim_config &c, const EventInfo &ev, const int32_t *active,
                                const float *current, int64_t *counts, int64_t pix_cap,
                                const sim_hits &out, void *scratch, cudaStream_t st);
 

@@ -61,7 +61,8 @@ _P = C.c_void_p
 
 class SimSegments(C.Structure):
     _fields_ = [(k, _P) for k in ("x0", "y0", "z0", "t0", "x1", "y1", "z1", "t1", "dE")] + [
-        ("n", C.c_int64), ("event_id", C.c_uint64)]
+        ("n", C.c_int64), ("event_id", C.c_uint64), ("event_offsets", _P), ("event_ids", _P),
+        ("n_events", C.c_int64)]
 
 
 class SimResponse(C.Structure):
@@ -95,7 +96,8 @@ def lib():
         L.sim_strerror.argtypes = [C.c_int]
         L.sim_last_cuda_error.restype = C.c_int
         L.sim_abi_sizes.argtypes = [cp(C.c_int64)]
-        L.sim_workspace_size.argtypes = [cp(SimConfig), C.c_int64, C.c_int64, C.c_int64, cp(C.c_size_t)]
+        L.sim_workspace_size.argtypes = [cp(SimConfig), C.c_int64, C.c_int64, C.c_int64, C.c_int64,
+                                         cp(C.c_size_t)]
         L.sim_workspace_counts.restype = C.c_void_p
         L.sim_workspace_counts.argtypes = [_P]
         L.sim_quench_drift.argtypes = [cp(SimConfig), cp(SimSegments), cp(SimDrifted), _P]
@@ -103,12 +105,12 @@ def lib():
                                     _P, _P, C.c_int64, _P, _P, _P, C.c_int64, _P, C.c_size_t, _P]
         L.sim_induced_current.argtypes = [cp(SimConfig), cp(SimSegments), cp(SimDrifted), cp(SimResponse),
                                           _P, _P, _P, _P, C.c_int64, _P, _P, C.c_size_t, _P]
-        L.sim_electronics.argtypes = [cp(SimConfig), C.c_uint64, _P, _P, _P, C.c_int64, cp(SimHits),
+        L.sim_electronics.argtypes = [cp(SimConfig), cp(SimSegments), _P, _P, _P, C.c_int64, cp(SimHits),
                                       _P, C.c_size_t, _P]
         L.sim_event.argtypes = [cp(SimConfig), cp(SimSegments), cp(SimResponse), C.c_int64, C.c_int64,
                                 cp(SimHits), _P, C.c_size_t, _P]
-        L.sim_event_view_of.argtypes = [cp(SimConfig), C.c_int64, C.c_int64, C.c_int64, _P, C.c_size_t,
-                                        cp(SimEventView)]
+        L.sim_event_view_of.argtypes = [cp(SimConfig), C.c_int64, C.c_int64, C.c_int64, C.c_int64, _P,
+                                        C.c_size_t, cp(SimEventView)]
         L.sim_pixel_map_noalloc.argtypes = [cp(SimConfig), cp(SimSegments), cp(SimDrifted), cp(SimResponse),
                                             _P, _P, C.c_int64, _P, _P, _P, C.c_int64, _P, _P]
         for f in ("sim_workspace_size", "sim_quench_drift", "sim_pixel_map", "sim_induced_current",
@@ -151,14 +153,19 @@ def _stream(stream):
 
 
 class Segments:
-    """Segment columns as FP32 CUDA tensors (x0, y0, z0, t0, x1, y1, z1, t1, dE)."""
+    """Segment columns as FP32 CUDA tensors (x0, y0, z0, t0, x1, y1, z1, t1, dE).
+
+    One event (``event_id``) or, with ``offsets`` (int64 [n_events + 1]) and
+    ``ids`` (uint64 as int64 [n_events]) CUDA tensors, a batch of events."""
 
     KEYS = ("x0", "y0", "z0", "t0", "x1", "y1", "z1", "t1", "dE")
 
-    def __init__(self, cols: dict, event_id: int = 0):
+    def __init__(self, cols: dict, event_id: int = 0, offsets=None, ids=None):
         self.cols = cols
         self.n = int(cols["x0"].numel())
         self.event_id = int(event_id)
+        self.offsets, self.ids = offsets, ids
+        self.n_events = 0 if offsets is None else int(offsets.numel()) - 1
 
     @classmethod
     def from_numpy(cls, seg: dict, event_id: int = 0, device="cuda"):
@@ -166,12 +173,26 @@ class Segments:
         return cls({k: torch.as_tensor(np.ascontiguousarray(seg[k], dtype=np.float32), device=device)
                     for k in cls.KEYS}, event_id)
 
+    @classmethod
+    def batch_from_numpy(cls, events: list, event_ids: list, device="cuda"):
+        """Concatenate per-event segment dicts into one batch."""
+        import torch
+        cols = {k: torch.as_tensor(np.ascontiguousarray(np.concatenate([e[k] for e in events]), dtype=np.float32),
+                                   device=device) for k in cls.KEYS}
+        off = np.zeros(len(events) + 1, dtype=np.int64)
+        off[1:] = np.cumsum([len(e["x0"]) for e in events])
+        ids = np.asarray([int(i) for i in event_ids], dtype=np.uint64).view(np.int64)
+        return cls(cols, 0, torch.as_tensor(off, device=device), torch.as_tensor(ids, device=device))
+
     def struct(self) -> SimSegments:
         s = SimSegments()
         for k in self.KEYS:
             setattr(s, k, _ptr(self.cols[k]))
         s.n = self.n
         s.event_id = self.event_id
+        s.event_offsets = _ptr(self.offsets)
+        s.event_ids = _ptr(self.ids)
+        s.n_events = self.n_events
         return s
 
 
@@ -246,9 +267,9 @@ class Hits:
         return {k: getattr(self, k)[:n].cpu().numpy() for k in ("pixel", "t_cross", "t_adc", "adc", "q")}
 
 
-def workspace_size(cfg: SimConfig, max_segments: int, max_pairs: int, max_pixels: int) -> int:
+def workspace_size(cfg: SimConfig, max_segments: int, max_pairs: int, max_pixels: int, max_events: int = 0) -> int:
     b = C.c_size_t()
-    _check(lib().sim_workspace_size(C.byref(cfg), max_segments, max_pairs, max_pixels, C.byref(b)),
+    _check(lib().sim_workspace_size(C.byref(cfg), max_events, max_segments, max_pairs, max_pixels, C.byref(b)),
            "sim_workspace_size")
     return int(b.value)
 
@@ -291,11 +312,12 @@ def sim_induced_current(cfg: SimConfig, seg: Segments, dr: Drifted, resp: Respon
                                      _stream(stream)), "sim_induced_current")
 
 
-def sim_electronics(cfg: SimConfig, event_id: int, active_pixels, current, counts, hits: Hits, ws,
-                    stream=None):
+def sim_electronics(cfg: SimConfig, events, active_pixels, current, counts, hits: Hits, ws, stream=None):
+    """``events``: the Segments (or a plain event id) whose event ids key the noise."""
     h = hits.struct()
+    ev = events.struct() if isinstance(events, Segments) else SimSegments(n=0, event_id=int(events))
     pix_cap = int(current.shape[0])
-    _check(lib().sim_electronics(C.byref(cfg), int(event_id), _ptr(active_pixels), _ptr(current), _ptr(counts),
+    _check(lib().sim_electronics(C.byref(cfg), C.byref(ev), _ptr(active_pixels), _ptr(current), _ptr(counts),
                                  pix_cap, C.byref(h), _ptr(ws), int(ws.numel() * ws.element_size()),
                                  _stream(stream)), "sim_electronics")
 
@@ -307,9 +329,11 @@ def sim_event(cfg: SimConfig, seg: Segments, resp: Response, max_pairs: int, max
                            _ptr(ws), int(ws.numel() * ws.element_size()), _stream(stream)), "sim_event")
 
 
-def sim_event_view_of(cfg: SimConfig, n_segments: int, max_pairs: int, max_pixels: int, ws) -> SimEventView:
+def sim_event_view_of(cfg: SimConfig, n_segments: int, max_pairs: int, max_pixels: int, ws,
+                      max_events: int = 0) -> SimEventView:
     v = SimEventView()
-    _check(lib().sim_event_view_of(C.byref(cfg), int(n_segments), int(max_pairs), int(max_pixels), _ptr(ws),
+    _check(lib().sim_event_view_of(C.byref(cfg), int(max_events), int(n_segments), int(max_pairs), int(max_pixels),
+                                   _ptr(ws),
                                    int(ws.numel() * ws.element_size()), C.byref(v)), "sim_event_view_of")
     return v
 
@@ -342,23 +366,27 @@ class EventRunner:
     """
 
     def __init__(self, cfg: dict, lut_padded, lut_nt: int, bins_per_pitch: int, max_segments: int,
-                 max_pairs: int, max_pixels: int, max_hits: int, device="cuda"):
+                 max_pairs: int, max_pixels: int, max_hits: int, device="cuda", max_events: int = 0):
         import torch
         self.cfg_dict = cfg
         self.cfg = make_config(cfg)
         self.resp = Response(lut_padded, lut_nt, bins_per_pitch)
         self.max_segments, self.max_pairs, self.max_pixels = int(max_segments), int(max_pairs), int(max_pixels)
-        self.ws_bytes = workspace_size(self.cfg, self.max_segments, self.max_pairs, self.max_pixels)
+        self.max_events = int(max_events)
+        self.ws_bytes = workspace_size(self.cfg, self.max_segments, self.max_pairs, self.max_pixels,
+                                       self.max_events)
         self.ws = torch.empty((self.ws_bytes + 7) // 8, dtype=torch.int64, device=device)
         self.hits = Hits(max_hits, device)
         self.device = device
 
     def view(self, n_segments: int) -> SimEventView:
-        return sim_event_view_of(self.cfg, n_segments, self.max_pairs, self.max_pixels, self.ws)
+        return sim_event_view_of(self.cfg, n_segments, self.max_pairs, self.max_pixels, self.ws, self.max_events)
 
     def enqueue(self, seg: Segments, stream=None):
         if seg.n > self.max_segments:
             raise ValueError("event larger than the runner's max_segments")
+        if seg.n_events > max(self.max_events, 1):
+            raise ValueError("batch larger than the runner's max_events")
         sim_event(self.cfg, seg, self.resp, self.max_pairs, self.max_pixels, self.hits, self.ws, stream)
 
     def counts(self):

@@ -174,6 +174,18 @@ def module_event(cfg, seed, n_target=20000):
     return to_f32(split_at_planes(seg, boundary_planes(cfg)))
 
 
+def batch_events(cfg, seed, n_events, lo=1.0e3, hi=2.0e5):
+    """``n_events`` interactions with segment counts log-uniform in [lo, hi]
+    (the module-event mixture scaled by its size), each split at the cathode."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), n_events)).astype(np.int64)
+    out = []
+    for n in sizes:
+        seg = interaction(cfg, rng, int(n))
+        out.append(to_f32(split_at_planes(seg, boundary_planes(cfg))))
+    return out
+
+
 def rock_muon(cfg, rng, t0):
     """A straight muon crossing the whole module array, mostly along x."""
     g = geometry(cfg)

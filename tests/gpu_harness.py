@@ -67,7 +67,7 @@ class Steps:
         return self
 
     def electronics(self):
-        sim.sim_electronics(self.cfg, self.event_id, self.active, self.current[: self.pix_cap], self.counts,
+        sim.sim_electronics(self.cfg, self.seg, self.active, self.current[: self.pix_cap], self.counts,
                             self.hits, self.ws)
         return self
 

@@ -58,10 +58,11 @@ def test_host_argument_checks_reject_before_launch(L):
     from synth import params
     cfg = sim.make_config(params.module_config())
     b = C.c_size_t()
-    assert L.sim_workspace_size(C.byref(cfg), 100, 1000, 100, C.byref(b)) == 0 and b.value > 0
-    assert L.sim_workspace_size(C.byref(cfg), -1, 1000, 100, C.byref(b)) == -1
+    assert L.sim_workspace_size(C.byref(cfg), 0, 100, 1000, 100, C.byref(b)) == 0 and b.value > 0
+    assert L.sim_workspace_size(C.byref(cfg), 0, -1, 1000, 100, C.byref(b)) == -1
+    assert L.sim_workspace_size(C.byref(cfg), 20000, 1, 1, 1, C.byref(b)) == -1   # > 2^31 virtual pixels
     bad = sim.make_config(params.module_config(n_ticks=0))
-    assert L.sim_workspace_size(C.byref(bad), 1, 1, 1, C.byref(b)) == -1
+    assert L.sim_workspace_size(C.byref(bad), 0, 1, 1, 1, C.byref(b)) == -1
     seg = sim.SimSegments()
     seg.n = 5                                   # null columns
     d = sim.SimDrifted()

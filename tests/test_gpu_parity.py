@@ -196,7 +196,7 @@ def test_electronics_closed_form_gpu():
     ws = torch.zeros((sim.workspace_size(c, 0, 0, P) + 7) // 8, dtype=torch.int64, device=dev)
     counts = ws[:4]
     counts[1] = P
-    sim.sim_electronics(c, 0, active, cur, counts, hits, ws)
+    sim.sim_electronics(c, 0, active, cur, counts, hits, ws)     # event id 0
     torch.cuda.synchronize()
     n = int(counts[2])
     h = hits.to_numpy(n)
