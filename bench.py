@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--workload", choices=["module", "tile", "spill"], default="module")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--precision", type=int, choices=[0, 1, 2], default=0,
+                    help="induced-current form: 0 FP32 direct, 1 BF16 / 2 FP16 tensor cores")
     return ap.parse_args()
 
 
@@ -260,6 +262,7 @@ def run_ours(args):
         tdist.init_process_group("nccl", device_id=dev)
         pg = tdist
     cfg, seg, desc = workload(args.workload)
+    cfg["precision"] = args.precision
     S = len(seg["x0"])
     T = int(cfg["n_ticks"])
     lut64 = response.lut_for(cfg, params.LUT)
@@ -357,6 +360,18 @@ def run_ours(args):
                 "traffic": stored_traffic("induced_current.cu"), "kernel": "k_induced_current",
                 "peak_note": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz",
                 "work_note": "2 flop x 9 pixels x 1950 table ticks per (point, perturbation)"}
+    if args.precision:
+        # tensor-core form: dense MMA work of the launch (counted on the device) against the
+        # measured dense 16-bit tensor peak; the algorithmic work above is kept as useful_frac
+        n_mma = int(run.ws[4].item())
+        dense = 2.0 * 128 * 32 * 16 * n_mma / a4_s / 1e12
+        tpk = measured_peaks().get("bf16_tflops") or 1900.0
+        roofline = {"bound": "tensor", "achieved": dense, "peak": tpk, "unit": "TFLOP/s", "frac": dense / tpk,
+                    "traffic": stored_traffic("induced_current_tc.cu"), "kernel": "k_induced_current_tc",
+                    "mma_per_launch": n_mma, "useful_achieved": achieved, "useful_frac": achieved / tpk,
+                    "peak_note": "measured dense bf16 burst (fp16 has the same nominal rate)",
+                    "work_note": "dense: 2 x 128 x 32 x 16 flop per MMA; useful: 2 flop x 9 pixels x 1950 "
+                                 "table ticks per (point, perturbation)"}
 
     # end to end through the public API: pinned host segments in, hits out
     io = sim.EventIO(run)
@@ -391,7 +406,7 @@ def run_ours(args):
         print(json.dumps({
             "metric": "segments/s", "value": value, "unit": "segments/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": ["f32", "bf16", "f16"][args.precision],
             "data": "synthetic",
             "config": {"workload": desc, "segments": S, "active_pixels": n_pix, "pairs": n_pairs,
                        "hits": n_hits, "n_ticks": T, "points": samples, "parallelism": f"replicas{world}",

@@ -46,6 +46,7 @@ extern "C" {
 #define SIM_STATUS_PIXEL_OVERFLOW 2
 #define SIM_STATUS_HIT_OVERFLOW 4
 #define SIM_STATUS_TICK_RANGE 8
+#define SIM_STATUS_TIMEOUT 16     /* a bounded device-side wait gave up (tensor-core form) */
 
 /* Simulation parameters (host struct, copied at each call).  Floating-point
  * fields are FP32.  Citations: recombination Sec. 3.1 Eq. (birks)/(box);
@@ -73,7 +74,9 @@ typedef struct sim_config {
     int32_t hold_ticks, min_adc_interval_ticks, periodic_reset_ticks, adc_bits;
     /* counter-based RNG seed (Philox4x32-10 key = seed ^ event_id) */
     uint64_t seed;
-    /* arithmetic form of the induced-current step: 0 = FP32 direct */
+    /* arithmetic form of the induced-current step (sim_induced_current):
+     * 0 = FP32 direct gather; 1 = tensor-core contraction with BF16 operands,
+     * 2 = with FP16 operands (FP32 accumulation in both) */
     int32_t precision;
     int32_t reserved;
 } sim_config;
@@ -189,11 +192,23 @@ int sim_pixel_map(const sim_config *cfg, const sim_segments *seg, const sim_drif
  * the table read bilinearly at the folded transverse offset and linearly at
  * the fractional arrival tick a; summed over segments in increasing index
  * order.  current: FP32 [pix_cap][n_ticks]; rows [0, counts[1]) are written.
- * counts: device int64[4] counts block as written by sim_pixel_map ([1] =
+ * counts: device int64[5] counts block as written by sim_pixel_map ([1] =
  * active pixels, [3] = status); nothing is computed when the status word is
- * nonzero or counts[1] > pix_cap.  Workspace (scratch from byte 256 on):
- * sim_workspace_size(cfg, 0, 0, 0, pix_cap) bytes, sized for the current device
- * (a per-CTA record buffer).  Table limits: nb * nb <= 2048, nt <= 2048. */
+ * nonzero or counts[1] > pix_cap.
+ * cfg->precision selects the arithmetic: 0 sums the terms in FP32 in the
+ * order above; 1 (BF16) and 2 (FP16) regroup them as I[p, k] = sum over table
+ * nodes n and arrival ticks a of Q[p, n, a] R[n, k - a + L - 1] (Q: charge
+ * deposited on node n at tick a by the linear weights) and contract Q with the
+ * Toeplitz unfolding of each table row on the tensor cores.  Q is accumulated
+ * in fixed point (2^-12 e-) and rounded to the operand type, as is R; FP16 Q
+ * cells saturate at 262016 e-.  Results are bitwise reproducible for a given
+ * call; counts[4] receives the number of tensor-core MMA instructions
+ * (M = 128, N = 32, K = 16) of the call, and SIM_STATUS_TIMEOUT is set if a
+ * bounded device-side wait gave up.
+ * Workspace (scratch from byte 256 on): sim_workspace_size(cfg, 0, 0, 0,
+ * pix_cap) bytes, sized for the current device (per-CTA record buffers; with
+ * precision 1/2 also the unfolded table, ~1.4 GB in all on 152 SMs).  Table
+ * limits: nb * nb <= 2048, nt <= 2048. */
 int sim_induced_current(const sim_config *cfg, const sim_segments *seg, const sim_drifted *dr,
                         const sim_response *resp, const int32_t *active_pixels,
                         const int32_t *pix_seg_off, const int32_t *pix_seg_ids,

@@ -30,7 +30,7 @@ bool cfg_ok(const sim_config *c)
     if (c->mc_per_sample < 1 || !(c->diff_clip_sigma >= 0.f) || !(c->lifetime_us > 0.f)) return false;
     if (c->recomb_model != 0 && c->recomb_model != 1) return false;
     if (c->adc_bits < 1 || c->adc_bits > 16 || c->hold_ticks < 0 || c->min_adc_interval_ticks < 0) return false;
-    if (c->periodic_reset_ticks < 0 || c->precision != 0) return false;
+    if (c->periodic_reset_ticks < 0 || c->precision < 0 || c->precision > 2) return false;
     return true;
 }
 
@@ -69,6 +69,21 @@ bool hits_ok(const sim_hits *h)
     return h && h->capacity >= 0 && (h->capacity == 0 || (h->pixel && h->t_cross && h->t_adc && h->adc && h->q));
 }
 
+// Scratch and launch of the induced-current form selected by cfg.precision.
+size_t current_scratch(const sim_config &c, int64_t pixels)
+{
+    return c.precision == 0 ? current_scratch_bytes(pixels) : current_tc_scratch_bytes(pixels);
+}
+
+cudaError_t launch_current(const sim_config &c, const sim_segments &s, const sim_drifted &d, const sim_response &r,
+                           const int32_t *active, const int32_t *off, const int32_t *ids, const int64_t *counts,
+                           int64_t pix_cap, float *current, void *scratch, cudaStream_t st)
+{
+    if (c.precision == 0)
+        return launch_induced_current(c, s, d, r, active, off, ids, counts, pix_cap, current, scratch, st);
+    return launch_induced_current_tc(c, s, d, r, active, off, ids, counts, pix_cap, current, scratch, st);
+}
+
 // Layout of sim_event's workspace.
 struct Layout {
     size_t counts, scratch, Qa, td, sT, sL, anode, ns, anch;
@@ -86,7 +101,7 @@ Layout layout(const sim_config &c, int64_t slots, int64_t n, int64_t pairs, int6
     };
     L.counts = take(256);
     size_t sc = map_scratch_bytes(c, n, slots);
-    const size_t es = elec_scratch_bytes(c, pixels), cs = current_scratch_bytes(pixels);
+    const size_t es = elec_scratch_bytes(c, pixels), cs = pixels > 0 ? current_scratch(c, pixels) : 0;
     if (es > sc) sc = es;
     if (cs > sc) sc = cs;
     L.scratch = take(sc);
@@ -214,11 +229,10 @@ int sim_induced_current(const sim_config *cfg, const sim_segments *seg, const si
     if (pix_cap > 0 && (!active_pixels || !pix_seg_off || !pix_seg_ids || !current)) return SIM_ERR_INVALID_ARG;
     if (pix_cap > 0 && seg->n > 0 && !drifted_ok(dr)) return SIM_ERR_INVALID_ARG;
     if (pix_cap == 0) return SIM_OK;
-    if (ws_bytes < 256 + current_scratch_bytes(pix_cap)) return SIM_ERR_CAPACITY;
+    if (ws_bytes < 256 + current_scratch(*cfg, pix_cap)) return SIM_ERR_CAPACITY;
     const sim_drifted d0 = dr ? *dr : sim_drifted{};
-    const cudaError_t e = launch_induced_current(*cfg, *seg, d0, *resp, active_pixels, pix_seg_off, pix_seg_ids,
-                                                 counts, pix_cap, current, reinterpret_cast<char *>(ws) + 256,
-                                                 (cudaStream_t)stream);
+    const cudaError_t e = launch_current(*cfg, *seg, d0, *resp, active_pixels, pix_seg_off, pix_seg_ids, counts,
+                                         pix_cap, current, reinterpret_cast<char *>(ws) + 256, (cudaStream_t)stream);
     return e == cudaSuccess ? SIM_OK : cuda_fail(e);
 }
 
@@ -264,8 +278,8 @@ int sim_event(const sim_config *cfg, const sim_segments *seg, const sim_response
                          max_pairs, v.active_pixels, v.pix_seg_off, v.pix_seg_ids, max_pixels, v.counts,
                          w + L.scratch, st);
     if (e != cudaSuccess) return cuda_fail(e);
-    e = launch_induced_current(*cfg, *seg, v.dr, *resp, v.active_pixels, v.pix_seg_off, v.pix_seg_ids, v.counts,
-                               max_pixels, v.current, w + L.scratch, st);
+    e = launch_current(*cfg, *seg, v.dr, *resp, v.active_pixels, v.pix_seg_off, v.pix_seg_ids, v.counts, max_pixels,
+                       v.current, w + L.scratch, st);
     if (e != cudaSuccess) return cuda_fail(e);
     e = launch_electronics(*cfg, events_of(*seg), v.active_pixels, v.current, v.counts, max_pixels, *out,
                            w + L.scratch, st);

@@ -1,0 +1,70 @@
+// current_records.cuh -- the per-(point, pixel) record of Eq. (current)
+// (arXiv:2212.09807 Sec. 3.3.2) shared by both arithmetic forms of the
+// induced-current step, so that both sum exactly the same terms.
+#pragma once
+
+#include "sim_internal.cuh"
+
+namespace larsim {
+
+// One perturbed point seen from one pixel: arrival tick A + f (integer part
+// and fraction), the table bin b0 = bx * nb + by of the folded offset
+// (bx, by), and the q-scaled bilinear weights of the four table rows
+// (bx, by), (bx+1, by), (bx, by+1), (bx+1, by+1) (zero for rows beyond the table).
+struct __align__(16) Rec {
+    int A, b0;
+    float f, pad;
+    float4 w;
+};
+
+// Pixel-independent part of the record of point `idx` (= mu M + nu) of a
+// segment: position in pitch units relative to the anchor's reference pixel
+// corner, and the arrival tick relative to the anchor's A0.
+struct PointPos {
+    float fx, fy, lin;
+};
+
+__device__ __forceinline__ PointPos point_position(const Anchor &A, int idx, int M, uint64_t key,
+                                                   uint32_t seg_local, float clip)
+{
+    const int mu = (M == 1) ? idx : idx / M;
+    float3 n = normals3(key, seg_local, (uint32_t)idx, 1u);
+    n.x = fminf(fmaxf(n.x, -clip), clip);
+    n.y = fminf(fmaxf(n.y, -clip), clip);
+    n.z = fminf(fmaxf(n.z, -clip), clip);
+    const float u = ((float)mu + 0.5f) / (float)A.N;
+    PointPos p;
+    p.fx = A.fx0 + u * A.dX + A.sTp * n.x;
+    p.fy = A.fy0 + u * A.dY + A.sTp * n.y;
+    float lin = A.fa0 + u * A.da + A.sLc * n.z * A.kz;
+    const float dmu = A.d0 + u * A.dd + A.sLc * n.z;
+    if (dmu < 0.f) lin -= 2.0f * dmu * A.kz;     // charge beyond the anode plane drifts back
+    p.lin = lin;
+    return p;
+}
+
+// Record of a point for the pixel whose centre is (cx, cy) in the same pitch
+// units; false when the folded offset is beyond the table (nb bins of 1/bpp
+// pitch in x or y).
+__device__ __forceinline__ bool point_record(const Anchor &A, const PointPos &p, float cx, float cy, float fbpp,
+                                             int nb, Rec &r)
+{
+    const float fnb = (float)nb;
+    const float xi = fmaxf(fabsf((p.fx - cx) * fbpp) - 0.5f, 0.f);
+    const float yi = fmaxf(fabsf((p.fy - cy) * fbpp) - 0.5f, 0.f);
+    if (!(xi < fnb && yi < fnb)) return false;
+    const float fl = floorf(p.lin);
+    const int bx = (int)xi, by = (int)yi;
+    const float wx = xi - (float)bx, wy = yi - (float)by;
+    // node nb (beyond the table) reads zero: far corners get no weight
+    const float ex = (bx + 1 < nb) ? 1.f : 0.f, ey = (by + 1 < nb) ? 1.f : 0.f;
+    const float q1 = A.q * (1.f - wx), q2 = A.q * wx * ex;
+    r.A = A.A0 + (int)fl;
+    r.b0 = bx * nb + by;
+    r.f = p.lin - fl;
+    r.pad = 0.f;
+    r.w = make_float4(q1 * (1.f - wy), q2 * (1.f - wy), q1 * wy * ey, q2 * wy * ey);
+    return true;
+}
+
+}  // namespace larsim

@@ -33,7 +33,7 @@
 // table is read from L2 once per (pixel, bin) instead of once per record.
 // Summation order is fixed (chunks in point order, bins increasing, records
 // in point order within a bin): results are bitwise reproducible.
-#include "sim_internal.cuh"
+#include "current_records.cuh"
 
 namespace larsim {
 
@@ -49,12 +49,6 @@ constexpr int kMaxRow = 2048;                   // staged row length (>= nt roun
 constexpr int kEdge = kHalf + 8;                // zero quads before position 0 and after L - 1
 constexpr int kQuads = kMaxRow + 2 * kEdge;     // staged quads (position p at p + kEdge)
 constexpr int kPosPerThread = kMaxRow / kThreads;   // positions staged per thread
-
-struct __align__(16) Rec {
-    int A, b0;
-    float f, pad;
-    float4 w;                                   // q-scaled weights of rows (0,0), (1,0), (0,1), (1,1)
-};
 
 struct CurArgs {
     sim_config c;
@@ -191,7 +185,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int T = a.c.n_ticks, L = a.nt, M = a.c.mc_per_sample, nb2 = a.nb * a.nb;
     const float clip = a.c.diff_clip_sigma;
-    const float fbpp = (float)a.bpp, fnb = (float)a.nb;
+    const float fbpp = (float)a.bpp;
     const int npx = a.g.npx_x * a.g.npx_y;
     Rec *recs = a.recs + (size_t)blockIdx.x * kRecCap;
     Rec *sorted = a.sorted + (size_t)blockIdx.x * kRecCap;
@@ -234,33 +228,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a)
                     bool ok = false;
                     Rec r;
                     if (idx < total) {
-                        const int mu = (M == 1) ? idx : idx / M;
-                        float3 n = normals3(key, (uint32_t)(sg - seg0), (uint32_t)idx, 1u);
-                        n.x = fminf(fmaxf(n.x, -clip), clip);
-                        n.y = fminf(fmaxf(n.y, -clip), clip);
-                        n.z = fminf(fmaxf(n.z, -clip), clip);
-                        const float u = ((float)mu + 0.5f) / (float)A.N;
-                        const float fx = A.fx0 + u * A.dX + A.sTp * n.x;
-                        const float fy = A.fy0 + u * A.dY + A.sTp * n.y;
-                        const float xi = fmaxf(fabsf((fx - cx) * fbpp) - 0.5f, 0.f);
-                        const float yi = fmaxf(fabsf((fy - cy) * fbpp) - 0.5f, 0.f);
-                        if (xi < fnb && yi < fnb) {
-                            ok = true;
-                            float lin = A.fa0 + u * A.da + A.sLc * n.z * A.kz;
-                            const float dmu = A.d0 + u * A.dd + A.sLc * n.z;
-                            if (dmu < 0.f) lin -= 2.0f * dmu * A.kz;
-                            const float fl = floorf(lin);
-                            const int bx = (int)xi, by = (int)yi;
-                            const float wx = xi - (float)bx, wy = yi - (float)by;
-                            // node nb (beyond the table) reads zero: far corners get no weight
-                            const float ex = (bx + 1 < a.nb) ? 1.f : 0.f, ey = (by + 1 < a.nb) ? 1.f : 0.f;
-                            const float q1 = A.q * (1.f - wx), q2 = A.q * wx * ex;
-                            r.A = A.A0 + (int)fl;
-                            r.b0 = bx * a.nb + by;
-                            r.f = lin - fl;
-                            r.pad = 0.f;
-                            r.w = make_float4(q1 * (1.f - wy), q2 * (1.f - wy), q1 * wy * ey, q2 * wy * ey);
-                        }
+                        const PointPos pp = point_position(A, idx, M, key, (uint32_t)(sg - seg0), clip);
+                        ok = point_record(A, pp, cx, cy, fbpp, a.nb, r);
                     }
                     const unsigned m = __ballot_sync(0xffffffffu, ok);
                     if (lane == 0) s->warp_n[warp] = __popc(m);

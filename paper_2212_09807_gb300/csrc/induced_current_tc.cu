@@ -1,0 +1,1031 @@
+// induced_current_tc.cu -- step 4 of the charge path (arXiv:2212.09807
+// Sec. 3.3.2, Eq. (current)) as a tensor-core contraction on sm_103a:
+// tcgen05 MMAs with FP16 or BF16 operands and FP32 accumulators in tensor
+// memory.  Same terms as the FP32 direct form (the records of
+// current_records.cuh), different arithmetic.
+//
+// With the table read bilinearly in the folded offset and linearly in the
+// arrival tick, the per-pixel sum of Eq. (current) is a sum of shifted table
+// rows of the table nodes:
+//   I[p, k] = sum_node sum_a Q[p, node, a] R[node, k - a + L - 1],
+// where a record (arrival A + f, bin b0, weights w_c of the four corner nodes
+// b0 + c) deposits (1 - f) w_c at tick A and f w_c at tick A + 1 of node
+// b0 + c.  Cut the arrival ticks into blocks of 16 (ab) and the output ticks
+// into tiles of 128 (t): for one node and one block the contribution to one
+// tile is a matrix product
+//   D_t[r, p] += sum_{a' < 16} Im[128 t - 16 ab + rho0 + r, a'] Q[p, 16 ab + a']
+// with Im[rho, a'] = R[node, rho - rho0 - a' + L - 1] (zero outside the row),
+// the im2col (Toeplitz) unfolding of the row: M = 128 ticks, N = 32 pixels,
+// K = 16 arrival ticks.
+//
+// Design: one CTA of 256 threads per SM (persistent, dynamic group queue).
+//  - A CTA owns a group of 32 active pixels and a pass of 2048 ticks; the
+//    accumulators D (16 tiles of 128 ticks x 32 pixels, FP32) stay in tensor
+//    memory (all 512 columns) for the whole pass.
+//  - The im2col unfolding of every table row is built once per call in
+//    global memory (FP16/BF16, canonical no-swizzle K-major layout); for each
+//    node the CTA copies that row's unfolding (rho0 + 128 rows x 32 bytes)
+//    into shared memory with one bulk asynchronous copy, double-buffered.
+//  - Records of the group's pixels are generated into a per-CTA buffer and
+//    sorted per pixel by table bin (counting sort).  A node receives the
+//    records of four bins (its corners) of each pixel.
+//  - Builder warps 4-7 (warp = corner, lane = pixel) turn a node's records
+//    into charge tiles Q[16 blocks][16 ticks][32 pixels], accumulated with
+//    integer atomics in fixed point (order-independent, so the result is
+//    bitwise reproducible), then converted to FP16/BF16 operand tiles.
+//  - Issuer warps 0-3 (one thread each) own tick tiles t = w, w + 4, ... and
+//    issue the MMAs of each batch; tcgen05.commit on mbarriers returns the
+//    operand buffers.  At the end of a pass warps 0-3 read D back (tcgen05.ld,
+//    lane = tick) and store the currents.
+// Every mbarrier wait is bounded; a wait that gives up sets
+// SIM_STATUS_TIMEOUT in the status word and the CTA drains and returns.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "current_records.cuh"
+
+namespace larsim {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kGroup = 32;                  // pixels per group (MMA N)
+constexpr int kTileM = 128;                 // ticks per accumulator tile (MMA M)
+constexpr int kTiles = 16;                  // tiles in tensor memory
+constexpr int kPassTicks = kTileM * kTiles; // ticks per pass
+constexpr int kBlk = 16;                    // arrival ticks per block (MMA K)
+constexpr int kSlots = 16;                  // blocks per operand batch
+constexpr int kMaxBins = 2048;              // nb * nb <= kMaxBins
+constexpr int kMaxRows = 2304;              // im2col rows: rho0 + 128 for nt <= 2048
+constexpr int kRowBytes = 32;               // 16 FP16 per im2col row
+constexpr int kRecCap = 1 << 17;            // records per chunk per CTA
+constexpr int kSubsPerSm = 4;               // work-balanced sub-groups per SM (target)
+constexpr int kFlushNodes = 64;             // nodes per accumulation window (see flush_acc)
+constexpr float kFix = 4096.f;              // fixed-point scale of the charge accumulators (2^-12 e-)
+constexpr int kIssuers = 4;
+constexpr uint32_t kTmemCols = 512;
+constexpr int kMaxSpin = 1 << 22;           // bounded mbarrier waits (x ~ 0.5 us each)
+
+struct BatchMeta {
+    int node, count, last, pad;
+    unsigned char blk[kSlots];              // block index relative to the pass start
+};
+
+struct __align__(1024) TcSmem {
+    unsigned char im[2][kMaxRows * kRowBytes];
+    unsigned char bst[2][kSlots * 1024];
+    union {
+        struct {
+            int hist[kMaxBins];
+            unsigned char nflag[kMaxBins];
+            int scan_tmp[kThreads / 32 + 1];
+            int warp_n[kThreads / 32];
+        } g;
+        int acc[kSlots * kBlk * kGroup];
+    } u;
+    unsigned short nodes[kMaxBins];
+    BatchMeta meta[2];
+    uint64_t full_im[2], empty_im[2], full_b[2], empty_b[2], done;
+    uint32_t taddr;
+    uint32_t blkmask[8];
+    int lst_beg[128], lst_off[128], lst_wsum[4];
+    int pin[kGroup];
+    int n_nodes, group, abort;
+};
+
+struct TcArgs {
+    sim_config c;
+    int nb, nt, bpp, rho0, im_bytes;
+    uint32_t idesc;
+    float qscale;                           // fixed point -> operand units
+    float out_scale;                        // accumulator -> current (1 / table scale)
+    const unsigned char *table;             // im2col unfolding, [nb*nb][im_bytes]
+    const Anchor *anch;
+    const int32_t *active, *off, *segs;
+    const int64_t *counts;
+    unsigned long long *status;             // counts[3]; counts[4] receives the MMA count
+    int64_t pix_cap;
+    float *current;
+    uint64_t seed;
+    EventInfo ev;
+    Geo g;
+    int *queue;                             // next entry of `order`
+    const int4 *subs;                       // sub-groups {first pixel, pixels, work lo, work hi}
+    const int32_t *order;                   // sub-groups by decreasing work
+    const int64_t *n_subs;
+    Rec *recs, *sorted;                     // [grid][kRecCap]
+    int *offt;                              // [grid][kGroup][kMaxBins + 1]
+};
+
+// ----------------------------------------------------- PTX wrappers ----
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor, no swizzle: start, K-direction core-matrix
+// stride (LBO), M/N-direction 8-row-group stride (SBO), version bit 46.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t a, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((a >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, A/B format (0 FP16,
+// 1 BF16), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t instr_desc(int fmt, int M, int N)
+{
+    return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of element (row, k) of a K-major tile with 16 K elements:
+// 8-row x 16-byte core matrices, K-adjacent ones 128 B apart, row groups 256 B apart.
+__host__ __device__ __forceinline__ int core_off(int row, int k)
+{
+    return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t id)
+{
+    asm volatile("{\n .reg .pred p;\n setp.eq.u32 p, 1, 1;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d), "l"(a), "l"(b), "r"(id)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void bar_init(uint64_t *bar, int n)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
+}
+
+// Bounded wait for the completion of the phase with the given parity.
+__device__ __forceinline__ bool bar_wait(TcSmem *s, uint64_t *bar, uint32_t parity)
+{
+    for (int it = 0; it < kMaxSpin; ++it) {
+        uint32_t ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok)
+                     : "r"(saddr(bar)), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+        if (*(volatile int *)&s->abort) return false;
+    }
+    atomicExch(&s->abort, 1);
+    return false;
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     saddr(dst)),
+                 "l"(src), "r"(bytes), "r"(saddr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void builders_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Barrier of the builder threads that also returns whether any of them saw
+// the abort flag (a uniform decision: no builder is left waiting at a barrier).
+__device__ __forceinline__ bool builders_any_abort(TcSmem *s)
+{
+    const int mine = *(volatile int *)&s->abort;
+    int any;
+    asm volatile("{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.or.pred q, 1, 128, p;\n"
+                 " selp.s32 %0, 1, 0, q;\n}\n"
+                 : "=r"(any)
+                 : "r"(mine)
+                 : "memory");
+    return any != 0;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t ta, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                   "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+                   "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+                   "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(ta));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_zero32(uint32_t ta)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+                 "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(ta),
+                 "r"(0u)
+                 : "memory");
+}
+
+// --------------------------------------------------------- helpers ----
+// Exclusive scan of one int per thread across the CTA; *tot = total.
+__device__ __forceinline__ int block_scan(int v, TcSmem *s, int *tot)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int W = kThreads / 32;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s->u.g.scan_tmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const int w = lane < W ? s->u.g.scan_tmp[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < W) s->u.g.scan_tmp[lane] = wi - w;
+        if (lane == W - 1) s->u.g.scan_tmp[W] = wi;
+    }
+    __syncthreads();
+    const int r = s->u.g.scan_tmp[warp] + x - v;
+    *tot = s->u.g.scan_tmp[W];
+    __syncthreads();
+    return r;
+}
+
+// Two operand values; FP16 saturates at its largest finite value.
+template <int FMT>
+__device__ __forceinline__ uint32_t pack2(float a, float b)
+{
+    if (FMT == 0) {
+        const __half2 h = __floats2half2_rn(fminf(fmaxf(a, -65504.f), 65504.f), fminf(fmaxf(b, -65504.f), 65504.f));
+        return *reinterpret_cast<const uint32_t *>(&h);
+    } else {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<const uint32_t *>(&h);
+    }
+}
+
+// ------------------------------------------------- record generation ----
+// Generation cursor of a group: pixel slot, CSR position, point index.
+struct GenState {
+    int gp, e, base;
+};
+
+// Generates the records of the group's pixels from the cursor on, until the
+// chunk buffer is full or the group is done; sorts each pixel's part by bin
+// into `sorted`, writes its bin offsets to offt, marks the nodes it touches.
+// Returns the number of records of the chunk; st.gp == npg when done.
+__device__ int gen_chunk(const TcArgs &a, TcSmem *s, GenState &st, int64_t pi0, int npg, Rec *recs, Rec *sorted,
+                         int *offt)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nb = a.nb, nb2 = nb * nb, M = a.c.mc_per_sample;
+    const float clip = a.c.diff_clip_sigma, fbpp = (float)a.bpp;
+    const int npx = a.g.npx_x * a.g.npx_y;
+    int nrec = 0;
+    while (st.gp < npg) {
+        const int64_t pi = pi0 + st.gp;
+        const int32_t pid = a.active[pi];
+        const int an = pid / npx;
+        const int rem = pid - an * npx;
+        const int iy = rem / a.g.npx_x, ix = rem - iy * a.g.npx_x;
+        const int slot = an / a.g.n_anodes;
+        const uint64_t key = slot_key(a.seed, a.ev, slot);
+        const int64_t seg0 = slot_first(a.ev, slot);
+        if (st.e < 0) {
+            st.e = a.off[pi];
+            st.base = 0;
+        }
+        const int e1 = a.off[pi + 1];
+        const int start = nrec;
+        bool full = false;
+        while (st.e < e1) {
+            const int sg = a.segs[st.e];
+            const Anchor A = a.anch[sg];
+            const int total = A.N * M;
+            if (st.base >= total) {
+                ++st.e;
+                st.base = 0;
+                continue;
+            }
+            const int idx = st.base + tid;
+            bool ok = false;
+            Rec r;
+            if (idx < total) {
+                const PointPos pp = point_position(A, idx, M, key, (uint32_t)(sg - seg0), clip);
+                ok = point_record(A, pp, (float)(ix - A.ix_ref) + 0.5f, (float)(iy - A.iy_ref) + 0.5f, fbpp, nb, r);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, ok);
+            if (lane == 0) s->u.g.warp_n[warp] = __popc(m);
+            __syncthreads();
+            int wb = 0, nq = 0;
+#pragma unroll
+            for (int w2 = 0; w2 < kThreads / 32; ++w2) {
+                const int c2 = s->u.g.warp_n[w2];
+                wb += (w2 < warp) ? c2 : 0;
+                nq += c2;
+            }
+            __syncthreads();
+            if (nrec + nq > kRecCap) {      // chunk full: this batch is redone in the next chunk
+                full = true;
+                break;
+            }
+            if (ok) {
+                const int d = nrec + wb + __popc(m & ((1u << lane) - 1u));
+                recs[d] = r;
+                atomicAdd(&s->u.g.hist[r.b0], 1);
+            }
+            nrec += nq;
+            st.base += kThreads;
+        }
+        __syncthreads();
+        if (nrec > start) {
+            // bin offsets of this pixel's part, node flags, scatter cursors
+            constexpr int kB = kMaxBins / kThreads;
+            int v[kB], sv = 0;
+#pragma unroll
+            for (int i = 0; i < kB; ++i) {
+                const int b = tid * kB + i;
+                v[i] = (b < nb2) ? s->u.g.hist[b] : 0;
+                sv += v[i];
+            }
+            int tot;
+            int pv = start + block_scan(sv, s, &tot);
+            int *orow = offt + (size_t)st.gp * (kMaxBins + 1);
+#pragma unroll
+            for (int i = 0; i < kB; ++i) {
+                const int b = tid * kB + i;
+                if (b < nb2) {
+                    orow[b] = pv;
+                    s->u.g.hist[b] = pv;
+                    if (v[i] > 0) {
+                        const int bx = b / nb, by = b - bx * nb;
+                        s->u.g.nflag[b] = 1;
+                        if (bx + 1 < nb) s->u.g.nflag[b + nb] = 1;
+                        if (by + 1 < nb) s->u.g.nflag[b + 1] = 1;
+                        if (bx + 1 < nb && by + 1 < nb) s->u.g.nflag[b + nb + 1] = 1;
+                    }
+                }
+                pv += v[i];
+            }
+            if (tid == 0) {
+                orow[nb2] = nrec;
+                s->pin[st.gp] = 1;
+            }
+            __syncthreads();
+            for (int i = start + tid; i < nrec; i += kThreads) {
+                const Rec r = recs[i];
+                sorted[atomicAdd(&s->u.g.hist[r.b0], 1)] = r;
+            }
+            __syncthreads();
+            for (int b = tid; b < nb2; b += kThreads) s->u.g.hist[b] = 0;
+            __syncthreads();
+        }
+        if (full) break;
+        ++st.gp;
+        st.e = -1;
+    }
+    return nrec;
+}
+
+// ------------------------------------------------------------ roles ----
+// List L of a node (L = corner c * 32 + pixel) holding flat record index k:
+// the last L with lst_off[L] <= k (empty lists share their successor's offset).
+__device__ __forceinline__ int find_list(const int *off, int k)
+{
+    int lo = 0;
+#pragma unroll
+    for (int step = 64; step > 0; step >>= 1)
+        if (off[lo + step] <= k) lo += step;
+    return lo;
+}
+
+// Builder threads (warps 4-7, bt = 0..127).  For each node the 128 record
+// lists (corner c = bt / 32 of pixel bt % 32: the pixel's records in bin
+// node - c) are concatenated and the builders share the records evenly; the
+// charge of each (block, tick, pixel) cell is summed with integer atomics, so
+// the order does not matter.  Publishes each node's operand batches in order.
+// Control flow is uniform across the builders (their named barriers); after
+// an abort they stop at the next node.
+template <int FMT>
+__device__ void build_batches(const TcArgs &a, TcSmem *s, const Rec *sorted, const int *offt,
+                              const unsigned short *nodes, int nn, uint32_t &q)
+{
+    constexpr int U = 4;                                // records in flight per thread
+    const int bt = threadIdx.x - 128, lane = bt & 31, cw = bt >> 5;
+    const int nb = a.nb;
+    for (int u = 0; u < nn; ++u) {
+        if (builders_any_abort(s)) return;
+        const int n = nodes[u];
+        const int nx = n / nb, ny = n - nx * nb;
+        const int bx = nx - (cw & 1), by = ny - (cw >> 1);
+        int beg = 0, len = 0;
+        if (s->pin[lane] && bx >= 0 && by >= 0) {
+            const int *orow = offt + (size_t)lane * (kMaxBins + 1);
+            const int b = bx * nb + by;
+            beg = orow[b];
+            len = orow[b + 1] - beg;
+        }
+        int x = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s->lst_wsum[cw] = x;
+        if (bt < 8) s->blkmask[bt] = 0;
+        builders_sync();
+        int R = 0, pre = 0;
+#pragma unroll
+        for (int w2 = 0; w2 < 4; ++w2) {
+            pre += (w2 < cw) ? s->lst_wsum[w2] : 0;
+            R += s->lst_wsum[w2];
+        }
+        s->lst_beg[bt] = beg;
+        s->lst_off[bt] = pre + x - len;
+        builders_sync();
+        // pass 1: blocks present in this pass's window (arrival ticks are relative to the pass start)
+        for (int k0 = bt; k0 < R; k0 += U * 128) {
+            int4 h[U];
+            float w[U];
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const int k = k0 + j * 128;
+                h[j] = make_int4(0, 0, 0, 0);
+                w[j] = 0.f;
+                if (k < R) {
+                    const int L = find_list(s->lst_off, k);
+                    const Rec *r = sorted + s->lst_beg[L] + (k - s->lst_off[L]);
+                    h[j] = *reinterpret_cast<const int4 *>(r);
+                    w[j] = reinterpret_cast<const float *>(&r->w)[L >> 5];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const float f = __int_as_float(h[j].z);
+#pragma unroll
+                for (int tap = 0; tap < 2; ++tap) {
+                    const float val = tap ? f * w[j] : (1.f - f) * w[j];
+                    const int rb = (h[j].x + tap) >> 4;
+                    if (val != 0.f && rb >= 0 && rb < 256) atomicOr(&s->blkmask[rb >> 5], 1u << (rb & 31));
+                }
+            }
+        }
+        builders_sync();
+        uint32_t m[8];
+        int pw[8], nblk = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            m[j] = s->blkmask[j];
+            pw[j] = nblk;
+            nblk += __popc(m[j]);
+        }
+        const int nbatch = nblk > 0 ? (nblk + kSlots - 1) / kSlots : 1;
+        for (int kb = 0; kb < nbatch; ++kb) {
+            for (int i = bt; i < kSlots * kBlk * kGroup / 4; i += 128)
+                reinterpret_cast<int4 *>(s->u.acc)[i] = make_int4(0, 0, 0, 0);
+            builders_sync();
+            // pass 2: fixed-point charge of the blocks of this batch
+            for (int k0 = bt; k0 < R; k0 += U * 128) {
+                int4 h[U];
+                float w[U];
+                int px[U];
+#pragma unroll
+                for (int j = 0; j < U; ++j) {
+                    const int k = k0 + j * 128;
+                    h[j] = make_int4(0, 0, 0, 0);
+                    w[j] = 0.f;
+                    px[j] = 0;
+                    if (k < R) {
+                        const int L = find_list(s->lst_off, k);
+                        const Rec *r = sorted + s->lst_beg[L] + (k - s->lst_off[L]);
+                        h[j] = *reinterpret_cast<const int4 *>(r);
+                        w[j] = reinterpret_cast<const float *>(&r->w)[L >> 5];
+                        px[j] = L & 31;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < U; ++j) {
+                    const float f = __int_as_float(h[j].z);
+#pragma unroll
+                    for (int tap = 0; tap < 2; ++tap) {
+                        const float val = tap ? f * w[j] : (1.f - f) * w[j];
+                        const int rel = h[j].x + tap;
+                        const int rb = rel >> 4;
+                        if (val == 0.f || rb < 0 || rb >= 256) continue;
+                        const int wd = rb >> 5, bit = rb & 31;
+                        const int rank = pw[wd] + __popc(m[wd] & ((1u << bit) - 1u));
+                        if ((rank >> 4) != kb) continue;
+                        atomicAdd(&s->u.acc[((rank & (kSlots - 1)) * kBlk + (rel & (kBlk - 1))) * kGroup + px[j]],
+                                  __float2int_rn(val * kFix));
+                    }
+                }
+            }
+            builders_sync();
+            const int st = q & 1;
+            if (q >= 2) bar_wait(s, &s->empty_b[st], ((q - 2) >> 1) & 1);   // on failure: abort set, go on
+            const int count = min(kSlots, nblk - kb * kSlots);
+            unsigned char *dst = s->bst[st];
+            // one 16-byte core-matrix row (8 ticks of one pixel) per step
+            for (int j = bt; j < count * kGroup * 2; j += 128) {
+                const int sl = j >> 6, p = j & (kGroup - 1), h = (j >> 5) & 1;
+                const int *ac = s->u.acc + (sl * kBlk + 8 * h) * kGroup + p;
+                uint4 v;
+                v.x = pack2<FMT>((float)ac[0 * kGroup] * a.qscale, (float)ac[1 * kGroup] * a.qscale);
+                v.y = pack2<FMT>((float)ac[2 * kGroup] * a.qscale, (float)ac[3 * kGroup] * a.qscale);
+                v.z = pack2<FMT>((float)ac[4 * kGroup] * a.qscale, (float)ac[5 * kGroup] * a.qscale);
+                v.w = pack2<FMT>((float)ac[6 * kGroup] * a.qscale, (float)ac[7 * kGroup] * a.qscale);
+                *reinterpret_cast<uint4 *>(dst + sl * 1024 + core_off(p, 8 * h)) = v;
+            }
+            if (bt < count) {
+                // block of slot kb * kSlots + bt: its set bit
+                const int want = kb * kSlots + bt;
+                int j = 0;
+                while (j < 7 && pw[j + 1] <= want) ++j;
+                uint32_t xm = m[j];
+                for (int z = want - pw[j]; z > 0; --z) xm &= xm - 1u;
+                s->meta[st].blk[bt] = (unsigned char)(j * 32 + __ffs(xm) - 1);
+            }
+            if (bt == 0) {
+                s->meta[st].node = n;
+                s->meta[st].count = count > 0 ? count : 0;
+                s->meta[st].last = (kb == nbatch - 1);
+            }
+            fence_async_smem();
+            builders_sync();
+            if (bt == 0) bar_arrive(&s->full_b[st]);
+            ++q;
+        }
+    }
+}
+
+// Issuer thread of warp w (0-3): MMAs of tiles t = w, w + 4, ... for every batch.
+__device__ void issue_mmas(const TcArgs &a, TcSmem *s, int w, const unsigned short *nodes, int nn, uint32_t S,
+                           uint32_t &q, int k0, unsigned long long &n_mma)
+{
+    const int T = a.c.n_ticks;
+    const uint32_t tm = s->taddr;
+    tc_fence_after();
+    auto load_im = [&](uint32_t sn, int node) {
+        const int b = sn & 1;
+        if (sn >= 2 && !bar_wait(s, &s->empty_im[b], ((sn - 2) >> 1) & 1)) return;
+        bulk_load(s->im[b], a.table + (size_t)node * a.im_bytes, (uint32_t)a.im_bytes, &s->full_im[b]);
+    };
+    if (w == 0 && nn > 0) load_im(S, nodes[0]);
+    for (int u = 0; u < nn; ++u) {
+        const uint32_t sn = S + u;
+        const int ib = sn & 1;
+        if (!bar_wait(s, &s->full_im[ib], (sn >> 1) & 1)) return;
+        const uint32_t im0 = saddr(s->im[ib]);
+        int last = 0;
+        do {
+            const int st = q & 1;
+            if (!bar_wait(s, &s->full_b[st], (q >> 1) & 1)) return;
+            const int count = s->meta[st].count;
+            last = s->meta[st].last;
+            const uint32_t b0 = saddr(s->bst[st]);
+            tc_fence_after();
+            for (int t = w; t < kTiles; t += kIssuers) {
+                if (k0 + kTileM * t >= T) break;
+                const uint32_t d = tm + (uint32_t)(kGroup * t);
+                for (int i = 0; i < count; ++i) {
+                    const int delta = kTileM * t - kBlk * (int)s->meta[st].blk[i];
+                    if (delta > 0 || delta < -a.rho0) continue;     // the A tile is all zero
+                    const uint32_t arow = (uint32_t)(delta + a.rho0);
+                    mma_f16(d, smem_desc(im0 + (arow >> 3) * 256, 128, 256), smem_desc(b0 + i * 1024, 128, 256),
+                            a.idesc);
+                    ++n_mma;
+                }
+            }
+            mma_commit(&s->empty_b[st]);
+            ++q;
+        } while (!last);
+        mma_commit(&s->empty_im[ib]);
+        if (w == 0 && u + 1 < nn) load_im(sn + 1, nodes[u + 1]);
+    }
+}
+
+
+// ------------------------------------------------------ work planning ----
+// Pixel groups are cut into sub-groups of balanced work: the work of a pixel
+// is estimated by its candidate points sum_{s -> p} N_s M; a 32-pixel group
+// is split into k (a power of two <= 32) sub-groups of 32 / k pixels so that
+// each holds at most total / (kSubsPerSm * SMs); sub-groups are then taken
+// in order of decreasing work.
+
+__device__ __forceinline__ int64_t active_count(const int64_t *counts, int64_t pix_cap)
+{
+    return (counts[3] == 0 && counts[1] <= pix_cap) ? counts[1] : 0;
+}
+
+__global__ void k_plan_work(const int64_t *counts, int64_t pix_cap, const int32_t *off, const int32_t *segs,
+                            const int32_t *n_samples, int M, long long *pwork, unsigned long long *total)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t npix = active_count(counts, pix_cap);
+    long long w = 0;
+    if (p < npix) {
+        for (int e = off[p]; e < off[p + 1]; ++e) w += n_samples[segs[e]];
+        w *= M;
+        pwork[p] = w;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+    if ((threadIdx.x & 31) == 0 && w) atomicAdd(total, (unsigned long long)w);
+}
+
+__global__ void k_plan_split(const int64_t *counts, int64_t pix_cap, const long long *pwork,
+                             const unsigned long long *total, int target, int32_t *nsub, int64_t ngroups_cap)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ngroups_cap) return;
+    const int64_t npix = active_count(counts, pix_cap);
+    int k = 0;
+    if (g * kGroup < npix) {
+        long long gw = 0;
+        for (int64_t p = g * kGroup; p < min(npix, (g + 1) * kGroup); ++p) gw += pwork[p];
+        const long long wcap = max(1ll, (long long)(*total / (unsigned long long)target));
+        k = 1;
+        while (k < kGroup && gw > wcap * k) k <<= 1;
+    }
+    nsub[g] = k;
+}
+
+__global__ void k_plan_emit(const int64_t *counts, int64_t pix_cap, const long long *pwork, const int32_t *nsub,
+                            const int32_t *pos, int4 *subs, int64_t ngroups_cap)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ngroups_cap) return;
+    const int k = nsub[g];
+    if (k == 0) return;
+    const int64_t npix = active_count(counts, pix_cap);
+    const int size = kGroup / k;
+    for (int j = 0; j < k; ++j) {
+        const int64_t first = g * kGroup + (int64_t)j * size;
+        const int cnt = (int)max((int64_t)0, min((int64_t)size, npix - first));
+        long long w = 0;
+        for (int i = 0; i < cnt; ++i) w += pwork[first + i];
+        subs[pos[g] + j] = make_int4((int)first, cnt, (int)(w & 0xffffffffll), (int)(w >> 32));
+    }
+}
+
+__device__ __forceinline__ long long sub_work(const int4 &v)
+{
+    return (long long)(((unsigned long long)(unsigned)v.w << 32) | (unsigned)v.z);
+}
+
+// order[rank] = j, rank by decreasing work, ties by index.
+__global__ void k_plan_rank(const int4 *subs, const int64_t *n_subs, int32_t *order)
+{
+    __shared__ long long tile[1024];
+    const int64_t n = *n_subs;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long wj = j < n ? sub_work(subs[j]) : 0;
+    int rank = 0;
+    for (int64_t t0 = 0; t0 < n; t0 += 1024) {
+        for (int i = threadIdx.x; i < 1024; i += blockDim.x) tile[i] = t0 + i < n ? sub_work(subs[t0 + i]) : 0;
+        __syncthreads();
+        if (j < n) {
+            const int m = (int)min((int64_t)1024, n - t0);
+            for (int i = 0; i < m; ++i) {
+                const long long wi = tile[i];
+                rank += (wi > wj) || (wi == wj && t0 + i < j);
+            }
+        }
+        __syncthreads();
+    }
+    if (j < n) order[rank] = (int32_t)j;
+}
+
+// Warps 0-3 (all lanes): waits for every MMA issued so far, adds the
+// accumulators to the current rows of the group (stores them when `first`),
+// and zeroes them.  The tensor cores' FP32 accumulation truncates: summing a
+// whole pixel's contributions in one accumulator biased the result low by up
+// to ~2e-3 in the densest pixels; a window of kFlushNodes nodes keeps each
+// accumulator a small fraction of the final value, and the windows are added
+// in FP32 with round-to-nearest.
+__device__ void flush_acc(const TcArgs &a, TcSmem *s, uint32_t tm, uint32_t &flushes, int k0, int64_t pi0, int npg,
+                          bool first)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int T = a.c.n_ticks;
+    if (lane == 0) mma_commit(&s->done);
+    __syncwarp();
+    const bool ok = bar_wait(s, &s->done, flushes & 1);
+    tc_fence_after();
+    for (int t = 0; t < kTiles; ++t) {
+        const int tick0 = k0 + kTileM * t;
+        if (tick0 >= T) break;
+        const uint32_t ta = tm + ((uint32_t)(32 * warp) << 16) + kGroup * t;
+        float v[32];
+        tmem_ld32(ta, v);
+        const int tick = tick0 + 32 * warp + lane;
+        if (ok && tick < T) {
+#pragma unroll
+            for (int p = 0; p < kGroup; ++p) {
+                if (p < npg) {
+                    float *dst = a.current + (size_t)(pi0 + p) * T + tick;
+                    *dst = first ? v[p] * a.out_scale : *dst + v[p] * a.out_scale;
+                }
+            }
+        }
+        tmem_zero32(ta);
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    tc_fence_before();
+    ++flushes;
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(kThreads, 1) k_induced_current_tc(TcArgs a)
+{
+    extern __shared__ unsigned char smem_raw[];
+    TcSmem *s = reinterpret_cast<TcSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool go = a.counts[3] == 0 && a.counts[1] <= a.pix_cap;
+    const int64_t nsub = go ? *a.n_subs : 0;
+    const int T = a.c.n_ticks, nb2 = a.nb * a.nb;
+    Rec *recs = a.recs + (size_t)blockIdx.x * kRecCap;
+    Rec *sorted = a.sorted + (size_t)blockIdx.x * kRecCap;
+    int *offt = a.offt + (size_t)blockIdx.x * kGroup * (kMaxBins + 1);
+
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            bar_init(&s->full_im[i], 1);
+            bar_init(&s->empty_im[i], kIssuers);
+            bar_init(&s->full_b[i], 1);
+            bar_init(&s->empty_b[i], kIssuers);
+        }
+        bar_init(&s->done, kIssuers);
+        s->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s->taddr)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tm = s->taddr;
+    if (warp < 4) {
+        for (int t = 0; t < kTiles; ++t) tmem_zero32(tm + ((uint32_t)(32 * warp) << 16) + kGroup * t);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+
+    uint32_t S = 0, q = 0, flushes = 0;     // node, batch and flush sequence numbers (barrier phases)
+    unsigned long long n_mma = 0;           // MMAs issued by this thread
+    for (;;) {
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) s->group = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int64_t g = s->group;
+        if (g >= nsub || *(volatile int *)&s->abort) break;
+        const int4 sub = a.subs[a.order[g]];
+        const int64_t pi0 = sub.x;
+        const int npg = sub.y;
+        if (npg <= 0) continue;
+        for (int k0 = 0; k0 < T; k0 += kPassTicks) {
+            GenState st{0, -1, 0};
+            bool first = true;                  // no accumulator window stored yet in this pass
+            while (st.gp < npg) {
+                // ---- chunk: generate and sort records, list the nodes touched ----
+                for (int b = tid; b < nb2; b += kThreads) {
+                    s->u.g.hist[b] = 0;
+                    s->u.g.nflag[b] = 0;
+                }
+                if (tid < kGroup) s->pin[tid] = 0;
+                __syncthreads();
+                // records keep arrival ticks relative to the pass start
+                const int nrec = gen_chunk(a, s, st, pi0, npg, recs, sorted, offt);
+                {
+                    constexpr int kB = kMaxBins / kThreads;
+                    int fl[kB], sf = 0;
+#pragma unroll
+                    for (int i = 0; i < kB; ++i) {
+                        const int b = tid * kB + i;
+                        fl[i] = (b < nb2 && nrec > 0) ? s->u.g.nflag[b] : 0;
+                        sf += fl[i];
+                    }
+                    int tot;
+                    int pf = block_scan(sf, s, &tot);
+#pragma unroll
+                    for (int i = 0; i < kB; ++i) {
+                        if (fl[i]) s->nodes[pf++] = (unsigned short)(tid * kB + i);
+                    }
+                    if (tid == 0) s->n_nodes = tot;
+                }
+                // shift arrival ticks to the pass start
+                if (k0 != 0)
+                    for (int i = tid; i < nrec; i += kThreads) sorted[i].A -= k0;
+                __syncthreads();
+                const int nn = s->n_nodes;
+                // ---- node windows: warps 0-3 issue, warps 4-7 build; then flush ----
+                for (int u0 = 0; u0 < nn; u0 += kFlushNodes) {
+                    const int cnt = min(kFlushNodes, nn - u0);
+                    if (warp >= 4) {
+                        build_batches<FMT>(a, s, sorted, offt, s->nodes + u0, cnt, q);
+                    } else if (lane == 0) {
+                        issue_mmas(a, s, warp, s->nodes + u0, cnt, S, q, k0, n_mma);
+                    }
+                    S += cnt;
+                    __syncthreads();
+                    if (warp < 4) {
+                        q = __shfl_sync(0xffffffffu, q, 0);   // the two roles agree unless a wait gave up
+                        flush_acc(a, s, tm, flushes, k0, pi0, npg, first);
+                    }
+                    first = false;
+                    __syncthreads();
+                }
+            }
+            // a pass without records still writes its (zero) currents
+            if (first) {
+                if (warp < 4) flush_acc(a, s, tm, flushes, k0, pi0, npg, true);
+                __syncthreads();
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && s->abort) atomicOr(a.status, (unsigned long long)SIM_STATUS_TIMEOUT);
+    if (warp < 4 && lane == 0 && n_mma) atomicAdd(a.status + 1, n_mma);
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kTmemCols) : "memory");
+    }
+}
+
+// im2col unfolding of the table rows, one 16-byte chunk (8 K values) per thread.
+template <int FMT>
+__global__ void k_im2col(const float *lut, int ld, int L, int nb2, int rho0, int rows, float scale,
+                         unsigned char *table)
+{
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (int64_t)nb2 * rows * 2) return;
+    const int n = (int)(id / (rows * 2));
+    const int rem = (int)(id - (int64_t)n * rows * 2);
+    const int rho = rem >> 1, h = rem & 1;
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int j = rho - rho0 - (8 * h + e) + L - 1;
+        v[e] = (j >= 0 && j < L) ? lut[(size_t)n * ld + j] * scale : 0.f;
+    }
+    uint4 o;
+    o.x = pack2<FMT>(v[0], v[1]);
+    o.y = pack2<FMT>(v[2], v[3]);
+    o.z = pack2<FMT>(v[4], v[5]);
+    o.w = pack2<FMT>(v[6], v[7]);
+    *reinterpret_cast<uint4 *>(table + (size_t)n * rows * kRowBytes + core_off(rho, 8 * h)) = o;
+}
+
+int tc_grid()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+int rho0_of(int L) { return 16 * ((L + 126) / 16); }
+
+struct TcLayout {
+    size_t queue, table, recs, sorted, offt, pwork, nsub, pos, subs, order, scan, total;
+};
+
+TcLayout tc_layout(int grid, int64_t pix_cap)
+{
+    TcLayout t;
+    size_t o = 0;
+    auto take = [&](size_t b) {
+        const size_t at = o;
+        o += align256(b);
+        return at;
+    };
+    const int64_t ng = (pix_cap + kGroup - 1) / kGroup;
+    t.queue = take(256);                    // [0] queue, [8] work total, [16] sub-group count
+    t.pwork = take(sizeof(long long) * (size_t)pix_cap);
+    t.nsub = take(sizeof(int32_t) * (size_t)ng);
+    t.pos = take(sizeof(int32_t) * (size_t)(ng + 1));
+    t.subs = take(sizeof(int4) * (size_t)ng * kGroup);
+    t.order = take(sizeof(int32_t) * (size_t)ng * kGroup);
+    t.scan = take(scan_scratch_bytes(ng));
+    t.table = take((size_t)kMaxBins * kMaxRows * kRowBytes);
+    t.recs = take((size_t)grid * kRecCap * sizeof(Rec));
+    t.sorted = take((size_t)grid * kRecCap * sizeof(Rec));
+    t.offt = take((size_t)grid * kGroup * (kMaxBins + 1) * sizeof(int));
+    t.total = o;
+    return t;
+}
+
+}  // namespace
+
+size_t current_tc_scratch_bytes(int64_t pix_cap) { return tc_layout(tc_grid(), pix_cap > 0 ? pix_cap : 1).total; }
+
+// Operand scales.  FP16: charge tiles in units of 4 e- (the fixed-point
+// quantum 2^-12 e- becomes 2^-14, the smallest normal FP16 number: the tensor
+// cores flush FP16 subnormals; cells above 262016 e- saturate) and table
+// values x 2^15 (rows are normalised to 1; values down to ~2e-9 stay normal),
+// products rescaled by 2^-13 when the accumulators are read.  BF16 has the
+// FP32 exponent range: no scaling.
+cudaError_t launch_induced_current_tc(const sim_config &c, const sim_segments &s, const sim_drifted &d,
+                                      const sim_response &r, const int32_t *active, const int32_t *pix_seg_off,
+                                      const int32_t *pix_seg_ids, const int64_t *counts, int64_t pix_cap,
+                                      float *current, void *scratch, cudaStream_t st)
+{
+    if (pix_cap <= 0) return cudaSuccess;
+    const int fmt = c.precision == 1 ? 1 : 0;      // 1: BF16, 2: FP16
+    const int grid = tc_grid();
+    const TcLayout lay = tc_layout(grid, pix_cap);
+    char *p = reinterpret_cast<char *>(scratch);
+    TcArgs a;
+    a.c = c;
+    a.nb = r.nb;
+    a.nt = r.nt;
+    a.bpp = r.bins_per_pitch;
+    a.rho0 = rho0_of(r.nt);
+    const int rows = a.rho0 + kTileM;
+    a.im_bytes = rows * kRowBytes;
+    a.idesc = instr_desc(fmt, kTileM, kGroup);
+    const float rscale = fmt == 0 ? 32768.f : 1.f, qunit = fmt == 0 ? 4.f : 1.f;
+    a.qscale = 1.f / (kFix * qunit);
+    a.out_scale = qunit / rscale;
+    a.table = reinterpret_cast<const unsigned char *>(p + lay.table);
+    a.anch = reinterpret_cast<const Anchor *>(d.anchors);
+    a.active = active;
+    a.off = pix_seg_off;
+    a.segs = pix_seg_ids;
+    a.counts = counts;
+    a.status = reinterpret_cast<unsigned long long *>(const_cast<int64_t *>(counts) + 3);
+    a.pix_cap = pix_cap;
+    a.current = current;
+    a.seed = c.seed;
+    a.ev = events_of(s);
+    a.g = geo_of(c);
+    a.queue = reinterpret_cast<int *>(p + lay.queue);
+    unsigned long long *wtotal = reinterpret_cast<unsigned long long *>(p + lay.queue + 8);
+    int64_t *n_subs = reinterpret_cast<int64_t *>(p + lay.queue + 16);
+    a.n_subs = n_subs;
+    a.subs = reinterpret_cast<const int4 *>(p + lay.subs);
+    a.order = reinterpret_cast<const int32_t *>(p + lay.order);
+    a.recs = reinterpret_cast<Rec *>(p + lay.recs);
+    a.sorted = reinterpret_cast<Rec *>(p + lay.sorted);
+    a.offt = reinterpret_cast<int *>(p + lay.offt);
+
+    cudaError_t e = cudaMemsetAsync(a.queue, 0, 24, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.status + 1, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    // work plan
+    const int64_t ng = (pix_cap + kGroup - 1) / kGroup;
+    long long *pwork = reinterpret_cast<long long *>(p + lay.pwork);
+    int32_t *nsub = reinterpret_cast<int32_t *>(p + lay.nsub);
+    int32_t *pos = reinterpret_cast<int32_t *>(p + lay.pos);
+    k_plan_work<<<(unsigned)((pix_cap + 255) / 256), 256, 0, st>>>(counts, pix_cap, pix_seg_off, pix_seg_ids,
+                                                                    d.n_samples, c.mc_per_sample, pwork, wtotal);
+    k_plan_split<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(counts, pix_cap, pwork, wtotal, kSubsPerSm * grid, nsub,
+                                                               ng);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = launch_exclusive_scan(nsub, pos, ng, n_subs, p + lay.scan, st);
+    if (e != cudaSuccess) return e;
+    k_plan_emit<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(counts, pix_cap, pwork, nsub, pos,
+                                                              reinterpret_cast<int4 *>(p + lay.subs), ng);
+    k_plan_rank<<<(unsigned)((ng * kGroup + 255) / 256), 256, 0, st>>>(a.subs, n_subs,
+                                                                      reinterpret_cast<int32_t *>(p + lay.order));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int nb2 = r.nb * r.nb;
+    const int64_t chunks = (int64_t)nb2 * rows * 2;
+    const unsigned blocks = (unsigned)((chunks + 255) / 256);
+    unsigned char *table = reinterpret_cast<unsigned char *>(p + lay.table);
+    if (fmt == 1) k_im2col<1><<<blocks, 256, 0, st>>>(r.lut, r.ld, r.nt, nb2, a.rho0, rows, rscale, table);
+    else k_im2col<0><<<blocks, 256, 0, st>>>(r.lut, r.ld, r.nt, nb2, a.rho0, rows, rscale, table);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = sizeof(TcSmem) + 1024;
+    auto kern = fmt == 1 ? k_induced_current_tc<1> : k_induced_current_tc<0>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace larsim
