@@ -66,7 +66,7 @@ constexpr int kIssuers = 4;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kMaxSpin = 1 << 22;           // bounded mbarrier waits (x ~ 0.5 us each)
 
-struct BatchMeta {
+struct __align__(16) BatchMeta {
     int node, count, last, pad;
     unsigned char blk[kSlots];              // block index relative to the pass start
 };
@@ -459,17 +459,21 @@ __device__ void build_batches(const TcArgs &a, TcSmem *s, const Rec *sorted, con
         s->lst_beg[bt] = beg;
         s->lst_off[bt] = pre + x - len;
         builders_sync();
+        // each builder takes a contiguous slice of the concatenated lists
+        const int k_lo = (R * bt) >> 7, k_hi = (R * (bt + 1)) >> 7;
+        const int L_lo = k_lo < k_hi ? find_list(s->lst_off, k_lo) : 0;
         // pass 1: blocks present in this pass's window (arrival ticks are relative to the pass start)
-        for (int k0 = bt; k0 < R; k0 += U * 128) {
+        int L = L_lo;
+        for (int k0 = k_lo; k0 < k_hi; k0 += U) {
             int4 h[U];
             float w[U];
 #pragma unroll
             for (int j = 0; j < U; ++j) {
-                const int k = k0 + j * 128;
+                const int k = k0 + j;
                 h[j] = make_int4(0, 0, 0, 0);
                 w[j] = 0.f;
-                if (k < R) {
-                    const int L = find_list(s->lst_off, k);
+                if (k < k_hi) {
+                    while (L < 127 && s->lst_off[L + 1] <= k) ++L;
                     const Rec *r = sorted + s->lst_beg[L] + (k - s->lst_off[L]);
                     h[j] = *reinterpret_cast<const int4 *>(r);
                     w[j] = reinterpret_cast<const float *>(&r->w)[L >> 5];
@@ -501,18 +505,20 @@ __device__ void build_batches(const TcArgs &a, TcSmem *s, const Rec *sorted, con
                 reinterpret_cast<int4 *>(s->u.acc)[i] = make_int4(0, 0, 0, 0);
             builders_sync();
             // pass 2: fixed-point charge of the blocks of this batch
-            for (int k0 = bt; k0 < R; k0 += U * 128) {
+            int L2 = L_lo;
+            for (int k0 = k_lo; k0 < k_hi; k0 += U) {
                 int4 h[U];
                 float w[U];
                 int px[U];
 #pragma unroll
                 for (int j = 0; j < U; ++j) {
-                    const int k = k0 + j * 128;
+                    const int k = k0 + j;
                     h[j] = make_int4(0, 0, 0, 0);
                     w[j] = 0.f;
                     px[j] = 0;
-                    if (k < R) {
-                        const int L = find_list(s->lst_off, k);
+                    if (k < k_hi) {
+                        while (L2 < 127 && s->lst_off[L2 + 1] <= k) ++L2;
+                        const int L = L2;
                         const Rec *r = sorted + s->lst_beg[L] + (k - s->lst_off[L]);
                         h[j] = *reinterpret_cast<const int4 *>(r);
                         w[j] = reinterpret_cast<const float *>(&r->w)[L >> 5];
@@ -598,20 +604,28 @@ __device__ void issue_mmas(const TcArgs &a, TcSmem *s, int w, const unsigned sho
             if (!bar_wait(s, &s->full_b[st], (q >> 1) & 1)) return;
             const int count = s->meta[st].count;
             last = s->meta[st].last;
-            const uint32_t b0 = saddr(s->bst[st]);
+            const uint4 bw = *reinterpret_cast<const uint4 *>(s->meta[st].blk);
+            const uint32_t b4[4] = {bw.x, bw.y, bw.z, bw.w};
+            // descriptors advance by address >> 4: one im2col row is 32 bytes, one slot 1024
+            const uint64_t ad0 = smem_desc(im0, 128, 256), bd0 = smem_desc(saddr(s->bst[st]), 128, 256);
             tc_fence_after();
+            uint32_t issued = 0;
             for (int t = w; t < kTiles; t += kIssuers) {
                 if (k0 + kTileM * t >= T) break;
                 const uint32_t d = tm + (uint32_t)(kGroup * t);
-                for (int i = 0; i < count; ++i) {
-                    const int delta = kTileM * t - kBlk * (int)s->meta[st].blk[i];
-                    if (delta > 0 || delta < -a.rho0) continue;     // the A tile is all zero
-                    const uint32_t arow = (uint32_t)(delta + a.rho0);
-                    mma_f16(d, smem_desc(im0 + (arow >> 3) * 256, 128, 256), smem_desc(b0 + i * 1024, 128, 256),
-                            a.idesc);
-                    ++n_mma;
+                const int base = kTileM * t + a.rho0;          // A row of block 0; block b: base - 16 b
+#pragma unroll
+                for (int i = 0; i < kSlots; ++i) {
+                    if (i < count) {
+                        const int arow = base - kBlk * (int)((b4[i >> 2] >> (8 * (i & 3))) & 0xffu);
+                        if (arow >= 0 && arow <= a.rho0) {        // otherwise the A tile is all zero
+                            mma_f16(d, ad0 + (uint64_t)(2 * arow), bd0 + (uint64_t)(64 * i), a.idesc);
+                            ++issued;
+                        }
+                    }
                 }
             }
+            n_mma += issued;
             mma_commit(&s->empty_b[st]);
             ++q;
         } while (!last);
@@ -718,7 +732,7 @@ __global__ void k_plan_rank(const int4 *subs, const int64_t *n_subs, int32_t *or
 // whole pixel's contributions in one accumulator biased the result low by up
 // to ~2e-3 in the densest pixels; a window of kFlushNodes nodes keeps each
 // accumulator a small fraction of the final value, and the windows are added
-// in FP32 with round-to-nearest.
+// in FP32 with round-to-nearest (one FMA per window).
 __device__ void flush_acc(const TcArgs &a, TcSmem *s, uint32_t tm, uint32_t &flushes, int k0, int64_t pi0, int npg,
                           bool first)
 {
@@ -736,13 +750,20 @@ __device__ void flush_acc(const TcArgs &a, TcSmem *s, uint32_t tm, uint32_t &flu
         tmem_ld32(ta, v);
         const int tick = tick0 + 32 * warp + lane;
         if (ok && tick < T) {
+            float *base = a.current + (size_t)pi0 * T + tick;
+            if (!first) {
+                float old[kGroup];                  // all loads in flight before the stores
 #pragma unroll
-            for (int p = 0; p < kGroup; ++p) {
-                if (p < npg) {
-                    float *dst = a.current + (size_t)(pi0 + p) * T + tick;
-                    *dst = first ? v[p] * a.out_scale : *dst + v[p] * a.out_scale;
-                }
+                for (int p = 0; p < kGroup; ++p) old[p] = p < npg ? base[(size_t)p * T] : 0.f;
+#pragma unroll
+                for (int p = 0; p < kGroup; ++p) v[p] = fmaf(v[p], a.out_scale, old[p]);
+            } else {
+#pragma unroll
+                for (int p = 0; p < kGroup; ++p) v[p] *= a.out_scale;
             }
+#pragma unroll
+            for (int p = 0; p < kGroup; ++p)
+                if (p < npg) base[(size_t)p * T] = v[p];
         }
         tmem_zero32(ta);
     }
