@@ -31,7 +31,9 @@ sys.path.insert(0, ROOT)
 
 from synth import events, params, response  # noqa: E402
 
-KERNELS_PER_STEP = 22     # 1 quench/drift + 14 pixel map + 1 current + 6 electronics
+# kernels per step: 1 quench/drift + 14 pixel map + 6 electronics, plus the induced current:
+# 1 (FP32 direct) or 9 (tensor cores: work plan 4 + a 3-kernel scan, table unfolding 1, contraction 1)
+KERNELS_PER_STEP = {0: 22, 1: 30, 2: 30}
 FP32_LANES_PER_SM = 128
 
 
@@ -44,8 +46,9 @@ def parse():
     ap.add_argument("--workload", choices=["module", "tile", "spill"], default="module")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--precision", type=int, choices=[0, 1, 2], default=0,
-                    help="induced-current form: 0 FP32 direct, 1 BF16 / 2 FP16 tensor cores")
+    ap.add_argument("--precision", type=int, choices=[0, 1, 2], default=2,
+                    help="induced-current form of the headline: 0 FP32 direct, 1 BF16 / 2 FP16 tensor cores")
+    ap.add_argument("--no-forms", action="store_true", help="skip timing the other induced-current forms")
     return ap.parse_args()
 
 
@@ -249,29 +252,21 @@ def batched_vs_plain(cfg, lut, dev, n_events=32, lo=1.0e3, hi=1.0e4, reps=2):
 
 
 
-def run_ours(args):
+FORMS = {0: ("fp32_direct", "f32"), 1: ("bf16_tensor", "bf16"), 2: ("fp16_tensor", "f16")}
+
+
+def time_form(cfg, seg, lut, dev, precision, steps, warmup, rank):
+    """Times `steps` whole-path steps (the four entry points, one by one, each
+    bracketed by CUDA events on the current stream) with the induced-current
+    form `precision`, after `warmup` untimed steps and with L2 flushed before
+    every step.  Returns (runner, per-step-and-entry ms array, counts)."""
     import torch
     from paper_2212_09807_gb300 import sim
-
-    world, rank, local = dist()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    pg = None
-    if world > 1:
-        import torch.distributed as tdist
-        tdist.init_process_group("nccl", device_id=dev)
-        pg = tdist
-    cfg, seg, desc = workload(args.workload)
-    cfg["precision"] = args.precision
+    cfg = dict(cfg, precision=precision)
     S = len(seg["x0"])
     T = int(cfg["n_ticks"])
-    lut64 = response.lut_for(cfg, params.LUT)
-    lut_pad = response.pad_rows(lut64)
-    lut = torch.as_tensor(lut_pad, device=dev)
-
-    # capacities: grow until the event fits (one untimed sizing pass)
     caps = [40 * S, 4 * S, 4 * S]
-    while True:
+    while True:                         # capacities: grow until the event fits (untimed sizing pass)
         run = sim.EventRunner(cfg, lut, params.LUT["nt"], params.LUT["bins_per_pitch"], S, *caps, device=dev)
         segs = sim.Segments.from_numpy(seg, event_id=rank, device=dev)
         run.enqueue(segs)
@@ -282,8 +277,6 @@ def run_ours(args):
         caps = [max(caps[0], 2 * n_pairs), max(caps[1], 2 * n_pix), max(caps[2], 2 * n_hits)]
         del run
         torch.cuda.empty_cache()
-
-    # the same entry points sim_event calls, one by one, so that each step is timed
     v = run.view(S)
     A = sim._alias
     dr = sim.Drifted.wrap(v.dr)
@@ -310,31 +303,106 @@ def run_ours(args):
         evs[4].record()
 
     mk = lambda: [torch.cuda.Event(enable_timing=True) for _ in range(5)]  # noqa: E731
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         flush.zero_()
         step(mk())
     torch.cuda.synchronize()
-    n_pairs, n_pix, n_hits, status = run.counts()
-    assert status == 0
+    all_evs = []
+    for _ in range(steps):
+        flush.zero_()                  # outside the timed intervals: every step starts with a cold L2
+        e = mk()
+        step(e)
+        all_evs.append(e)
+    torch.cuda.synchronize()
+    per = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in all_evs])   # ms
+    counts_now = run.counts()
+    assert counts_now[3] == 0
+    run.segs = segs
+    return run, per, counts_now
+
+
+def form_roofline(run, cfg, precision, a4_s, props, sm_mhz, dev):
+    """Roofline of the induced-current kernel of one form: FP32 direct against
+    the FP32 FMA peak; tensor-core forms against the measured dense 16-bit
+    tensor peak (dense MMA work counted on the device), with the algorithmic
+    (useful) work also stated."""
+    import torch
+    from paper_2212_09807_gb300 import sim
+    S = run.max_segments
+    dn = run.view(S)
+    A = sim._alias
+    ns = A(dn.dr.n_samples, S, torch.int32, dev).cpu().numpy().astype(np.int64)
+    an = A(dn.dr.anode, S, torch.int32, dev).cpu().numpy()
+    samples = int(ns[an >= 0].sum()) * int(cfg["mc_per_sample"])
+    L = params.LUT["nt"]
+    w_alg = 2.0 * 9 * L * samples                       # flop per launch (9 pixels per point)
+    useful = w_alg / a4_s / 1e12
+    if precision == 0:
+        peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+        return {"bound": "alu", "achieved": useful, "peak": peak, "unit": "TFLOP/s", "frac": useful / peak,
+                "traffic": stored_traffic("induced_current.cu"), "kernel": "k_induced_current",
+                "peak_note": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz",
+                "work_note": "2 flop x 9 pixels x 1950 table ticks per (point, perturbation)"}, samples
+    n_mma = int(run.ws[4].item())
+    dense = 2.0 * 128 * 32 * 16 * n_mma / a4_s / 1e12
+    tpk = measured_peaks().get("bf16_tflops") or 1900.0
+    return {"bound": "tensor", "achieved": dense, "peak": tpk, "unit": "TFLOP/s", "frac": dense / tpk,
+            "traffic": stored_traffic("induced_current_tc.cu"), "kernel": "k_induced_current_tc",
+            "mma_per_launch": n_mma, "useful_achieved": useful, "useful_frac": useful / tpk,
+            "peak_note": "measured dense bf16 burst, of measured (fp16 has the same nominal rate)",
+            "work_note": "dense: 2 x 128 x 32 x 16 flop per MMA; useful: 2 flop x 9 pixels x 1950 "
+                         "table ticks per (point, perturbation)"}, samples
+
+
+def run_ours(args):
+    import torch
+    from paper_2212_09807_gb300 import sim
+
+    world, rank, local = dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=dev)
+        pg = tdist
+    cfg, seg, desc = workload(args.workload)
+    cfg["precision"] = args.precision
+    S = len(seg["x0"])
+    T = int(cfg["n_ticks"])
+    L = params.LUT["nt"]
+    lut64 = response.lut_for(cfg, params.LUT)
+    lut_pad = response.pad_rows(lut64)
+    lut = torch.as_tensor(lut_pad, device=dev)
+    props = torch.cuda.get_device_properties(dev)
+
+    # the other forms of the induced-current step, timed on the same event first (untimed for the headline)
+    forms = {}
+    if not args.no_forms:
+        for prec in (0, 1, 2):
+            if prec == args.precision:
+                continue
+            r2, per2, c2 = time_form(cfg, seg, lut, dev, prec, max(3, args.steps // 2), args.warmup, rank)
+            sm_max = measured_peaks().get("sm_max_mhz", 2070.0)
+            rl, _ = form_roofline(r2, cfg, prec, float(per2[:, 2].mean()) / 1e3, props, sm_max, dev)
+            forms[FORMS[prec][0]] = {"dtype": FORMS[prec][1], "ms_per_step": float(per2.sum(axis=1).mean()),
+                                     "segments_per_s": S / (float(per2.sum(axis=1).mean()) / 1e3),
+                                     "induced_current_ms": float(per2[:, 2].mean()), "roofline": rl}
+            del r2
+            torch.cuda.empty_cache()
+
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
-    props = torch.cuda.get_device_properties(dev)
     gpu_id = str(getattr(props, "uuid", local))
     if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) > 8:
         gpu_id = "GPU-" + gpu_id
     clk = ClockSampler(gpu_id)
     clk.start()
     time.sleep(0.15)
-    all_evs = []
-    for _ in range(args.steps):
-        flush.zero_()                  # outside the timed intervals: every step starts with a cold L2
-        e = mk()
-        step(e)
-        all_evs.append(e)
-    torch.cuda.synchronize()
+    run, per, (n_pairs, n_pix, n_hits, status) = time_form(cfg, seg, lut, dev, args.precision, args.steps,
+                                                           args.warmup, rank)
     clocks = clk.stop()
-    per = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in all_evs])   # ms
     step_ms = per.sum(axis=1)
     total_ms = float(step_ms.sum())
     if pg:
@@ -344,34 +412,11 @@ def run_ours(args):
     value = world * S * args.steps / (total_ms / 1e3)
     a45_ms = float(per[:, 2:].sum())
     pix_ticks = world * n_pix * T * args.steps / (a45_ms / 1e3)
-
-    # roofline of the dominant kernel (induced current)
-    dn = run.view(S)
-    ns = A(dn.dr.n_samples, S, torch.int32, dev).cpu().numpy().astype(np.int64)
-    an = A(dn.dr.anode, S, torch.int32, dev).cpu().numpy()
-    samples = int(ns[an >= 0].sum()) * int(cfg["mc_per_sample"])
-    L = params.LUT["nt"]
-    w_alg = 2.0 * 9 * L * samples                       # flop per launch (9 pixels per point)
-    a4_s = float(per[:, 2].mean()) / 1e3
-    achieved = w_alg / a4_s / 1e12
     sm_mhz = clocks.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
-    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": stored_traffic("induced_current.cu"), "kernel": "k_induced_current",
-                "peak_note": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz",
-                "work_note": "2 flop x 9 pixels x 1950 table ticks per (point, perturbation)"}
-    if args.precision:
-        # tensor-core form: dense MMA work of the launch (counted on the device) against the
-        # measured dense 16-bit tensor peak; the algorithmic work above is kept as useful_frac
-        n_mma = int(run.ws[4].item())
-        dense = 2.0 * 128 * 32 * 16 * n_mma / a4_s / 1e12
-        tpk = measured_peaks().get("bf16_tflops") or 1900.0
-        roofline = {"bound": "tensor", "achieved": dense, "peak": tpk, "unit": "TFLOP/s", "frac": dense / tpk,
-                    "traffic": stored_traffic("induced_current_tc.cu"), "kernel": "k_induced_current_tc",
-                    "mma_per_launch": n_mma, "useful_achieved": achieved, "useful_frac": achieved / tpk,
-                    "peak_note": "measured dense bf16 burst (fp16 has the same nominal rate)",
-                    "work_note": "dense: 2 x 128 x 32 x 16 flop per MMA; useful: 2 flop x 9 pixels x 1950 "
-                                 "table ticks per (point, perturbation)"}
+    roofline, samples = form_roofline(run, cfg, args.precision, float(per[:, 2].mean()) / 1e3, props, sm_mhz, dev)
+    forms[FORMS[args.precision][0]] = {"dtype": FORMS[args.precision][1], "ms_per_step": total_ms / args.steps,
+                                       "segments_per_s": value / world,
+                                       "induced_current_ms": float(per[:, 2].mean()), "roofline": roofline}
 
     # end to end through the public API: pinned host segments in, hits out
     io = sim.EventIO(run)
@@ -393,6 +438,8 @@ def run_ours(args):
         e2e_s = float(t.item())
     e2e = {"value": world * S * args.steps / e2e_s, "unit": "segments/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
+    del run, io
+    torch.cuda.empty_cache()
 
     batched = batched_vs_plain(cfg, lut, dev) if not args.no_batched else None
 
@@ -406,18 +453,19 @@ def run_ours(args):
         print(json.dumps({
             "metric": "segments/s", "value": value, "unit": "segments/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": ["f32", "bf16", "f16"][args.precision],
-            "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": FORMS[args.precision][1], "data": "synthetic",
             "config": {"workload": desc, "segments": S, "active_pixels": n_pix, "pairs": n_pairs,
                        "hits": n_hits, "n_ticks": T, "points": samples, "parallelism": f"replicas{world}",
+                       "induced_current_form": FORMS[args.precision][0] + " (FP32 accumulation)",
                        "l2": "flushed (256 MB write) before every timed step"},
             "pixel_ticks_per_s": pix_ticks,
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "step_breakdown_ms": {"quench_drift": float(per[:, 0].mean()), "pixel_map": float(per[:, 1].mean()),
                                   "induced_current": float(per[:, 2].mean()),
                                   "electronics": float(per[:, 3].mean())},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,
-            "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clocks,
+            "roofline": roofline, "forms": forms, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,
+            "gpu_launches": KERNELS_PER_STEP[args.precision] * args.steps, "clocks": clocks,
         }))
     if pg:
         pg.destroy_process_group()

@@ -58,3 +58,25 @@ def test_batch_rejects_inconsistent_arguments():
     with pytest.raises(sim.SimError) as err:
         run.enqueue(segs)
     assert err.value.code == -1
+
+
+def test_batch_tensor_core_form_matches_events_alone():
+    """The FP16 tensor-core form in a batch: same active pixels; currents equal
+    to the event alone up to the accumulation rounding (pixel groups, hence
+    the 64-node accumulation windows, differ between the two runs)."""
+    cfg = params.small_config(precision=2)
+    lut_dev, _ = lut_pair(cfg)
+    evs = [events.scatter_event(cfg, 60 + i, n, max_len=0.7) for i, n in enumerate((40, 3, 25))]
+    ids = [21, 8, 77]
+    det_px = params.geometry(cfg)["n_pixels"]
+    alone = [_run(cfg, lut_dev, sim.Segments.from_numpy(e, i), max(1, len(e["x0"]))) for e, i in zip(evs, ids)]
+    batch = sim.Segments.batch_from_numpy(evs, ids)
+    act, cur, _ = _run(cfg, lut_dev, batch, batch.n, max_events=len(evs))
+    slot = act // det_px
+    worst = 0.0
+    for e, (a1, c1, _) in enumerate(alone):
+        m = slot == e
+        assert np.array_equal(act[m] - e * det_px, a1)
+        scale = np.maximum(np.abs(c1).max(axis=1, keepdims=True), 1e-30)
+        worst = max(worst, float((np.abs(cur[m] - c1) / scale).max()))
+    assert worst <= 1e-5, worst
