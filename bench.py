@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--precision", type=int, choices=[0, 1, 2], default=2,
                     help="induced-current form of the headline: 0 FP32 direct, 1 BF16 / 2 FP16 tensor cores")
     ap.add_argument("--no-forms", action="store_true", help="skip timing the other induced-current forms")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-vs-plain request stream")
+    ap.add_argument("--serving-requests", type=int, default=12)
     return ap.parse_args()
 
 
@@ -354,6 +356,50 @@ def form_roofline(run, cfg, precision, a4_s, props, sm_mhz, dev):
                          "table ticks per (point, perturbation)"}, samples
 
 
+SLICE = 32768        # active pixels per current launch of a large request (serving form)
+
+
+def serving_vs_plain(precision, dev, n_requests=12, load=0.7, seed_off=20):
+    """Serving form against the plain per-event form on the same Poisson
+    request stream: 80 % single interactions (~2e4 segments) and 20 % whole
+    spills (~1.2e6 segments) on the 35-module detector; the arrival rate is
+    `load` times the plain form's capacity (measured on one request of each
+    kind first)."""
+    import torch
+    from paper_2212_09807_gb300 import serve
+    cfg = params.spill_config(precision=precision)
+    lut = torch.as_tensor(response.pad_rows(response.lut_for(cfg, params.LUT)), device=dev)
+    nt, bpp = params.LUT["nt"], params.LUT["bins_per_pitch"]
+    seed = params.BASE["seed"] + seed_off
+    inter = [events.module_event(cfg, seed + i) for i in range(4)]
+    spill = events.spill_event(cfg, seed + 9)
+    # service times of the plain form, one request of each kind (after a warm-up one)
+    probe = [serve.Request(0, 1, inter[0], 0.0, "interaction"), serve.Request(1, 2, inter[1], 0.0, "interaction"),
+             serve.Request(2, 3, spill, 0.0, "spill")]
+    res = serve.run_plain(cfg, lut, nt, bpp, probe, device=dev)
+    t_int = res[1].done - res[1].admitted
+    t_sp = res[2].done - res[2].admitted
+    mean_service = 0.8 * t_int + 0.2 * t_sp
+    rate = load / mean_service
+    rng = np.random.default_rng(seed)
+    t, reqs = 0.0, []
+    for i in range(n_requests):
+        t += rng.exponential(1.0 / rate)
+        if rng.random() < 0.2:
+            reqs.append(serve.Request(i, 5000 + i, spill, t, "spill"))
+        else:
+            reqs.append(serve.Request(i, 5000 + i, inter[i % len(inter)], t, "interaction"))
+    plain = serve.summarize(serve.run_plain(cfg, lut, nt, bpp, reqs, device=dev))
+    torch.cuda.empty_cache()
+    srv = serve.Server(cfg, lut, nt, bpp, hbm_budget=120e9, slice_pixels=SLICE, max_jobs=8, device=dev)
+    serving = serve.summarize(srv.run(reqs))
+    torch.cuda.empty_cache()
+    return {"requests": n_requests, "mix": "80% interactions (~2e4 segments), 20% spills (~1.2e6 segments), "
+            "35-module detector", "load": load, "rate_per_s": rate,
+            "plain_service_ms": {"interaction": t_int * 1e3, "spill": t_sp * 1e3},
+            "hbm_budget_gb": 120, "slice_pixels": SLICE, "plain": plain, "serving": serving}
+
+
 def run_ours(args):
     import torch
     from paper_2212_09807_gb300 import sim
@@ -442,6 +488,7 @@ def run_ours(args):
     torch.cuda.empty_cache()
 
     batched = batched_vs_plain(cfg, lut, dev) if not args.no_batched else None
+    serving = serving_vs_plain(args.precision, dev, args.serving_requests) if not args.no_serving else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -465,6 +512,7 @@ def run_ours(args):
                                   "induced_current": float(per[:, 2].mean()),
                                   "electronics": float(per[:, 3].mean())},
             "roofline": roofline, "forms": forms, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,
+            "serving": serving,
             "gpu_launches": KERNELS_PER_STEP[args.precision] * args.steps, "clocks": clocks,
         }))
     if pg:

@@ -215,6 +215,21 @@ int sim_induced_current(const sim_config *cfg, const sim_segments *seg, const si
                         const int64_t *counts, int64_t pix_cap, float *current, void *ws,
                         size_t ws_bytes, void *stream);
 
+/* Step 4 on a slice of the active pixels: as sim_induced_current, but only the
+ * rows of active pixels [pix_begin, min(counts[1], pix_end)) are computed and
+ * written (rows are indexed by active-pixel index, as in the full call).  Each
+ * pixel's current is the same as the full call's: the FP32 form bit for bit,
+ * the tensor-core form up to its accumulation rounding (its pixel groups are
+ * formed within the slice).  Lets a caller cut a large event's current step
+ * into shorter launches (other streams' work interleaves between them).
+ * 0 <= pix_begin <= pix_end; an empty slice is a no-op. */
+int sim_induced_current_range(const sim_config *cfg, const sim_segments *seg, const sim_drifted *dr,
+                              const sim_response *resp, const int32_t *active_pixels,
+                              const int32_t *pix_seg_off, const int32_t *pix_seg_ids,
+                              const int64_t *counts, int64_t pix_begin, int64_t pix_end,
+                              int64_t pix_cap, float *current, void *ws, size_t ws_bytes,
+                              void *stream);
+
 /* Step 5 (Sec. 3.4): per active pixel, tick by tick, charge integration,
  * discriminator with uncorrelated and threshold noise, hold, 8-bit ADC and
  * reset with pedestal noise (Philox counters keyed by pixel id and tick).

@@ -77,11 +77,14 @@ size_t current_scratch(const sim_config &c, int64_t pixels)
 
 cudaError_t launch_current(const sim_config &c, const sim_segments &s, const sim_drifted &d, const sim_response &r,
                            const int32_t *active, const int32_t *off, const int32_t *ids, const int64_t *counts,
-                           int64_t pix_cap, float *current, void *scratch, cudaStream_t st)
+                           int64_t pix_cap, float *current, void *scratch, cudaStream_t st,
+                           int64_t pix_begin = 0, int64_t pix_end = INT64_MAX)
 {
     if (c.precision == 0)
-        return launch_induced_current(c, s, d, r, active, off, ids, counts, pix_cap, current, scratch, st);
-    return launch_induced_current_tc(c, s, d, r, active, off, ids, counts, pix_cap, current, scratch, st);
+        return launch_induced_current(c, s, d, r, active, off, ids, counts, pix_cap, pix_begin, pix_end, current,
+                                      scratch, st);
+    return launch_induced_current_tc(c, s, d, r, active, off, ids, counts, pix_cap, pix_begin, pix_end, current,
+                                     scratch, st);
 }
 
 // Layout of sim_event's workspace.
@@ -218,22 +221,33 @@ int sim_pixel_map(const sim_config *cfg, const sim_segments *seg, const sim_drif
     return e == cudaSuccess ? SIM_OK : cuda_fail(e);
 }
 
+int sim_induced_current_range(const sim_config *cfg, const sim_segments *seg, const sim_drifted *dr,
+                              const sim_response *resp, const int32_t *active_pixels, const int32_t *pix_seg_off,
+                              const int32_t *pix_seg_ids, const int64_t *counts, int64_t pix_begin,
+                              int64_t pix_end, int64_t pix_cap, float *current, void *ws, size_t ws_bytes,
+                              void *stream)
+{
+    if (!cfg_ok(cfg) || !seg_ok(seg) || !events_ok(cfg, seg) || !resp_ok(resp, true) || !counts || pix_cap < 0 ||
+        !ws || pix_begin < 0 || pix_end < pix_begin)
+        return SIM_ERR_INVALID_ARG;
+    if (pix_cap > 0 && (!active_pixels || !pix_seg_off || !pix_seg_ids || !current)) return SIM_ERR_INVALID_ARG;
+    if (pix_cap > 0 && seg->n > 0 && !drifted_ok(dr)) return SIM_ERR_INVALID_ARG;
+    if (pix_cap == 0 || pix_begin >= pix_cap || pix_end == pix_begin) return SIM_OK;
+    if (ws_bytes < 256 + current_scratch(*cfg, pix_cap)) return SIM_ERR_CAPACITY;
+    const sim_drifted d0 = dr ? *dr : sim_drifted{};
+    const cudaError_t e = launch_current(*cfg, *seg, d0, *resp, active_pixels, pix_seg_off, pix_seg_ids, counts,
+                                         pix_cap, current, reinterpret_cast<char *>(ws) + 256, (cudaStream_t)stream,
+                                         pix_begin, pix_end);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e);
+}
+
 int sim_induced_current(const sim_config *cfg, const sim_segments *seg, const sim_drifted *dr,
                         const sim_response *resp, const int32_t *active_pixels, const int32_t *pix_seg_off,
                         const int32_t *pix_seg_ids, const int64_t *counts, int64_t pix_cap, float *current,
                         void *ws, size_t ws_bytes, void *stream)
 {
-    if (!cfg_ok(cfg) || !seg_ok(seg) || !events_ok(cfg, seg) || !resp_ok(resp, true) || !counts || pix_cap < 0 ||
-        !ws)
-        return SIM_ERR_INVALID_ARG;
-    if (pix_cap > 0 && (!active_pixels || !pix_seg_off || !pix_seg_ids || !current)) return SIM_ERR_INVALID_ARG;
-    if (pix_cap > 0 && seg->n > 0 && !drifted_ok(dr)) return SIM_ERR_INVALID_ARG;
-    if (pix_cap == 0) return SIM_OK;
-    if (ws_bytes < 256 + current_scratch(*cfg, pix_cap)) return SIM_ERR_CAPACITY;
-    const sim_drifted d0 = dr ? *dr : sim_drifted{};
-    const cudaError_t e = launch_current(*cfg, *seg, d0, *resp, active_pixels, pix_seg_off, pix_seg_ids, counts,
-                                         pix_cap, current, reinterpret_cast<char *>(ws) + 256, (cudaStream_t)stream);
-    return e == cudaSuccess ? SIM_OK : cuda_fail(e);
+    return sim_induced_current_range(cfg, seg, dr, resp, active_pixels, pix_seg_off, pix_seg_ids, counts, 0,
+                                     INT64_MAX, pix_cap, current, ws, ws_bytes, stream);
 }
 
 int sim_electronics(const sim_config *cfg, const sim_segments *events, const int32_t *active_pixels,

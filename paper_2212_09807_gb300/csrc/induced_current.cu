@@ -58,7 +58,7 @@ struct CurArgs {
     const Anchor *anch;
     const int32_t *active, *off, *segs;
     const int64_t *counts;
-    int64_t pix_cap;
+    int64_t pix_cap, pix_begin, pix_end;        // active pixels [pix_begin, min(counts[1], pix_end))
     float *current;
     uint64_t seed;
     EventInfo ev;
@@ -177,8 +177,8 @@ __device__ __forceinline__ void apply_block(const Smem *s, int p1, int L, int la
 __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a)
 {
     if (a.counts[3] != 0) return;
-    const int64_t npix = a.counts[1];
-    if (npix > a.pix_cap) return;
+    const int64_t npix = min(a.counts[1], a.pix_end);
+    if (a.counts[1] > a.pix_cap) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem *s = reinterpret_cast<Smem *>(smem_raw);
 
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a)
     const int blo_tick = kHalf * warp;                            // first tick of my low block
     const int bhi_tick = kPass - kHalf * (warp + 1);              // first tick of my high block
 
-    for (int64_t pi = blockIdx.x; pi < npix; pi += gridDim.x) {
+    for (int64_t pi = a.pix_begin + blockIdx.x; pi < npix; pi += gridDim.x) {
         const int32_t pid = a.active[pi];
         const int an = pid / npx;
         const int rem = pid - an * npx;
@@ -365,8 +365,8 @@ bool current_table_ok(int nb, int nt) { return nb * nb <= kMaxBins && ((nt + 3) 
 cudaError_t launch_induced_current(const sim_config &c, const sim_segments &s, const sim_drifted &d,
                                    const sim_response &r, const int32_t *active,
                                    const int32_t *pix_seg_off, const int32_t *pix_seg_ids,
-                                   const int64_t *counts, int64_t pix_cap, float *current, void *scratch,
-                                   cudaStream_t st)
+                                   const int64_t *counts, int64_t pix_cap, int64_t pix_begin, int64_t pix_end,
+                                   float *current, void *scratch, cudaStream_t st)
 {
     if (pix_cap <= 0) return cudaSuccess;
     CurArgs a;
@@ -384,6 +384,8 @@ cudaError_t launch_induced_current(const sim_config &c, const sim_segments &s, c
     a.segs = pix_seg_ids;
     a.counts = counts;
     a.pix_cap = pix_cap;
+    a.pix_begin = pix_begin;
+    a.pix_end = pix_end;
     a.current = current;
     a.seed = c.seed;
     a.ev = events_of(s);

@@ -642,19 +642,22 @@ __device__ void issue_mmas(const TcArgs &a, TcSmem *s, int w, const unsigned sho
 // each holds at most total / (kSubsPerSm * SMs); sub-groups are then taken
 // in order of decreasing work.
 
-__device__ __forceinline__ int64_t active_count(const int64_t *counts, int64_t pix_cap)
+// Active pixels of the call's range [begin, min(counts[1], end)), counted from begin.
+__device__ __forceinline__ int64_t active_count(const int64_t *counts, int64_t pix_cap, int64_t begin, int64_t end)
 {
-    return (counts[3] == 0 && counts[1] <= pix_cap) ? counts[1] : 0;
+    if (counts[3] != 0 || counts[1] > pix_cap) return 0;
+    return max((int64_t)0, min(counts[1], end) - begin);
 }
 
-__global__ void k_plan_work(const int64_t *counts, int64_t pix_cap, const int32_t *off, const int32_t *segs,
+__global__ void k_plan_work(const int64_t *counts, int64_t pix_cap, int64_t begin, int64_t end, const int32_t *off,
+                            const int32_t *segs,
                             const int32_t *n_samples, int M, long long *pwork, unsigned long long *total)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t npix = active_count(counts, pix_cap);
+    const int64_t npix = active_count(counts, pix_cap, begin, end);
     long long w = 0;
     if (p < npix) {
-        for (int e = off[p]; e < off[p + 1]; ++e) w += n_samples[segs[e]];
+        for (int e = off[begin + p]; e < off[begin + p + 1]; ++e) w += n_samples[segs[e]];
         w *= M;
         pwork[p] = w;
     }
@@ -663,12 +666,12 @@ __global__ void k_plan_work(const int64_t *counts, int64_t pix_cap, const int32_
     if ((threadIdx.x & 31) == 0 && w) atomicAdd(total, (unsigned long long)w);
 }
 
-__global__ void k_plan_split(const int64_t *counts, int64_t pix_cap, const long long *pwork,
+__global__ void k_plan_split(const int64_t *counts, int64_t pix_cap, int64_t begin, int64_t end, const long long *pwork,
                              const unsigned long long *total, int target, int32_t *nsub, int64_t ngroups_cap)
 {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ngroups_cap) return;
-    const int64_t npix = active_count(counts, pix_cap);
+    const int64_t npix = active_count(counts, pix_cap, begin, end);
     int k = 0;
     if (g * kGroup < npix) {
         long long gw = 0;
@@ -680,21 +683,22 @@ __global__ void k_plan_split(const int64_t *counts, int64_t pix_cap, const long 
     nsub[g] = k;
 }
 
-__global__ void k_plan_emit(const int64_t *counts, int64_t pix_cap, const long long *pwork, const int32_t *nsub,
+__global__ void k_plan_emit(const int64_t *counts, int64_t pix_cap, int64_t begin, int64_t end, const long long *pwork,
+                            const int32_t *nsub,
                             const int32_t *pos, int4 *subs, int64_t ngroups_cap)
 {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ngroups_cap) return;
     const int k = nsub[g];
     if (k == 0) return;
-    const int64_t npix = active_count(counts, pix_cap);
+    const int64_t npix = active_count(counts, pix_cap, begin, end);
     const int size = kGroup / k;
     for (int j = 0; j < k; ++j) {
         const int64_t first = g * kGroup + (int64_t)j * size;
         const int cnt = (int)max((int64_t)0, min((int64_t)size, npix - first));
         long long w = 0;
         for (int i = 0; i < cnt; ++i) w += pwork[first + i];
-        subs[pos[g] + j] = make_int4((int)first, cnt, (int)(w & 0xffffffffll), (int)(w >> 32));
+        subs[pos[g] + j] = make_int4((int)(begin + first), cnt, (int)(w & 0xffffffffll), (int)(w >> 32));
     }
 }
 
@@ -971,7 +975,8 @@ size_t current_tc_scratch_bytes(int64_t pix_cap) { return tc_layout(tc_grid(), p
 cudaError_t launch_induced_current_tc(const sim_config &c, const sim_segments &s, const sim_drifted &d,
                                       const sim_response &r, const int32_t *active, const int32_t *pix_seg_off,
                                       const int32_t *pix_seg_ids, const int64_t *counts, int64_t pix_cap,
-                                      float *current, void *scratch, cudaStream_t st)
+                                      int64_t pix_begin, int64_t pix_end, float *current, void *scratch,
+                                      cudaStream_t st)
 {
     if (pix_cap <= 0) return cudaSuccess;
     const int fmt = c.precision == 1 ? 1 : 0;      // 1: BF16, 2: FP16
@@ -1020,14 +1025,15 @@ cudaError_t launch_induced_current_tc(const sim_config &c, const sim_segments &s
     long long *pwork = reinterpret_cast<long long *>(p + lay.pwork);
     int32_t *nsub = reinterpret_cast<int32_t *>(p + lay.nsub);
     int32_t *pos = reinterpret_cast<int32_t *>(p + lay.pos);
-    k_plan_work<<<(unsigned)((pix_cap + 255) / 256), 256, 0, st>>>(counts, pix_cap, pix_seg_off, pix_seg_ids,
-                                                                    d.n_samples, c.mc_per_sample, pwork, wtotal);
-    k_plan_split<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(counts, pix_cap, pwork, wtotal, kSubsPerSm * grid, nsub,
-                                                               ng);
+    k_plan_work<<<(unsigned)((pix_cap + 255) / 256), 256, 0, st>>>(counts, pix_cap, pix_begin, pix_end, pix_seg_off,
+                                                                    pix_seg_ids, d.n_samples, c.mc_per_sample, pwork,
+                                                                    wtotal);
+    k_plan_split<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(counts, pix_cap, pix_begin, pix_end, pwork, wtotal,
+                                                               kSubsPerSm * grid, nsub, ng);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_exclusive_scan(nsub, pos, ng, n_subs, p + lay.scan, st);
     if (e != cudaSuccess) return e;
-    k_plan_emit<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(counts, pix_cap, pwork, nsub, pos,
+    k_plan_emit<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(counts, pix_cap, pix_begin, pix_end, pwork, nsub, pos,
                                                               reinterpret_cast<int4 *>(p + lay.subs), ng);
     k_plan_rank<<<(unsigned)((ng * kGroup + 255) / 256), 256, 0, st>>>(a.subs, n_subs,
                                                                       reinterpret_cast<int32_t *>(p + lay.order));

@@ -166,20 +166,21 @@ cudaError_t launch_pixel_map(const sim_config &c, const sim_segments &s, const s
                              cudaStream_t st);
 
 // Induced current, FP32 direct form (precision 0) and tensor-core form
-// (precision 1 BF16, 2 FP16 operands); same arguments.
+// (precision 1 BF16, 2 FP16 operands); same arguments.  Rows of the active
+// pixels [pix_begin, min(counts[1], pix_end)) are computed.
 size_t current_scratch_bytes(int64_t pix_cap);
 bool current_table_ok(int nb, int nt);
 cudaError_t launch_induced_current(const sim_config &c, const sim_segments &s, const sim_drifted &d,
                                    const sim_response &r, const int32_t *active,
                                    const int32_t *pix_seg_off, const int32_t *pix_seg_ids,
-                                   const int64_t *counts, int64_t pix_cap, float *current, void *scratch,
-                                   cudaStream_t st);
+                                   const int64_t *counts, int64_t pix_cap, int64_t pix_begin, int64_t pix_end,
+                                   float *current, void *scratch, cudaStream_t st);
 size_t current_tc_scratch_bytes(int64_t pix_cap);
 cudaError_t launch_induced_current_tc(const sim_config &c, const sim_segments &s, const sim_drifted &d,
                                       const sim_response &r, const int32_t *active,
                                       const int32_t *pix_seg_off, const int32_t *pix_seg_ids,
-                                      const int64_t *counts, int64_t pix_cap, float *current, void *scratch,
-                                      cudaStream_t st);
+                                      const int64_t *counts, int64_t pix_cap, int64_t pix_begin, int64_t pix_end,
+                                      float *current, void *scratch, cudaStream_t st);
 
 size_t elec_scratch_bytes(const sim_config &c, int64_t pix_cap);
 cudaError_t launch_electronics(const sim_config &c, const EventInfo &ev, const int32_t *active,

@@ -105,6 +105,9 @@ def lib():
                                     _P, _P, C.c_int64, _P, _P, _P, C.c_int64, _P, C.c_size_t, _P]
         L.sim_induced_current.argtypes = [cp(SimConfig), cp(SimSegments), cp(SimDrifted), cp(SimResponse),
                                           _P, _P, _P, _P, C.c_int64, _P, _P, C.c_size_t, _P]
+        L.sim_induced_current_range.argtypes = [cp(SimConfig), cp(SimSegments), cp(SimDrifted), cp(SimResponse),
+                                                _P, _P, _P, _P, C.c_int64, C.c_int64, C.c_int64, _P, _P,
+                                                C.c_size_t, _P]
         L.sim_electronics.argtypes = [cp(SimConfig), cp(SimSegments), _P, _P, _P, C.c_int64, cp(SimHits),
                                       _P, C.c_size_t, _P]
         L.sim_event.argtypes = [cp(SimConfig), cp(SimSegments), cp(SimResponse), C.c_int64, C.c_int64,
@@ -114,7 +117,7 @@ def lib():
         L.sim_pixel_map_noalloc.argtypes = [cp(SimConfig), cp(SimSegments), cp(SimDrifted), cp(SimResponse),
                                             _P, _P, C.c_int64, _P, _P, _P, C.c_int64, _P, _P]
         for f in ("sim_workspace_size", "sim_quench_drift", "sim_pixel_map", "sim_induced_current",
-                  "sim_electronics", "sim_event", "sim_event_view_of", "sim_pixel_map_noalloc"):
+                  "sim_induced_current_range", "sim_electronics", "sim_event", "sim_event_view_of", "sim_pixel_map_noalloc"):
             getattr(L, f).restype = C.c_int
         sizes = (C.c_int64 * 5)()
         L.sim_abi_sizes(sizes)
@@ -310,6 +313,18 @@ def sim_induced_current(cfg: SimConfig, seg: Segments, dr: Drifted, resp: Respon
                                      _ptr(pix_seg_off), _ptr(pix_seg_ids), _ptr(counts), pix_cap,
                                      _ptr(current), _ptr(ws), int(ws.numel() * ws.element_size()),
                                      _stream(stream)), "sim_induced_current")
+
+
+def sim_induced_current_range(cfg: SimConfig, seg: Segments, dr: Drifted, resp: Response, active_pixels,
+                              pix_seg_off, pix_seg_ids, counts, pix_begin: int, pix_end: int, current, ws,
+                              stream=None):
+    s, d, r = seg.struct(), dr.struct(), resp.struct()
+    pix_cap = int(current.shape[0])
+    _check(lib().sim_induced_current_range(C.byref(cfg), C.byref(s), C.byref(d), C.byref(r), _ptr(active_pixels),
+                                           _ptr(pix_seg_off), _ptr(pix_seg_ids), _ptr(counts), int(pix_begin),
+                                           int(pix_end), pix_cap, _ptr(current), _ptr(ws),
+                                           int(ws.numel() * ws.element_size()), _stream(stream)),
+           "sim_induced_current_range")
 
 
 def sim_electronics(cfg: SimConfig, events, active_pixels, current, counts, hits: Hits, ws, stream=None):
