@@ -78,7 +78,22 @@ typedef struct sim_config {
      * 0 = FP32 direct gather; 1 = tensor-core contraction with BF16 operands,
      * 2 = with FP16 operands (FP32 accumulation in both) */
     int32_t precision;
-    int32_t reserved;
+    /* running CSA charge of the front end (sim_electronics): 0 = FP32,
+     * 1 = FP64 (for long windows, where FP32 sums drift); decisions compare
+     * FP32 roundings either way */
+    int32_t fp64_charge;
+    /* optional device bitmask of disabled channels (bit p % 32 of word p / 32
+     * set: detector pixel id p is disabled; NULL: none).  A disabled pixel's
+     * current is computed but its front end produces no hits; in a batch the
+     * mask applies to every event slot. */
+    const uint32_t *disabled_pixels;
+    /* 0: lifetime and diffusion evaluated once per segment, at its midpoint
+     * (Sec. 3.2); 1: at each point's own drift distance: a point carries
+     * Q_a/(N M) exp(-(t_point - t_drift)/tau) and diffuses with
+     * sqrt(2 D t_point); sim_quench_drift then reports sigma_T/L of the
+     * segment's farther end (they bound every point's, and size the map) */
+    int32_t per_point_drift;
+    int32_t pad_;
 } sim_config;
 
 /* Energy-deposit segments S_i = (r_s, r_e, E) (Sec. 2), as structure-of-arrays

@@ -47,7 +47,7 @@ class _Cfg(C.Structure):
         ("hold", C.c_int32), ("min_int", C.c_int32), ("periodic", C.c_int32),
         ("adc_bits", C.c_int32),
         ("seed", C.c_uint64),
-        ("nb", C.c_int32), ("nt", C.c_int32), ("bins_per_pitch", C.c_int32), ("pad", C.c_int32),
+        ("nb", C.c_int32), ("nt", C.c_int32), ("bins_per_pitch", C.c_int32), ("per_point", C.c_int32),
     ]
 
 
@@ -78,7 +78,7 @@ def lib():
         L.ora_pair_margin.argtypes = [P(_Cfg), C.c_float, C.c_float, C.c_float, C.c_float,
                                       C.c_double, C.c_int32, C.c_int32]
         L.ora_pair_margin.restype = C.c_double
-        L.ora_pixel_current.argtypes = ([P(_Cfg), f64p] + [f32p] * 8 + [f64p] * 3
+        L.ora_pixel_current.argtypes = ([P(_Cfg), f64p] + [f32p] * 8 + [f64p] * 4
                                         + [i32p, i32p, C.c_uint64, C.c_int32, i64p, C.c_int64, f64p])
         L.ora_electronics.argtypes = [P(_Cfg), C.c_uint64, C.c_int32, f64p, C.c_int64,
                                       i32p, i32p, i32p, f64p, C.c_double, i32p]
@@ -115,6 +115,7 @@ def make_cfg(cfg: dict, lut_par: dict) -> _Cfg:
     c.periodic, c.adc_bits = int(cfg["periodic_reset_ticks"]), int(cfg["adc_bits"])
     c.seed = int(cfg["seed"]) & 0xFFFFFFFFFFFFFFFF
     c.nb, c.nt, c.bins_per_pitch = int(lut_par["nb"]), int(lut_par["nt"]), int(lut_par["bins_per_pitch"])
+    c.per_point = int(cfg.get("per_point_drift", 0))
     return c
 
 
@@ -234,7 +235,8 @@ class Oracle:
         I = np.zeros(int(self.c.n_ticks))
         self.L.ora_pixel_current(C.byref(self.c), _p(lut, C.c_double),
                                  *[_p(a, C.c_float) for a in cols[:8]],
-                                 _p(dr["Qa"], C.c_double), _p(dr["sigma_T"], C.c_double),
+                                 _p(dr["Qa"], C.c_double), _p(dr["t_drift"], C.c_double),
+                                 _p(dr["sigma_T"], C.c_double),
                                  _p(dr["sigma_L"], C.c_double), _p(dr["anode"], C.c_int32),
                                  _p(dr["n_samples"], C.c_int32), event_id, int(pixel),
                                  _p(segs, C.c_int64), len(segs), _p(I, C.c_double))

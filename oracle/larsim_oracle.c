@@ -60,7 +60,10 @@ typedef struct ora_cfg {
     uint64_t seed;
     /* response table */
     int32_t nb, nt, bins_per_pitch;
-    int32_t pad;
+    /* 0: lifetime and diffusion evaluated once per segment, at its midpoint;
+     * 1: at each point's own drift distance (the segment's sigma_T/L outputs
+     * are then those of its farther end, which bound every point's) */
+    int32_t per_point;
 } ora_cfg;
 
 size_t ora_cfg_size(void) { return sizeof(ora_cfg); }
@@ -235,8 +238,14 @@ void ora_quench_drift(const ora_cfg *c, int64_t n,
         /* Eq. (lifetime) */
         double qa = QR * exp(-td / c->lifetime);
         /* sigma = sqrt(2 D t), D converted from cm^2/s to cm^2/us */
-        double sT = sqrt(2.0 * (c->DT * 1e-6) * td);
-        double sL = sqrt(2.0 * (c->DL * 1e-6) * td);
+        double tsig = td;
+        if (c->per_point) {
+            double t0d = fabs((double)z0[i] - L.za) / c->vdrift;
+            double t1d = fabs((double)z1[i] - L.za) / c->vdrift;
+            tsig = t0d > t1d ? t0d : t1d;
+        }
+        double sT = sqrt(2.0 * (c->DT * 1e-6) * tsig);
+        double sL = sqrt(2.0 * (c->DL * 1e-6) * tsig);
         double N = ceil(dx / c->step);
         if (N < 1.0) N = 1.0;
         dedx_out[i] = dedx;
@@ -393,6 +402,9 @@ static double ora_lut(const ora_cfg *c, const double *lut, int bx, int by, int64
  * normals from Philox counter (s, mu M + nu, 1, 0), clipped at +-clip; each
  * perturbed point carries q = Q_a / (N_s M) and arrives at
  * t_a = t_mu + |z_mu + dz - z_anode| / v_drift (Eq. (drift) per point).
+ * With per_point, the point's own drift time t = |z_mu - z_anode| / v_drift
+ * sets its charge q exp(-(t - t_drift)/tau) (Eq. (lifetime) at the point
+ * instead of the midpoint) and its widths sigma = sqrt(2 D t).
  * The table is read at the folded offset (|dx|, |dy|) by bilinear
  * interpolation between bin-centred nodes (node nb reads 0; offsets below
  * half a bin read node 0) and at the fractional arrival tick by linear
@@ -403,8 +415,8 @@ static double ora_lut(const ora_cfg *c, const double *lut, int bx, int by, int64
 void ora_pixel_current(const ora_cfg *c, const double *lut,
                        const float *x0, const float *y0, const float *z0, const float *t0,
                        const float *x1, const float *y1, const float *z1, const float *t1,
-                       const double *Qa, const double *sigma_T, const double *sigma_L,
-                       const int32_t *anode, const int32_t *n_samples,
+                       const double *Qa, const double *t_drift, const double *sigma_T,
+                       const double *sigma_L, const int32_t *anode, const int32_t *n_samples,
                        uint64_t event_id, int32_t pixel, const int64_t *segs, int64_t n_segs,
                        double *I)
 {
@@ -427,6 +439,13 @@ void ora_pixel_current(const ora_cfg *c, const double *lut,
             double y = (double)y0[s] + u * ((double)y1[s] - (double)y0[s]);
             double z = (double)z0[s] + u * ((double)z1[s] - (double)z0[s]);
             double t = (double)t0[s] + u * ((double)t1[s] - (double)t0[s]);
+            double qp = q, sTp = sigma_T[s], sLp = sigma_L[s];
+            if (c->per_point) {
+                double tp = fabs(z - za) / c->vdrift;
+                qp = q * exp(-(tp - t_drift[s]) / c->lifetime);
+                sTp = sqrt(2.0 * (c->DT * 1e-6) * tp);
+                sLp = sqrt(2.0 * (c->DL * 1e-6) * tp);
+            }
             for (int nu = 0; nu < c->M; ++nu) {
                 double n[4];
                 ora_normals(c->seed, event_id, (uint32_t)s, (uint32_t)(mu * c->M + nu), 1u, 0u, n);
@@ -434,9 +453,9 @@ void ora_pixel_current(const ora_cfg *c, const double *lut,
                     if (n[d] > c->clip) n[d] = c->clip;
                     if (n[d] < -c->clip) n[d] = -c->clip;
                 }
-                double dxp = x + sigma_T[s] * n[0] - xc;
-                double dyp = y + sigma_T[s] * n[1] - yc;
-                double zz = z + sigma_L[s] * n[2];
+                double dxp = x + sTp * n[0] - xc;
+                double dyp = y + sTp * n[1] - yc;
+                double zz = z + sLp * n[2];
                 double ta = t + fabs(zz - za) / c->vdrift;
                 double xi = fabs(dxp) / h - 0.5;
                 double yi = fabs(dyp) / h - 0.5;
@@ -460,7 +479,7 @@ void ora_pixel_current(const ora_cfg *c, const double *lut,
                     int64_t j2 = j1 - 1;
                     double r1 = (j1 >= 0 && j1 < L) ? Rxy[j1] : 0.0;
                     double r2 = (j2 >= 0 && j2 < L) ? Rxy[j2] : 0.0;
-                    I[k] += q * ((1.0 - f) * r1 + f * r2);
+                    I[k] += qp * ((1.0 - f) * r1 + f * r2);
                 }
             }
         }

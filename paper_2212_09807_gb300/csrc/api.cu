@@ -31,6 +31,8 @@ bool cfg_ok(const sim_config *c)
     if (c->recomb_model != 0 && c->recomb_model != 1) return false;
     if (c->adc_bits < 1 || c->adc_bits > 16 || c->hold_ticks < 0 || c->min_adc_interval_ticks < 0) return false;
     if (c->periodic_reset_ticks < 0 || c->precision < 0 || c->precision > 2) return false;
+    if (c->fp64_charge != 0 && c->fp64_charge != 1) return false;
+    if (c->per_point_drift != 0 && c->per_point_drift != 1) return false;
     return true;
 }
 

@@ -19,13 +19,32 @@ struct __align__(16) Rec {
 
 // Pixel-independent part of the record of point `idx` (= mu M + nu) of a
 // segment: position in pitch units relative to the anchor's reference pixel
-// corner, and the arrival tick relative to the anchor's A0.
+// corner, the arrival tick relative to the anchor's A0, and the charge.
 struct PointPos {
-    float fx, fy, lin;
+    float fx, fy, lin, q;
 };
 
+// Drift constants for per-point lifetime and widths (Sec. 3.2 evaluated at
+// each point): off when per_point == 0.
+struct DriftPar {
+    int per_point;
+    float inv_vd, inv_tau, two_dt, two_dl, inv_pitch;   // us/cm, 1/us, cm^2/us, cm^2/us, 1/cm
+};
+
+inline DriftPar drift_par_of(const sim_config &c)
+{
+    DriftPar d;
+    d.per_point = c.per_point_drift;
+    d.inv_vd = 1.0f / c.vdrift_cm_us;
+    d.inv_tau = 1.0f / c.lifetime_us;
+    d.two_dt = 2.0f * (c.diff_tran_cm2_s * 1e-6f);
+    d.two_dl = 2.0f * (c.diff_long_cm2_s * 1e-6f);
+    d.inv_pitch = 1.0f / c.pitch_cm;
+    return d;
+}
+
 __device__ __forceinline__ PointPos point_position(const Anchor &A, int idx, int M, uint64_t key,
-                                                   uint32_t seg_local, float clip)
+                                                   uint32_t seg_local, float clip, const DriftPar &dp)
 {
     const int mu = (M == 1) ? idx : idx / M;
     float3 n = normals3(key, seg_local, (uint32_t)idx, 1u);
@@ -33,13 +52,23 @@ __device__ __forceinline__ PointPos point_position(const Anchor &A, int idx, int
     n.y = fminf(fmaxf(n.y, -clip), clip);
     n.z = fminf(fmaxf(n.z, -clip), clip);
     const float u = ((float)mu + 0.5f) / (float)A.N;
+    float sTp = A.sTp, sLc = A.sLc, q = A.q;
+    if (dp.per_point) {
+        // the point's own drift time; the anchor's charge carries the midpoint's attenuation
+        const float t = fabsf(A.d0 + u * A.dd) * dp.inv_vd;
+        const float tm = fabsf(A.d0 + 0.5f * A.dd) * dp.inv_vd;
+        q = A.q * expf(-(t - tm) * dp.inv_tau);
+        sTp = sqrtf(dp.two_dt * t) * dp.inv_pitch;
+        sLc = A.sLc * sqrtf(dp.two_dl * t);          // A.sLc holds the drift direction (+-1)
+    }
     PointPos p;
-    p.fx = A.fx0 + u * A.dX + A.sTp * n.x;
-    p.fy = A.fy0 + u * A.dY + A.sTp * n.y;
-    float lin = A.fa0 + u * A.da + A.sLc * n.z * A.kz;
-    const float dmu = A.d0 + u * A.dd + A.sLc * n.z;
+    p.fx = A.fx0 + u * A.dX + sTp * n.x;
+    p.fy = A.fy0 + u * A.dY + sTp * n.y;
+    float lin = A.fa0 + u * A.da + sLc * n.z * A.kz;
+    const float dmu = A.d0 + u * A.dd + sLc * n.z;
     if (dmu < 0.f) lin -= 2.0f * dmu * A.kz;     // charge beyond the anode plane drifts back
     p.lin = lin;
+    p.q = q;
     return p;
 }
 
@@ -58,7 +87,7 @@ __device__ __forceinline__ bool point_record(const Anchor &A, const PointPos &p,
     const float wx = xi - (float)bx, wy = yi - (float)by;
     // node nb (beyond the table) reads zero: far corners get no weight
     const float ex = (bx + 1 < nb) ? 1.f : 0.f, ey = (by + 1 < nb) ? 1.f : 0.f;
-    const float q1 = A.q * (1.f - wx), q2 = A.q * wx * ex;
+    const float q1 = p.q * (1.f - wx), q2 = p.q * wx * ex;
     r.A = A.A0 + (int)fl;
     r.b0 = bx * nb + by;
     r.f = p.lin - fl;

@@ -46,16 +46,20 @@ struct ElArgs {
     int hmax;
 };
 
-__device__ __forceinline__ float warp_incl_scan_f(float v, int lane)
+template <typename Acc>
+__device__ __forceinline__ Acc warp_incl_scan(Acc v, int lane)
 {
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const float u = __shfl_up_sync(0xffffffffu, v, o);
+        const Acc u = __shfl_up_sync(0xffffffffu, v, o);
         if (lane >= o) v += u;
     }
     return v;
 }
 
+// Acc: type of the running CSA charge (float, or double for long windows);
+// threshold and ADC decisions compare FP32 roundings of the Acc operands.
+template <typename Acc>
 __global__ void __launch_bounds__(kWarps * 32) k_electronics(ElArgs a)
 {
     if ((a.counts[3] & (SIM_STATUS_PAIR_OVERFLOW | SIM_STATUS_PIXEL_OVERFLOW)) != 0) return;
@@ -75,10 +79,14 @@ __global__ void __launch_bounds__(kWarps * 32) k_electronics(ElArgs a)
         const int32_t vpid = a.active[pi];
         const int slot = (int)(vpid / a.det_px);
         const uint32_t pid = (uint32_t)(vpid - slot * a.det_px);
+        if (c.disabled_pixels && ((__ldg(c.disabled_pixels + (pid >> 5)) >> (pid & 31)) & 1u)) {
+            if (lane == 0) a.nhit[pi] = 0;      // channel disabled: no hits
+            continue;
+        }
         const uint64_t key = slot_key(a.c.seed, a.ev, slot);
         const float *I = a.current + (size_t)pi * T;
         HitRec *st = a.stage + (size_t)pi * a.hmax;
-        float qoff = 0.f;         // CSA charge before this chunk's first tick
+        Acc qoff = 0;             // CSA charge before this chunk's first tick
         bool idle = true;
         int t_cross = -1, t_adc = -1;
         int last_adc = -(1 << 30);
@@ -87,7 +95,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_electronics(ElArgs a)
         for (int k0 = 0; k0 < T; k0 += 32) {
             const int k = k0 + lane;
             const float x = (k < T) ? I[k] : 0.f;
-            const float sc = warp_incl_scan_f(x, lane);
+            const Acc sc = warp_incl_scan<Acc>((Acc)x, lane);
             const int nl = min(32, T - k0);
             int pos = 0;
             while (pos < nl) {
@@ -101,9 +109,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_electronics(ElArgs a)
                     bool cross = false;
                     if (lane >= pos && lane < lim) {
                         const float2 n = normals2(key, pid, (uint32_t)k, 2u);
-                        const float v = qoff + sc + c.sigma_unc_e * n.x;
-                        const float thr = c.thr_e + c.sigma_disc_e * n.y;
-                        cross = v >= thr;
+                        const Acc v = qoff + sc + (Acc)c.sigma_unc_e * (Acc)n.x;
+                        const Acc thr = (Acc)c.thr_e + (Acc)c.sigma_disc_e * (Acc)n.y;
+                        cross = (float)v >= (float)thr;
                     }
                     const unsigned m = __ballot_sync(0xffffffffu, cross);
                     if (m) {
@@ -113,9 +121,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_electronics(ElArgs a)
                         idle = false;
                         pos = cl;
                     } else if (lim < nl) {
-                        const float r = c.sigma_reset_e * normals2(key, pid, (uint32_t)(k0 + lim), 4u).x;
-                        const float sprev = __shfl_sync(0xffffffffu, sc, max(lim - 1, 0));
-                        qoff = r - (lim > 0 ? sprev : 0.f);
+                        const Acc r = (Acc)c.sigma_reset_e * (Acc)normals2(key, pid, (uint32_t)(k0 + lim), 4u).x;
+                        const Acc sprev = __shfl_sync(0xffffffffu, sc, max(lim - 1, 0));
+                        qoff = r - (lim > 0 ? sprev : (Acc)0);
                         per_done = k0 + lim;
                         pos = lim;
                     } else {
@@ -124,13 +132,13 @@ __global__ void __launch_bounds__(kWarps * 32) k_electronics(ElArgs a)
                 } else {
                     if (t_adc < k0 + nl) {
                         const int l = t_adc - k0;
-                        const float sl = __shfl_sync(0xffffffffu, sc, l);
+                        const Acc sl = __shfl_sync(0xffffffffu, sc, l);
                         const float nu = normals2(key, pid, (uint32_t)t_adc, 2u).x;
-                        const float v = qoff + sl + c.sigma_unc_e * nu;
-                        const float code = fminf(fmaxf(floorf(v / lsb_e), 0.f), adc_max);
-                        if (lane == 0 && nh < a.hmax) st[nh] = HitRec{t_cross, t_adc, (int32_t)code, v};
+                        const Acc v = qoff + sl + (Acc)c.sigma_unc_e * (Acc)nu;
+                        const float code = fminf(fmaxf(floorf((float)v / lsb_e), 0.f), adc_max);
+                        if (lane == 0 && nh < a.hmax) st[nh] = HitRec{t_cross, t_adc, (int32_t)code, (float)v};
                         ++nh;
-                        const float r = c.sigma_reset_e * normals2(key, pid, (uint32_t)t_adc, 3u).x;
+                        const Acc r = (Acc)c.sigma_reset_e * (Acc)normals2(key, pid, (uint32_t)t_adc, 3u).x;
                         qoff = r - sl;
                         last_adc = t_adc;
                         idle = true;
@@ -227,7 +235,8 @@ cudaError_t launch_electronics(const sim_config &c, const EventInfo &ev, const i
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int64_t grid = (pix_cap + kWarps - 1) / kWarps;
     if (grid > (int64_t)sms * 16) grid = (int64_t)sms * 16;
-    k_electronics<<<(unsigned)grid, kWarps * 32, 0, st>>>(a);
+    if (c.fp64_charge) k_electronics<double><<<(unsigned)grid, kWarps * 32, 0, st>>>(a);
+    else k_electronics<float><<<(unsigned)grid, kWarps * 32, 0, st>>>(a);
     e = launch_exclusive_scan(nhit, nhit, pix_cap, counts + 2, scan_ws, st);
     if (e != cudaSuccess) return e;
     k_hits_status<<<1, 1, 0, st>>>(counts, out.capacity, out.n_out);

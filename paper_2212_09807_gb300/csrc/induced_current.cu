@@ -63,6 +63,7 @@ struct CurArgs {
     uint64_t seed;
     EventInfo ev;
     Geo g;
+    DriftPar dp;
     Rec *recs;                                  // [grid][kRecCap], point order
     Rec *sorted;                                // [grid][kRecCap], bin order
 };
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a)
                     bool ok = false;
                     Rec r;
                     if (idx < total) {
-                        const PointPos pp = point_position(A, idx, M, key, (uint32_t)(sg - seg0), clip);
+                        const PointPos pp = point_position(A, idx, M, key, (uint32_t)(sg - seg0), clip, a.dp);
                         ok = point_record(A, pp, cx, cy, fbpp, a.nb, r);
                     }
                     const unsigned m = __ballot_sync(0xffffffffu, ok);
@@ -390,6 +391,7 @@ cudaError_t launch_induced_current(const sim_config &c, const sim_segments &s, c
     a.seed = c.seed;
     a.ev = events_of(s);
     a.g = geo_of(c);
+    a.dp = drift_par_of(c);
     const int grid = grid_for(pix_cap);
     char *p = reinterpret_cast<char *>(scratch);
     a.recs = reinterpret_cast<Rec *>(p);

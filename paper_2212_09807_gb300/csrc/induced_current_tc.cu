@@ -109,6 +109,7 @@ struct TcArgs {
     uint64_t seed;
     EventInfo ev;
     Geo g;
+    DriftPar dp;
     int *queue;                             // next entry of `order`
     const int4 *subs;                       // sub-groups {first pixel, pixels, work lo, work hi}
     const int32_t *order;                   // sub-groups by decreasing work
@@ -327,7 +328,7 @@ __device__ int gen_chunk(const TcArgs &a, TcSmem *s, GenState &st, int64_t pi0, 
             bool ok = false;
             Rec r;
             if (idx < total) {
-                const PointPos pp = point_position(A, idx, M, key, (uint32_t)(sg - seg0), clip);
+                const PointPos pp = point_position(A, idx, M, key, (uint32_t)(sg - seg0), clip, a.dp);
                 ok = point_record(A, pp, (float)(ix - A.ix_ref) + 0.5f, (float)(iy - A.iy_ref) + 0.5f, fbpp, nb, r);
             }
             const unsigned m = __ballot_sync(0xffffffffu, ok);
@@ -1007,6 +1008,7 @@ cudaError_t launch_induced_current_tc(const sim_config &c, const sim_segments &s
     a.seed = c.seed;
     a.ev = events_of(s);
     a.g = geo_of(c);
+    a.dp = drift_par_of(c);
     a.queue = reinterpret_cast<int *>(p + lay.queue);
     unsigned long long *wtotal = reinterpret_cast<unsigned long long *>(p + lay.queue + 8);
     int64_t *n_subs = reinterpret_cast<int64_t *>(p + lay.queue + 16);

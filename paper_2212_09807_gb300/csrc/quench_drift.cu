@@ -91,8 +91,15 @@ __global__ void __launch_bounds__(256) k_quench_drift(sim_config c, sim_segments
     // ---- step 2: drift time, lifetime, diffusion at the midpoint ----
     const float td = (float)fabs(zm - L.za) / c.vdrift_cm_us;
     const float Qa = QR * expf(-td / c.lifetime_us);
-    const float sT = sqrtf(2.0f * (c.diff_tran_cm2_s * 1e-6f) * td);
-    const float sL = sqrtf(2.0f * (c.diff_long_cm2_s * 1e-6f) * td);
+    // widths: at the midpoint, or (per-point drift) at the farther end, which bounds every point's
+    float tsig = td;
+    if (c.per_point_drift) {
+        const float t0d = (float)fabs((double)z0 - L.za) / c.vdrift_cm_us;
+        const float t1d = (float)fabs((double)z1 - L.za) / c.vdrift_cm_us;
+        tsig = fmaxf(t0d, t1d);
+    }
+    const float sT = sqrtf(2.0f * (c.diff_tran_cm2_s * 1e-6f) * tsig);
+    const float sL = sqrtf(2.0f * (c.diff_long_cm2_s * 1e-6f) * tsig);
     o.Qa[i] = Qa;
     o.t_drift[i] = td;
     o.sigma_T[i] = sT;
@@ -126,8 +133,10 @@ __global__ void __launch_bounds__(256) k_quench_drift(sim_config c, sim_segments
     a.fa0 = (float)(a0 - A0);
     a.da = (float)(((double)t1 - (double)t0) / tick + dd / vt);
     a.q = Qa / ((float)N * (float)c.mc_per_sample);
+    // sTp sizes the pixel map (the farther end's width under per-point drift, whose points
+    // compute their own widths); under per-point drift sLc keeps only the drift direction
     a.sTp = sT / c.pitch_cm;
-    a.sLc = (float)sgn * sL;
+    a.sLc = c.per_point_drift ? (float)sgn : (float)sgn * sL;
     a.d0 = (float)d0;
     a.dd = (float)dd;
     a.kz = (float)(1.0 / vt);

@@ -52,7 +52,8 @@ class SimConfig(C.Structure):
         ("hold_ticks", C.c_int32), ("min_adc_interval_ticks", C.c_int32),
         ("periodic_reset_ticks", C.c_int32), ("adc_bits", C.c_int32),
         ("seed", C.c_uint64),
-        ("precision", C.c_int32), ("reserved", C.c_int32),
+        ("precision", C.c_int32), ("fp64_charge", C.c_int32), ("disabled_pixels", C.c_void_p),
+        ("per_point_drift", C.c_int32), ("pad_", C.c_int32),
     ]
 
 
@@ -138,9 +139,13 @@ def make_config(cfg: dict) -> SimConfig:
     """sim_config from a parameter dict (floats rounded to FP32 by ctypes)."""
     c = SimConfig()
     for name, ct in SimConfig._fields_:
-        if name == "reserved":
+        if name == "disabled_pixels":       # optional CUDA tensor (int32/uint32 words) or None
+            m = cfg.get(name)
+            c.disabled_pixels = None if m is None else int(m.data_ptr())
             continue
-        v = cfg[name]
+        if name == "pad_":
+            continue
+        v = cfg.get(name, 0) if name in ("precision", "fp64_charge", "per_point_drift") else cfg[name]
         setattr(c, name, int(v) & 0xFFFFFFFFFFFFFFFF if name == "seed" else (float(v) if ct is C.c_float else int(v)))
     return c
 

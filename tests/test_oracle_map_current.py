@@ -325,3 +325,61 @@ def test_longitudinal_spread_matches_sigma_L():
         I0 += o0.pixel_current(s0, o0.quench_drift(s0), pid, [0])
     sa2 = (d["sigma_L"][0] / (np.float32(0.16) * np.float32(0.1))) ** 2
     assert abs((var(I) - var(I0)) / (sa2 - 1.0 / 12) - 1) < 0.08
+
+
+def test_per_point_drift_charge_is_the_pointwise_lifetime_sum():
+    """Per-point drift: each point carries Q_a/N exp(-(t_mu - t_mid)/tau) with
+    t_mu its own drift time (Eq. (lifetime) at the point), so the charge
+    collected over all pixels and ticks is that closed-form geometric sum;
+    per-segment drift collects Q_a.  Short lifetime (40 us) and no diffusion
+    make the difference large."""
+    cfg = params.small_config(n_ticks=4000, t_window0_us=-200.0, lifetime_us=40.0, diff_long_cm2_s=0.0,
+                              diff_tran_cm2_s=0.0, per_point_drift=1)
+    lut = response.lut_for(cfg, params.LUT)
+    o = oracle.Oracle(cfg, params.LUT, lut)
+    rows = [(15.3, 20.1, 5.0, 0, 15.4, 20.05, 9.0, 0, 8.0),       # 4 cm along the drift, TPC 0
+            (30.2, 12.7, 41.0, 0, 30.1, 12.75, 47.5, 0, 9.0)]      # 6.5 cm, TPC 1
+    seg = _seg(rows)
+    d = o.quench_drift(seg)
+    pix, _, _, _ = o.pixel_map(seg, d)
+    for s in range(2):
+        total = sum(o.pixel_current(seg, d, p, [s]).sum() for p, sl in pix.items() if s in sl)
+        z0, z1 = float(seg["z0"][s]), float(seg["z1"][s])
+        za = 0.0 if z0 < 30 else 60.0
+        N = int(d["n_samples"][s])
+        v = float(np.float32(cfg["vdrift_cm_us"]))
+        tau = float(np.float32(cfg["lifetime_us"]))
+        t_first = abs(z0 + (z1 - z0) * 0.5 / N - za) / v
+        dt = (abs(z0 + (z1 - z0) * 1.5 / N - za) - abs(z0 + (z1 - z0) * 0.5 / N - za)) / v
+        r = np.exp(-dt / tau)
+        expect = d["Qa"][s] / N * np.exp(-(t_first - d["t_drift"][s]) / tau) * (1 - r ** N) / (1 - r)
+        assert abs(total / expect - 1.0) < 1e-9, (s, total, expect)
+        assert abs(total / d["Qa"][s] - 1.0) > 1e-3          # differs from the per-segment charge
+    # the map radius of per-point drift uses the farther end's width: here zero (no diffusion)
+    assert np.all(d["sigma_T"] == 0.0)
+
+
+def test_per_point_drift_reduces_to_per_segment_without_lifetime_and_diffusion():
+    base = dict(lifetime_us=1e12, diff_long_cm2_s=0.0, diff_tran_cm2_s=0.0)
+    seg = _seg([(12.0, 9.0, 11.0, 0, 12.6, 9.3, 13.2, 0, 1.5)])
+    out = []
+    for pp in (0, 1):
+        cfg = params.small_config(per_point_drift=pp, **base)
+        o = oracle.Oracle(cfg, params.LUT, response.lut_for(cfg, params.LUT))
+        d = o.quench_drift(seg)
+        pix, _, _, _ = o.pixel_map(seg, d)
+        out.append({p: o.pixel_current(seg, d, p, s) for p, s in pix.items()})
+    assert out[0].keys() == out[1].keys()
+    for p in out[0]:
+        np.testing.assert_allclose(out[1][p], out[0][p], rtol=1e-9, atol=1e-12)
+
+
+def test_per_point_drift_map_width_is_the_farther_end():
+    cfg = params.small_config(per_point_drift=1)
+    o = oracle.Oracle(cfg, params.LUT)
+    seg = _seg([(12.0, 9.0, 3.0, 0, 12.6, 9.3, 13.0, 0, 1.5), (12.0, 9.0, 55.0, 0, 12.6, 9.3, 45.0, 0, 1.5)])
+    d = o.quench_drift(seg)
+    for s, far in ((0, 13.0), (1, 60.0 - 45.0)):
+        t = far / float(np.float32(cfg["vdrift_cm_us"]))
+        np.testing.assert_allclose(d["sigma_T"][s], np.sqrt(2 * float(np.float32(cfg["diff_tran_cm2_s"])) * 1e-6 * t),
+                                   rtol=1e-12)
