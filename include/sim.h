@@ -93,7 +93,9 @@ typedef struct sim_config {
      * sqrt(2 D t_point); sim_quench_drift then reports sigma_T/L of the
      * segment's farther end (they bound every point's, and size the map) */
     int32_t per_point_drift;
-    int32_t pad_;
+    /* table lookup: 0 = bilinear in the folded offset and linear in the
+     * arrival tick; 1 = nearest node and nearest tick (halves round up) */
+    int32_t nearest_lut;
 } sim_config;
 
 /* Energy-deposit segments S_i = (r_s, r_e, E) (Sec. 2), as structure-of-arrays

@@ -48,6 +48,7 @@ class _Cfg(C.Structure):
         ("adc_bits", C.c_int32),
         ("seed", C.c_uint64),
         ("nb", C.c_int32), ("nt", C.c_int32), ("bins_per_pitch", C.c_int32), ("per_point", C.c_int32),
+        ("nearest", C.c_int32), ("pad2", C.c_int32),
     ]
 
 
@@ -79,7 +80,8 @@ def lib():
                                       C.c_double, C.c_int32, C.c_int32]
         L.ora_pair_margin.restype = C.c_double
         L.ora_pixel_current.argtypes = ([P(_Cfg), f64p] + [f32p] * 8 + [f64p] * 4
-                                        + [i32p, i32p, C.c_uint64, C.c_int32, i64p, C.c_int64, f64p])
+                                        + [i32p, i32p, C.c_uint64, C.c_int32, i64p, C.c_int64, f64p, C.c_double,
+                                           C.POINTER(C.c_int64)])
         L.ora_electronics.argtypes = [P(_Cfg), C.c_uint64, C.c_int32, f64p, C.c_int64,
                                       i32p, i32p, i32p, f64p, C.c_double, i32p]
         L.ora_electronics.restype = C.c_int64
@@ -116,6 +118,7 @@ def make_cfg(cfg: dict, lut_par: dict) -> _Cfg:
     c.seed = int(cfg["seed"]) & 0xFFFFFFFFFFFFFFFF
     c.nb, c.nt, c.bins_per_pitch = int(lut_par["nb"]), int(lut_par["nt"]), int(lut_par["bins_per_pitch"])
     c.per_point = int(cfg.get("per_point_drift", 0))
+    c.nearest = int(cfg.get("nearest_lut", 0))
     return c
 
 
@@ -227,20 +230,24 @@ class Oracle:
 
     # -- step 4 ------------------------------------------------------------
     def pixel_current(self, seg: dict, dr: dict, pixel: int, segs, event_id: int = 0,
-                      lut: np.ndarray | None = None) -> np.ndarray:
+                      lut: np.ndarray | None = None, tie_band: float | None = None):
+        """Current of one pixel; with tie_band (nearest-bin lookup): also the
+        number of points with a rounding within tie_band of its half-way point."""
         lut = self.lut if lut is None else np.ascontiguousarray(np.asarray(lut, np.float64)[..., : self.nt])
         assert lut is not None
         cols = dr["_seg"]
         segs = np.ascontiguousarray(segs, dtype=np.int64)
         I = np.zeros(int(self.c.n_ticks))
+        nt_ = C.c_int64(0)
         self.L.ora_pixel_current(C.byref(self.c), _p(lut, C.c_double),
                                  *[_p(a, C.c_float) for a in cols[:8]],
                                  _p(dr["Qa"], C.c_double), _p(dr["t_drift"], C.c_double),
                                  _p(dr["sigma_T"], C.c_double),
                                  _p(dr["sigma_L"], C.c_double), _p(dr["anode"], C.c_int32),
                                  _p(dr["n_samples"], C.c_int32), event_id, int(pixel),
-                                 _p(segs, C.c_int64), len(segs), _p(I, C.c_double))
-        return I
+                                 _p(segs, C.c_int64), len(segs), _p(I, C.c_double),
+                                 float(tie_band or 0.0), C.byref(nt_))
+        return (I, int(nt_.value)) if tie_band is not None else I
 
     # -- step 5 ------------------------------------------------------------
     def electronics(self, pixel: int, I: np.ndarray, event_id: int = 0, band: float = 0.0) -> dict:

@@ -64,6 +64,10 @@ typedef struct ora_cfg {
      * 1: at each point's own drift distance (the segment's sigma_T/L outputs
      * are then those of its farther end, which bound every point's) */
     int32_t per_point;
+    /* 0: table read bilinearly in the offset and linearly in the arrival
+     * tick; 1: nearest node and nearest tick (halves round up) */
+    int32_t nearest;
+    int32_t pad2;
 } ora_cfg;
 
 size_t ora_cfg_size(void) { return sizeof(ora_cfg); }
@@ -402,6 +406,12 @@ static double ora_lut(const ora_cfg *c, const double *lut, int bx, int by, int64
  * normals from Philox counter (s, mu M + nu, 1, 0), clipped at +-clip; each
  * perturbed point carries q = Q_a / (N_s M) and arrives at
  * t_a = t_mu + |z_mu + dz - z_anode| / v_drift (Eq. (drift) per point).
+ * With nearest, the table is read at the nearest node (bx, by) =
+ * (floor(xi + 1/2), floor(yi + 1/2)) (none when it is node nb) and the
+ * nearest tick A = floor(a + 1/2): I[k] += q R[bx][by][k - A + L - 1];
+ * *n_ties (if non-null) receives the number of perturbed points with one of
+ * these roundings within tie_band (bins or ticks) of its half-way point:
+ * FP32 arithmetic may round those the other way.
  * With per_point, the point's own drift time t = |z_mu - z_anode| / v_drift
  * sets its charge q exp(-(t - t_drift)/tau) (Eq. (lifetime) at the point
  * instead of the midpoint) and its widths sigma = sqrt(2 D t).
@@ -418,8 +428,9 @@ void ora_pixel_current(const ora_cfg *c, const double *lut,
                        const double *Qa, const double *t_drift, const double *sigma_T,
                        const double *sigma_L, const int32_t *anode, const int32_t *n_samples,
                        uint64_t event_id, int32_t pixel, const int64_t *segs, int64_t n_segs,
-                       double *I)
+                       double *I, double tie_band, int64_t *n_ties)
 {
+    int64_t ties = 0;
     int T = c->n_ticks;
     int L = c->nt;
     double h = c->pitch / (double)c->bins_per_pitch;
@@ -462,6 +473,20 @@ void ora_pixel_current(const ora_cfg *c, const double *lut,
                 if (xi < 0.0) xi = 0.0;
                 if (yi < 0.0) yi = 0.0;
                 if (xi >= (double)c->nb || yi >= (double)c->nb) continue;
+                if (c->nearest) {
+                    double a = (ta - c->t_w0) / c->tick;
+                    double mx = fabs(xi - floor(xi) - 0.5), my = fabs(yi - floor(yi) - 0.5);
+                    double ma = fabs(a - floor(a) - 0.5);
+                    if (mx < tie_band || my < tie_band || ma < tie_band) ++ties;
+                    int nx = (int)floor(xi + 0.5), ny = (int)floor(yi + 0.5);
+                    if (nx >= c->nb || ny >= c->nb) continue;
+                    int64_t A = (int64_t)floor(a + 0.5);
+                    for (int k = 0; k < T; ++k) {
+                        int64_t j = (int64_t)k - A + L - 1;
+                        if (j >= 0 && j < L) I[k] += qp * ora_lut(c, lut, nx, ny, j);
+                    }
+                    continue;
+                }
                 int bx = (int)floor(xi), by = (int)floor(yi);
                 double wx = xi - bx, wy = yi - by;
                 for (int j = 0; j < L; ++j) {
@@ -485,6 +510,7 @@ void ora_pixel_current(const ora_cfg *c, const double *lut,
         }
     }
     free(Rxy);
+    if (n_ties) *n_ties = ties;
 }
 
 /* ---------------------------------------------------------- electronics -- */

@@ -33,6 +33,7 @@ bool cfg_ok(const sim_config *c)
     if (c->periodic_reset_ticks < 0 || c->precision < 0 || c->precision > 2) return false;
     if (c->fp64_charge != 0 && c->fp64_charge != 1) return false;
     if (c->per_point_drift != 0 && c->per_point_drift != 1) return false;
+    if (c->nearest_lut != 0 && c->nearest_lut != 1) return false;
     return true;
 }
 

@@ -74,14 +74,25 @@ __device__ __forceinline__ PointPos point_position(const Anchor &A, int idx, int
 
 // Record of a point for the pixel whose centre is (cx, cy) in the same pitch
 // units; false when the folded offset is beyond the table (nb bins of 1/bpp
-// pitch in x or y).
+// pitch in x or y).  nearest: the nearest node and the nearest tick (halves
+// round up) instead of the bilinear/linear reads; node nb reads zero.
 __device__ __forceinline__ bool point_record(const Anchor &A, const PointPos &p, float cx, float cy, float fbpp,
-                                             int nb, Rec &r)
+                                             int nb, int nearest, Rec &r)
 {
     const float fnb = (float)nb;
     const float xi = fmaxf(fabsf((p.fx - cx) * fbpp) - 0.5f, 0.f);
     const float yi = fmaxf(fabsf((p.fy - cy) * fbpp) - 0.5f, 0.f);
     if (!(xi < fnb && yi < fnb)) return false;
+    if (nearest) {
+        const int nx = (int)floorf(xi + 0.5f), ny = (int)floorf(yi + 0.5f);
+        if (nx >= nb || ny >= nb) return false;
+        r.A = A.A0 + (int)floorf(p.lin + 0.5f);
+        r.b0 = nx * nb + ny;
+        r.f = 0.f;
+        r.pad = 0.f;
+        r.w = make_float4(p.q, 0.f, 0.f, 0.f);
+        return true;
+    }
     const float fl = floorf(p.lin);
     const int bx = (int)xi, by = (int)yi;
     const float wx = xi - (float)bx, wy = yi - (float)by;

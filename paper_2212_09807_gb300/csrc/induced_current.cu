@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a)
                     Rec r;
                     if (idx < total) {
                         const PointPos pp = point_position(A, idx, M, key, (uint32_t)(sg - seg0), clip, a.dp);
-                        ok = point_record(A, pp, cx, cy, fbpp, a.nb, r);
+                        ok = point_record(A, pp, cx, cy, fbpp, a.nb, a.c.nearest_lut, r);
                     }
                     const unsigned m = __ballot_sync(0xffffffffu, ok);
                     if (lane == 0) s->warp_n[warp] = __popc(m);

@@ -329,7 +329,8 @@ __device__ int gen_chunk(const TcArgs &a, TcSmem *s, GenState &st, int64_t pi0, 
             Rec r;
             if (idx < total) {
                 const PointPos pp = point_position(A, idx, M, key, (uint32_t)(sg - seg0), clip, a.dp);
-                ok = point_record(A, pp, (float)(ix - A.ix_ref) + 0.5f, (float)(iy - A.iy_ref) + 0.5f, fbpp, nb, r);
+                ok = point_record(A, pp, (float)(ix - A.ix_ref) + 0.5f, (float)(iy - A.iy_ref) + 0.5f, fbpp, nb,
+                                  a.c.nearest_lut, r);
             }
             const unsigned m = __ballot_sync(0xffffffffu, ok);
             if (lane == 0) s->u.g.warp_n[warp] = __popc(m);

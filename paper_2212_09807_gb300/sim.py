@@ -53,7 +53,7 @@ class SimConfig(C.Structure):
         ("periodic_reset_ticks", C.c_int32), ("adc_bits", C.c_int32),
         ("seed", C.c_uint64),
         ("precision", C.c_int32), ("fp64_charge", C.c_int32), ("disabled_pixels", C.c_void_p),
-        ("per_point_drift", C.c_int32), ("pad_", C.c_int32),
+        ("per_point_drift", C.c_int32), ("nearest_lut", C.c_int32),
     ]
 
 
@@ -143,9 +143,7 @@ def make_config(cfg: dict) -> SimConfig:
             m = cfg.get(name)
             c.disabled_pixels = None if m is None else int(m.data_ptr())
             continue
-        if name == "pad_":
-            continue
-        v = cfg.get(name, 0) if name in ("precision", "fp64_charge", "per_point_drift") else cfg[name]
+        v = cfg.get(name, 0) if name in ("precision", "fp64_charge", "per_point_drift", "nearest_lut") else cfg[name]
         setattr(c, name, int(v) & 0xFFFFFFFFFFFFFFFF if name == "seed" else (float(v) if ct is C.c_float else int(v)))
     return c
 

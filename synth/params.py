@@ -43,7 +43,7 @@ BASE = dict(
     gain_e_per_mV=250.0, adc_lsb_mV=1000.0 / 256.0, hold_ticks=16,
     min_adc_interval_ticks=11, periodic_reset_ticks=0, adc_bits=8,
     # counter-based RNG seed and arithmetic form of the current step
-    seed=0x221209807, precision=0, fp64_charge=0, per_point_drift=0,
+    seed=0x221209807, precision=0, fp64_charge=0, per_point_drift=0, nearest_lut=0,
 )
 
 # Field-response look-up table (synthetic closed form, see synth.response)

@@ -96,3 +96,34 @@ def test_per_point_drift_against_oracle(precision):
     cfg0 = dict(cfg, per_point_drift=0)
     st0 = Steps(cfg0, seg, lut_dev, event_id=4).quench_drift().pixel_map().induced_current()
     assert abs(st0.current_np().sum() / cur.sum() - 1.0) > 1e-4
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_nearest_lookup_against_oracle(precision):
+    """Nearest-bin lookup: every pixel against the oracle.  A point whose
+    nearest-node or nearest-tick rounding lies within 1e-3 (bins, ticks) of
+    its half-way point may round the other way in FP32: each such point may
+    move its charge q to another table row, so the allowed difference is the
+    form's tolerance plus 2 q max|R| per tied point (counted by the oracle)."""
+    cfg = params.small_config(nearest_lut=1, precision=precision)
+    seg = events.scatter_event(cfg, 411, 50, max_len=0.8)
+    lut_dev, lut64 = lut_pair(cfg)
+    st = Steps(cfg, seg, lut_dev, event_id=6).quench_drift().pixel_map().induced_current()
+    m, cur = st.maps_np(), st.current_np()
+    o = oracle.Oracle(cfg, params.LUT, lut64)
+    d = o.quench_drift(seg)
+    rmax = float(np.abs(lut64).max())
+    tol = 1e-4 if precision == 0 else 1e-3
+    n_ties_total, checked = 0, 0
+    for i, p in enumerate(m["active"]):
+        segs = m["pix_ids"][m["pix_off"][i]:m["pix_off"][i + 1]]
+        ref, n_ties = o.pixel_current(seg, d, int(p), segs, event_id=6, tie_band=1e-3)
+        if np.abs(ref).sum() < 1.0:
+            continue
+        qmax = max(d["Qa"][s] / d["n_samples"][s] for s in segs if d["n_samples"][s] > 0)
+        bound = tol * np.abs(ref).max() + n_ties * 2 * qmax * rmax
+        assert np.abs(cur[i] - ref).max() <= bound, (p, n_ties)
+        n_ties_total += n_ties
+        checked += 1
+    print(f"nearest lookup, precision {precision}: pixels {checked}, tied points {n_ties_total}")
+    assert checked > 100

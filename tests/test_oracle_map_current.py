@@ -383,3 +383,48 @@ def test_per_point_drift_map_width_is_the_farther_end():
         t = far / float(np.float32(cfg["vdrift_cm_us"]))
         np.testing.assert_allclose(d["sigma_T"][s], np.sqrt(2 * float(np.float32(cfg["diff_tran_cm2_s"])) * 1e-6 * t),
                                    rtol=1e-12)
+
+
+@pytest.mark.parametrize("bx,by,frac", [(3, 7, 0.3), (10, 0, 0.7), (44, 20, 0.2)])
+def test_nearest_lookup_reads_the_nearest_node_and_tick(bx, by, frac):
+    """Nearest-bin variant: a point charge 0.3 bin off node (bx, by), arriving
+    `frac` of a tick after tick 64, reads that node's table row shifted to the
+    nearest tick, exactly."""
+    cfg = _exact_cfg(nearest_lut=1)
+    lut = np.random.default_rng(bx * 7 + by).random((45, 45, 64))
+    o = oracle.Oracle(cfg, LUT_SMALL, lut)
+    p, h = 0.46875, 0.46875 / 30
+    xc, yc = 10.5 * p, 20.5 * p
+    z = 1.0 + frac * 0.125 * 0.125                # arrival tick 64 + frac
+    seg = _seg([_point(xc, yc, (bx + 0.5 + 0.3) * h, (by + 0.5 - 0.3) * h, z)])
+    d = o.quench_drift(seg)
+    assert d["n_samples"][0] == 1
+    I = o.pixel_current(seg, d, 20 * 70 + 10, [0])
+    A = 64 + (1 if frac >= 0.5 else 0)
+    exp = np.zeros(128)
+    for k in range(128):
+        j = k - A + 64 - 1
+        if 0 <= j < 64:
+            exp[k] = d["Qa"][0] * lut[bx, by, j]
+    assert np.array_equal(I, exp)
+
+
+def test_nearest_lookup_conserves_charge():
+    """Nearest-bin variant: the pitch is a whole number of bins, so every
+    pixel's nearest node sits at the same sub-bin position and the table's
+    partition of unity still holds: charge is conserved."""
+    cfg = params.small_config(nearest_lut=1, n_ticks=4000, t_window0_us=-200.0)
+    lut = response.lut_for(cfg, params.LUT)
+    o = oracle.Oracle(cfg, params.LUT, lut)
+    rng = np.random.default_rng(22)
+    rows = []
+    for z in (3.0, 17.0, 41.0):
+        x, y = 10 + 30 * rng.random(), 10 + 30 * rng.random()
+        w = rng.normal(size=3)
+        w *= 0.25 / np.linalg.norm(w)
+        rows.append((x, y, z, 0, x + w[0], y + w[1], z + w[2], 0, 0.5))
+    seg = _seg(rows)
+    d = o.quench_drift(seg)
+    pix, _, _, _ = o.pixel_map(seg, d)
+    total = sum(o.pixel_current(seg, d, p, s).sum() for p, s in pix.items())
+    assert abs(total / d["Qa"].sum() - 1.0) < 1e-12
