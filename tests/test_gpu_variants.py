@@ -92,10 +92,14 @@ def test_per_point_drift_against_oracle(precision):
     rel, qrel = current_errors(cur[sig], ref[sig])
     print(f"per-point drift, precision {precision}: pixels {sig.sum()} rel max {rel.max():.2e} q max {qrel.max():.2e}")
     assert rel.max() <= (1e-4 if precision == 0 else 1e-3)
-    # the lifetime is visible: per-segment attenuation gives a different charge
+    # the variant is visible: per-segment drift distributes the charge differently along the
+    # segments (the totals agree to second order), compared on the pixels both maps hold
     cfg0 = dict(cfg, per_point_drift=0)
     st0 = Steps(cfg0, seg, lut_dev, event_id=4).quench_drift().pixel_map().induced_current()
-    assert abs(st0.current_np().sum() / cur.sum() - 1.0) > 1e-4
+    a0 = st0.maps_np()["active"]
+    common, i1, i0 = np.intersect1d(m["active"], a0, return_indices=True)
+    diff = np.abs(cur[i1] - st0.current_np()[i0]).max() / np.abs(cur[i1]).max()
+    assert diff > 1e-3, diff
 
 
 @pytest.mark.parametrize("precision", [0, 2])
