@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip timing the other induced-current forms")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-vs-plain request stream")
     ap.add_argument("--serving-requests", type=int, default=12)
+    ap.add_argument("--batched-events", type=int, default=32)
+    ap.add_argument("--batched-hi", type=float, default=1.0e4, help="largest event of the batched comparison")
     return ap.parse_args()
 
 
@@ -221,10 +223,11 @@ def batched_vs_plain(cfg, lut, dev, n_events=32, lo=1.0e3, hi=1.0e4, reps=2):
     sizes = [len(e["x0"]) for e in evs]
     total, big = sum(sizes), max(sizes)
     ids = list(range(1000, 1000 + n_events))
-    plain = sim.EventRunner(cfg, lut, params.LUT["nt"], params.LUT["bins_per_pitch"], big, 40 * big, 4 * big,
-                            4 * big, device=dev)
-    batch_run = sim.EventRunner(cfg, lut, params.LUT["nt"], params.LUT["bins_per_pitch"], total, 40 * total,
-                                4 * total, 4 * total, device=dev, max_events=n_events)
+    from paper_2212_09807_gb300 import serve
+    plain = sim.EventRunner(cfg, lut, params.LUT["nt"], params.LUT["bins_per_pitch"], big, *serve._caps(big),
+                            device=dev)
+    batch_run = sim.EventRunner(cfg, lut, params.LUT["nt"], params.LUT["bins_per_pitch"], total,
+                                *serve._caps(total), device=dev, max_events=n_events)
     singles = [sim.Segments.from_numpy(e, i, dev) for e, i in zip(evs, ids)]
     batch = sim.Segments.batch_from_numpy(evs, ids, dev)
     best_plain, best_batch, lat = None, None, None
@@ -487,7 +490,8 @@ def run_ours(args):
     del run, io
     torch.cuda.empty_cache()
 
-    batched = batched_vs_plain(cfg, lut, dev) if not args.no_batched else None
+    batched = (batched_vs_plain(cfg, lut, dev, args.batched_events, 1.0e3, args.batched_hi,
+                                reps=1 if args.batched_events > 64 else 2) if not args.no_batched else None)
     serving = serving_vs_plain(args.precision, dev, args.serving_requests) if not args.no_serving else None
 
     cpu = None
