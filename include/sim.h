@@ -22,7 +22,10 @@
  *    npx_x = tiles_x * px_per_tile, npx_y = tiles_y * px_per_tile.
  *  - Results depend only on (config, segments, event_id, seed), not on thread
  *    order or batch composition (the paper's requirement that a result must
- *    not depend on the order of execution of the threads, Sec. 2).
+ *    not depend on the order of execution of the threads, Sec. 2).  The
+ *    tensor-core current forms (sim_config.precision 1, 2) are bitwise
+ *    reproducible call by call; across batch compositions or pixel slices
+ *    their currents agree to their accumulation rounding (~1e-7).
  */
 #ifndef LARPIX_GB300_SIM_H
 #define LARPIX_GB300_SIM_H
