@@ -75,7 +75,7 @@ bool hits_ok(const sim_hits *h)
 // Scratch and launch of the induced-current form selected by cfg.precision.
 size_t current_scratch(const sim_config &c, int64_t pixels)
 {
-    return c.precision == 0 ? current_scratch_bytes(pixels) : current_tc_scratch_bytes(pixels);
+    return c.precision == 0 ? current_scratch_bytes(pixels) : current_tc_scratch_bytes(pixels, c.n_ticks);
 }
 
 cudaError_t launch_current(const sim_config &c, const sim_segments &s, const sim_drifted &d, const sim_response &r,

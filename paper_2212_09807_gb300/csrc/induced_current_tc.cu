@@ -39,6 +39,8 @@
 //    lane = tick) and store the currents.
 // Every mbarrier wait is bounded; a wait that gives up sets
 // SIM_STATUS_TIMEOUT in the status word and the CTA drains and returns.
+#include <algorithm>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -58,8 +60,9 @@ constexpr int kSlots = 16;                  // blocks per operand batch
 constexpr int kMaxBins = 2048;              // nb * nb <= kMaxBins
 constexpr int kMaxRows = 2304;              // im2col rows: rho0 + 128 for nt <= 2048
 constexpr int kRowBytes = 32;               // 16 FP16 per im2col row
-constexpr int kRecCap = 1 << 17;            // records per chunk per CTA
-constexpr int kSubsPerSm = 4;               // work-balanced sub-groups per SM (target)
+constexpr int kRecCap = 1 << 18;            // records per chunk per CTA
+constexpr int kSubsPerSm = 2;               // work-balanced units per SM (target)
+constexpr int kMaxSplit = 16;               // table-node ranges a pixel group may be cut into
 constexpr int kFlushNodes = 64;             // nodes per accumulation window (see flush_acc)
 constexpr float kFix = 4096.f;              // fixed-point scale of the charge accumulators (2^-12 e-)
 constexpr int kIssuers = 4;
@@ -93,6 +96,15 @@ struct __align__(1024) TcSmem {
     int n_nodes, group, abort;
 };
 
+// A unit of work: the pixel group [first, first + count) of the active list,
+// restricted to the table nodes with bx in [nb r / k, nb (r + 1) / k).  Units
+// of a group split in k > 1 write partial currents to `slice` (else -1).
+struct __align__(16) Unit {
+    int first, count, r, k;
+    int slice, pad;
+    long long work;
+};
+
 struct TcArgs {
     sim_config c;
     int nb, nt, bpp, rho0, im_bytes;
@@ -111,9 +123,10 @@ struct TcArgs {
     Geo g;
     DriftPar dp;
     int *queue;                             // next entry of `order`
-    const int4 *subs;                       // sub-groups {first pixel, pixels, work lo, work hi}
-    const int32_t *order;                   // sub-groups by decreasing work
-    const int64_t *n_subs;
+    const Unit *units;
+    const int32_t *order;                   // units by decreasing work
+    const int64_t *n_units;
+    float *slices;                          // partial currents [slice][kGroup][n_ticks]
     Rec *recs, *sorted;                     // [grid][kRecCap]
     int *offt;                              // [grid][kGroup][kMaxBins + 1]
 };
@@ -291,8 +304,8 @@ struct GenState {
 // chunk buffer is full or the group is done; sorts each pixel's part by bin
 // into `sorted`, writes its bin offsets to offt, marks the nodes it touches.
 // Returns the number of records of the chunk; st.gp == npg when done.
-__device__ int gen_chunk(const TcArgs &a, TcSmem *s, GenState &st, int64_t pi0, int npg, Rec *recs, Rec *sorted,
-                         int *offt)
+__device__ int gen_chunk(const TcArgs &a, TcSmem *s, GenState &st, int64_t pi0, int npg, int bx_lo, int bx_hi,
+                         Rec *recs, Rec *sorted, int *offt)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nb = a.nb, nb2 = nb * nb, M = a.c.mc_per_sample;
@@ -319,7 +332,19 @@ __device__ int gen_chunk(const TcArgs &a, TcSmem *s, GenState &st, int64_t pi0, 
             const int sg = a.segs[st.e];
             const Anchor A = a.anch[sg];
             const int total = A.N * M;
-            if (st.base >= total) {
+            bool skip = st.base >= total;
+            if (!skip && (bx_lo > 0 || bx_hi < nb)) {
+                // table rows bx this segment's points can reach from this pixel: its x-offsets
+                // span [d0, d1] (pitch units) widened by the diffusion clip; one bin of margin
+                const float cx = (float)(ix - A.ix_ref) + 0.5f;
+                const float d0 = A.fx0 - cx, d1 = A.fx0 + A.dX - cx, w = clip * A.sTp;
+                const float dmin = (d0 * d1 <= 0.f) ? 0.f : fminf(fabsf(d0), fabsf(d1));
+                const float dmax = fmaxf(fabsf(d0), fabsf(d1));
+                const int rmin = (int)floorf(fmaxf((dmin - w) * fbpp - 0.5f, 0.f)) - 1;
+                const int rmax = (int)floorf(fmaxf((dmax + w) * fbpp - 0.5f, 0.f)) + 1;
+                skip = rmax + 1 < bx_lo || rmin >= bx_hi;   // records' corners span rows bx, bx + 1
+            }
+            if (skip) {
                 ++st.e;
                 st.base = 0;
                 continue;
@@ -331,6 +356,10 @@ __device__ int gen_chunk(const TcArgs &a, TcSmem *s, GenState &st, int64_t pi0, 
                 const PointPos pp = point_position(A, idx, M, key, (uint32_t)(sg - seg0), clip, a.dp);
                 ok = point_record(A, pp, (float)(ix - A.ix_ref) + 0.5f, (float)(iy - A.iy_ref) + 0.5f, fbpp, nb,
                                   a.c.nearest_lut, r);
+                if (ok) {                       // corner nodes (bx, bx + 1) must reach the unit's range
+                    const int bx = r.b0 / nb;
+                    ok = bx < bx_hi && bx + 1 >= bx_lo;
+                }
             }
             const unsigned m = __ballot_sync(0xffffffffu, ok);
             if (lane == 0) s->u.g.warp_n[warp] = __popc(m);
@@ -375,12 +404,14 @@ __device__ int gen_chunk(const TcArgs &a, TcSmem *s, GenState &st, int64_t pi0, 
                 if (b < nb2) {
                     orow[b] = pv;
                     s->u.g.hist[b] = pv;
-                    if (v[i] > 0) {
+                    if (v[i] > 0) {                 // the bin's corner nodes within the unit's range
                         const int bx = b / nb, by = b - bx * nb;
-                        s->u.g.nflag[b] = 1;
-                        if (bx + 1 < nb) s->u.g.nflag[b + nb] = 1;
-                        if (by + 1 < nb) s->u.g.nflag[b + 1] = 1;
-                        if (bx + 1 < nb && by + 1 < nb) s->u.g.nflag[b + nb + 1] = 1;
+                        const bool in0 = bx >= bx_lo && bx < bx_hi;
+                        const bool in1 = bx + 1 < nb && bx + 1 >= bx_lo && bx + 1 < bx_hi;
+                        if (in0) s->u.g.nflag[b] = 1;
+                        if (in1) s->u.g.nflag[b + nb] = 1;
+                        if (in0 && by + 1 < nb) s->u.g.nflag[b + 1] = 1;
+                        if (in1 && by + 1 < nb) s->u.g.nflag[b + nb + 1] = 1;
                     }
                 }
                 pv += v[i];
@@ -638,11 +669,13 @@ __device__ void issue_mmas(const TcArgs &a, TcSmem *s, int w, const unsigned sho
 
 
 // ------------------------------------------------------ work planning ----
-// Pixel groups are cut into sub-groups of balanced work: the work of a pixel
-// is estimated by its candidate points sum_{s -> p} N_s M; a 32-pixel group
-// is split into k (a power of two <= 32) sub-groups of 32 / k pixels so that
-// each holds at most total / (kSubsPerSm * SMs); sub-groups are then taken
-// in order of decreasing work.
+// Units of balanced work: the work of a pixel is estimated by its candidate
+// points sum_{s -> p} N_s M; a 32-pixel group whose work exceeds
+// wcap = total / (kSubsPerSm * SMs) is cut into k (a power of two <= 16)
+// units by ranges of table-node rows bx, so that each unit holds at most about
+// wcap.  The units of a group issue disjoint MMAs (each node belongs to one
+// range); they write partial currents that k_plan_reduce adds in unit order.
+// Units are taken from the queue in order of decreasing work.
 
 // Active pixels of the call's range [begin, min(counts[1], end)), counted from begin.
 __device__ __forceinline__ int64_t active_count(const int64_t *counts, int64_t pix_cap, int64_t begin, int64_t end)
@@ -668,8 +701,10 @@ __global__ void k_plan_work(const int64_t *counts, int64_t pix_cap, int64_t begi
     if ((threadIdx.x & 31) == 0 && w) atomicAdd(total, (unsigned long long)w);
 }
 
+// Number of units of each group (nunit) and of partial slices (nslice: k when k > 1).
 __global__ void k_plan_split(const int64_t *counts, int64_t pix_cap, int64_t begin, int64_t end, const long long *pwork,
-                             const unsigned long long *total, int target, int32_t *nsub, int64_t ngroups_cap)
+                             const unsigned long long *total, int target, int32_t *nunit, int32_t *nslice,
+                             int64_t ngroups_cap)
 {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ngroups_cap) return;
@@ -678,47 +713,50 @@ __global__ void k_plan_split(const int64_t *counts, int64_t pix_cap, int64_t beg
     if (g * kGroup < npix) {
         long long gw = 0;
         for (int64_t p = g * kGroup; p < min(npix, (g + 1) * kGroup); ++p) gw += pwork[p];
-        const long long wcap = max(1ll, (long long)(*total / (unsigned long long)target));
+        // wcap rounded up: the split units then number fewer than 2 * target in all
+        const long long wcap = max(1ll, (long long)((*total + (unsigned long long)target - 1) / (unsigned long long)target));
         k = 1;
-        while (k < kGroup && gw > wcap * k) k <<= 1;
+        while (k < kMaxSplit && gw > wcap * k) k <<= 1;
     }
-    nsub[g] = k;
+    nunit[g] = k;
+    nslice[g] = k > 1 ? k : 0;
 }
 
 __global__ void k_plan_emit(const int64_t *counts, int64_t pix_cap, int64_t begin, int64_t end, const long long *pwork,
-                            const int32_t *nsub,
-                            const int32_t *pos, int4 *subs, int64_t ngroups_cap)
+                            const int32_t *nunit, const int32_t *pos, const int32_t *spos, Unit *units,
+                            int64_t ngroups_cap)
 {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ngroups_cap) return;
-    const int k = nsub[g];
+    const int k = nunit[g];
     if (k == 0) return;
     const int64_t npix = active_count(counts, pix_cap, begin, end);
-    const int size = kGroup / k;
-    for (int j = 0; j < k; ++j) {
-        const int64_t first = g * kGroup + (int64_t)j * size;
-        const int cnt = (int)max((int64_t)0, min((int64_t)size, npix - first));
-        long long w = 0;
-        for (int i = 0; i < cnt; ++i) w += pwork[first + i];
-        subs[pos[g] + j] = make_int4((int)(begin + first), cnt, (int)(w & 0xffffffffll), (int)(w >> 32));
+    const int cnt = (int)min((int64_t)kGroup, npix - g * kGroup);
+    long long w = 0;
+    for (int i = 0; i < cnt; ++i) w += pwork[g * kGroup + i];
+    for (int r = 0; r < k; ++r) {
+        Unit u;
+        u.first = (int)(begin + g * kGroup);
+        u.count = cnt;
+        u.r = r;
+        u.k = k;
+        u.slice = k > 1 ? spos[g] + r : -1;
+        u.pad = 0;
+        u.work = w / k;
+        units[pos[g] + r] = u;
     }
 }
 
-__device__ __forceinline__ long long sub_work(const int4 &v)
-{
-    return (long long)(((unsigned long long)(unsigned)v.w << 32) | (unsigned)v.z);
-}
-
 // order[rank] = j, rank by decreasing work, ties by index.
-__global__ void k_plan_rank(const int4 *subs, const int64_t *n_subs, int32_t *order)
+__global__ void k_plan_rank(const Unit *units, const int64_t *n_units, int32_t *order)
 {
     __shared__ long long tile[1024];
-    const int64_t n = *n_subs;
+    const int64_t n = *n_units;
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long wj = j < n ? sub_work(subs[j]) : 0;
+    const long long wj = j < n ? units[j].work : 0;
     int rank = 0;
     for (int64_t t0 = 0; t0 < n; t0 += 1024) {
-        for (int i = threadIdx.x; i < 1024; i += blockDim.x) tile[i] = t0 + i < n ? sub_work(subs[t0 + i]) : 0;
+        for (int i = threadIdx.x; i < 1024; i += blockDim.x) tile[i] = t0 + i < n ? units[t0 + i].work : 0;
         __syncthreads();
         if (j < n) {
             const int m = (int)min((int64_t)1024, n - t0);
@@ -732,14 +770,35 @@ __global__ void k_plan_rank(const int4 *subs, const int64_t *n_subs, int32_t *or
     if (j < n) order[rank] = (int32_t)j;
 }
 
+// Current of the pixels of split groups: the partial slices of the group's
+// units added in unit order (one CTA per group).
+__global__ void k_plan_reduce(const int64_t *counts, int64_t pix_cap, int64_t begin, int64_t end,
+                              const int32_t *nunit, const int32_t *spos, const float *slices, int T, float *current,
+                              int64_t ngroups_cap)
+{
+    const int64_t g = blockIdx.x;
+    if (g >= ngroups_cap) return;
+    const int k = nunit[g];
+    if (k <= 1) return;
+    const int64_t npix = active_count(counts, pix_cap, begin, end);
+    const int cnt = (int)min((int64_t)kGroup, npix - g * kGroup);
+    const float *src = slices + (size_t)spos[g] * kGroup * T;
+    float *dst = current + (size_t)(begin + g * kGroup) * T;
+    for (int i = threadIdx.x; i < cnt * T; i += blockDim.x) {
+        float v = src[i];
+        for (int r = 1; r < k; ++r) v += src[(size_t)r * kGroup * T + i];
+        dst[i] = v;
+    }
+}
+
 // Warps 0-3 (all lanes): waits for every MMA issued so far, adds the
-// accumulators to the current rows of the group (stores them when `first`),
-// and zeroes them.  The tensor cores' FP32 accumulation truncates: summing a
+// accumulators to the output rows of the unit (`rows`: the group's current
+// rows, or its partial slice; stores them when `first`), and zeroes them.  The tensor cores' FP32 accumulation truncates: summing a
 // whole pixel's contributions in one accumulator biased the result low by up
 // to ~2e-3 in the densest pixels; a window of kFlushNodes nodes keeps each
 // accumulator a small fraction of the final value, and the windows are added
 // in FP32 with round-to-nearest (one FMA per window).
-__device__ void flush_acc(const TcArgs &a, TcSmem *s, uint32_t tm, uint32_t &flushes, int k0, int64_t pi0, int npg,
+__device__ void flush_acc(const TcArgs &a, TcSmem *s, uint32_t tm, uint32_t &flushes, int k0, float *rows, int npg,
                           bool first)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -756,7 +815,7 @@ __device__ void flush_acc(const TcArgs &a, TcSmem *s, uint32_t tm, uint32_t &flu
         tmem_ld32(ta, v);
         const int tick = tick0 + 32 * warp + lane;
         if (ok && tick < T) {
-            float *base = a.current + (size_t)pi0 * T + tick;
+            float *base = rows + tick;
             if (!first) {
                 float old[kGroup];                  // all loads in flight before the stores
 #pragma unroll
@@ -785,7 +844,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_induced_current_tc(TcArgs a)
     TcSmem *s = reinterpret_cast<TcSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool go = a.counts[3] == 0 && a.counts[1] <= a.pix_cap;
-    const int64_t nsub = go ? *a.n_subs : 0;
+    const int64_t nsub = go ? *a.n_units : 0;
     const int T = a.c.n_ticks, nb2 = a.nb * a.nb;
     Rec *recs = a.recs + (size_t)blockIdx.x * kRecCap;
     Rec *sorted = a.sorted + (size_t)blockIdx.x * kRecCap;
@@ -827,10 +886,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_induced_current_tc(TcArgs a)
         __syncthreads();
         const int64_t g = s->group;
         if (g >= nsub || *(volatile int *)&s->abort) break;
-        const int4 sub = a.subs[a.order[g]];
-        const int64_t pi0 = sub.x;
-        const int npg = sub.y;
+        const Unit un = a.units[a.order[g]];
+        const int64_t pi0 = un.first;
+        const int npg = un.count;
         if (npg <= 0) continue;
+        const int bx_lo = a.nb * un.r / un.k, bx_hi = a.nb * (un.r + 1) / un.k;
+        float *rows = un.slice < 0 ? a.current + (size_t)pi0 * T : a.slices + (size_t)un.slice * kGroup * T;
         for (int k0 = 0; k0 < T; k0 += kPassTicks) {
             GenState st{0, -1, 0};
             bool first = true;                  // no accumulator window stored yet in this pass
@@ -843,7 +904,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_induced_current_tc(TcArgs a)
                 if (tid < kGroup) s->pin[tid] = 0;
                 __syncthreads();
                 // records keep arrival ticks relative to the pass start
-                const int nrec = gen_chunk(a, s, st, pi0, npg, recs, sorted, offt);
+                const int nrec = gen_chunk(a, s, st, pi0, npg, bx_lo, bx_hi, recs, sorted, offt);
                 {
                     constexpr int kB = kMaxBins / kThreads;
                     int fl[kB], sf = 0;
@@ -878,7 +939,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_induced_current_tc(TcArgs a)
                     __syncthreads();
                     if (warp < 4) {
                         q = __shfl_sync(0xffffffffu, q, 0);   // the two roles agree unless a wait gave up
-                        flush_acc(a, s, tm, flushes, k0, pi0, npg, first);
+                        flush_acc(a, s, tm, flushes, k0, rows, npg, first);
                     }
                     first = false;
                     __syncthreads();
@@ -886,7 +947,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_induced_current_tc(TcArgs a)
             }
             // a pass without records still writes its (zero) currents
             if (first) {
-                if (warp < 4) flush_acc(a, s, tm, flushes, k0, pi0, npg, true);
+                if (warp < 4) flush_acc(a, s, tm, flushes, k0, rows, npg, true);
                 __syncthreads();
             }
         }
@@ -936,10 +997,10 @@ int tc_grid()
 int rho0_of(int L) { return 16 * ((L + 126) / 16); }
 
 struct TcLayout {
-    size_t queue, table, recs, sorted, offt, pwork, nsub, pos, subs, order, scan, total;
+    size_t queue, table, recs, sorted, offt, pwork, nsub, pos, nslice, spos, units, order, slices, scan, total;
 };
 
-TcLayout tc_layout(int grid, int64_t pix_cap)
+TcLayout tc_layout(int grid, int64_t pix_cap, int T)
 {
     TcLayout t;
     size_t o = 0;
@@ -949,12 +1010,17 @@ TcLayout tc_layout(int grid, int64_t pix_cap)
         return at;
     };
     const int64_t ng = (pix_cap + kGroup - 1) / kGroup;
-    t.queue = take(256);                    // [0] queue, [8] work total, [16] sub-group count
+    t.queue = take(256);                    // [0] queue, [8] work total, [16] units, [24] slices
     t.pwork = take(sizeof(long long) * (size_t)pix_cap);
     t.nsub = take(sizeof(int32_t) * (size_t)ng);
     t.pos = take(sizeof(int32_t) * (size_t)(ng + 1));
-    t.subs = take(sizeof(int4) * (size_t)ng * kGroup);
-    t.order = take(sizeof(int32_t) * (size_t)ng * kGroup);
+    t.nslice = take(sizeof(int32_t) * (size_t)ng);
+    t.spos = take(sizeof(int32_t) * (size_t)(ng + 1));
+    t.units = take(sizeof(Unit) * (size_t)ng * kMaxSplit);
+    t.order = take(sizeof(int32_t) * (size_t)ng * kMaxSplit);
+    // split units number fewer than 2 * target (wcap rounded up), at most 16 per group
+    const int64_t max_slices = std::min<int64_t>(2 * (int64_t)kSubsPerSm * grid, ng * kMaxSplit);
+    t.slices = take(sizeof(float) * (size_t)max_slices * kGroup * (size_t)T);
     t.scan = take(scan_scratch_bytes(ng));
     t.table = take((size_t)kMaxBins * kMaxRows * kRowBytes);
     t.recs = take((size_t)grid * kRecCap * sizeof(Rec));
@@ -966,7 +1032,10 @@ TcLayout tc_layout(int grid, int64_t pix_cap)
 
 }  // namespace
 
-size_t current_tc_scratch_bytes(int64_t pix_cap) { return tc_layout(tc_grid(), pix_cap > 0 ? pix_cap : 1).total; }
+size_t current_tc_scratch_bytes(int64_t pix_cap, int T)
+{
+    return tc_layout(tc_grid(), pix_cap > 0 ? pix_cap : 1, T).total;
+}
 
 // Operand scales.  FP16: charge tiles in units of 4 e- (the fixed-point
 // quantum 2^-12 e- becomes 2^-14, the smallest normal FP16 number: the tensor
@@ -983,7 +1052,7 @@ cudaError_t launch_induced_current_tc(const sim_config &c, const sim_segments &s
     if (pix_cap <= 0) return cudaSuccess;
     const int fmt = c.precision == 1 ? 1 : 0;      // 1: BF16, 2: FP16
     const int grid = tc_grid();
-    const TcLayout lay = tc_layout(grid, pix_cap);
+    const TcLayout lay = tc_layout(grid, pix_cap, c.n_ticks);
     char *p = reinterpret_cast<char *>(scratch);
     TcArgs a;
     a.c = c;
@@ -1012,15 +1081,17 @@ cudaError_t launch_induced_current_tc(const sim_config &c, const sim_segments &s
     a.dp = drift_par_of(c);
     a.queue = reinterpret_cast<int *>(p + lay.queue);
     unsigned long long *wtotal = reinterpret_cast<unsigned long long *>(p + lay.queue + 8);
-    int64_t *n_subs = reinterpret_cast<int64_t *>(p + lay.queue + 16);
-    a.n_subs = n_subs;
-    a.subs = reinterpret_cast<const int4 *>(p + lay.subs);
+    int64_t *n_units = reinterpret_cast<int64_t *>(p + lay.queue + 16);
+    int64_t *n_slices = reinterpret_cast<int64_t *>(p + lay.queue + 24);
+    a.n_units = n_units;
+    a.units = reinterpret_cast<const Unit *>(p + lay.units);
     a.order = reinterpret_cast<const int32_t *>(p + lay.order);
+    a.slices = reinterpret_cast<float *>(p + lay.slices);
     a.recs = reinterpret_cast<Rec *>(p + lay.recs);
     a.sorted = reinterpret_cast<Rec *>(p + lay.sorted);
     a.offt = reinterpret_cast<int *>(p + lay.offt);
 
-    cudaError_t e = cudaMemsetAsync(a.queue, 0, 24, st);
+    cudaError_t e = cudaMemsetAsync(a.queue, 0, 32, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.status + 1, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     // work plan
@@ -1028,18 +1099,21 @@ cudaError_t launch_induced_current_tc(const sim_config &c, const sim_segments &s
     long long *pwork = reinterpret_cast<long long *>(p + lay.pwork);
     int32_t *nsub = reinterpret_cast<int32_t *>(p + lay.nsub);
     int32_t *pos = reinterpret_cast<int32_t *>(p + lay.pos);
+    int32_t *nslice = reinterpret_cast<int32_t *>(p + lay.nslice);
+    int32_t *spos = reinterpret_cast<int32_t *>(p + lay.spos);
     k_plan_work<<<(unsigned)((pix_cap + 255) / 256), 256, 0, st>>>(counts, pix_cap, pix_begin, pix_end, pix_seg_off,
                                                                     pix_seg_ids, d.n_samples, c.mc_per_sample, pwork,
                                                                     wtotal);
     k_plan_split<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(counts, pix_cap, pix_begin, pix_end, pwork, wtotal,
-                                                               kSubsPerSm * grid, nsub, ng);
+                                                               kSubsPerSm * grid, nsub, nslice, ng);
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = launch_exclusive_scan(nsub, pos, ng, n_subs, p + lay.scan, st);
+    if (e == cudaSuccess) e = launch_exclusive_scan(nsub, pos, ng, n_units, p + lay.scan, st);
+    if (e == cudaSuccess) e = launch_exclusive_scan(nslice, spos, ng, n_slices, p + lay.scan, st);
     if (e != cudaSuccess) return e;
     k_plan_emit<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(counts, pix_cap, pix_begin, pix_end, pwork, nsub, pos,
-                                                              reinterpret_cast<int4 *>(p + lay.subs), ng);
-    k_plan_rank<<<(unsigned)((ng * kGroup + 255) / 256), 256, 0, st>>>(a.subs, n_subs,
-                                                                      reinterpret_cast<int32_t *>(p + lay.order));
+                                                              spos, reinterpret_cast<Unit *>(p + lay.units), ng);
+    k_plan_rank<<<(unsigned)((ng * kMaxSplit + 255) / 256), 256, 0, st>>>(a.units, n_units,
+                                                                         reinterpret_cast<int32_t *>(p + lay.order));
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int nb2 = r.nb * r.nb;
@@ -1055,6 +1129,10 @@ cudaError_t launch_induced_current_tc(const sim_config &c, const sim_segments &s
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, kThreads, smem, st>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_plan_reduce<<<(unsigned)ng, 256, 0, st>>>(counts, pix_cap, pix_begin, pix_end, nsub, spos, a.slices, c.n_ticks,
+                                                current, ng);
     return cudaGetLastError();
 }
 
