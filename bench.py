@@ -32,8 +32,9 @@ sys.path.insert(0, ROOT)
 from synth import events, params, response  # noqa: E402
 
 # kernels per step: 1 quench/drift + 14 pixel map + 6 electronics, plus the induced current:
-# 1 (FP32 direct) or 9 (tensor cores: work plan 4 + a 3-kernel scan, table unfolding 1, contraction 1)
-KERNELS_PER_STEP = {0: 22, 1: 30, 2: 30}
+# 1 (FP32 direct) or 13 (tensor cores: work plan 4 + two 3-kernel scans, table unfolding 1,
+# contraction 1, reduction of split groups 1)
+KERNELS_PER_STEP = {0: 22, 1: 34, 2: 34}
 FP32_LANES_PER_SM = 128
 
 
@@ -349,14 +350,21 @@ def form_roofline(run, cfg, precision, a4_s, props, sm_mhz, dev):
                 "peak_note": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz",
                 "work_note": "2 flop x 9 pixels x 1950 table ticks per (point, perturbation)"}, samples
     n_mma = int(run.ws[4].item())
+    nnz = int(run.ws[5].item())
+    L = params.LUT["nt"]
     dense = 2.0 * 128 * 32 * 16 * n_mma / a4_s / 1e12
-    tpk = measured_peaks().get("bf16_tflops") or 1900.0
+    useful_q = 2.0 * nnz * L / a4_s / 1e12
+    tpk = measured_peaks().get("bf16_tflops_sustained") or 1700.0
     return {"bound": "tensor", "achieved": dense, "peak": tpk, "unit": "TFLOP/s", "frac": dense / tpk,
             "traffic": stored_traffic("induced_current_tc.cu"), "kernel": "k_induced_current_tc",
-            "mma_per_launch": n_mma, "useful_achieved": useful, "useful_frac": useful / tpk,
-            "peak_note": "measured dense bf16 burst, of measured (fp16 has the same nominal rate)",
-            "work_note": "dense: 2 x 128 x 32 x 16 flop per MMA; useful: 2 flop x 9 pixels x 1950 "
-                         "table ticks per (point, perturbation)"}, samples
+            "mma_per_launch": n_mma, "nnz_charge_cells": nnz,
+            "useful_achieved": useful_q, "useful_frac": useful_q / tpk,
+            "per_point_achieved": useful,
+            "peak_note": "measured dense bf16 sustained (kernel timed inside a step), of measured; fp16 has the "
+                         "same nominal rate",
+            "work_note": "dense: 2 x 128 x 32 x 16 flop per MMA (counted on the device); useful: 2 flop x "
+                         "nnz(Q) x 1950 table ticks (nonzero binned-charge cells, counted on the device); "
+                         "per_point: 2 flop x 9 pixels x 1950 ticks per (point, perturbation)"}, samples
 
 
 SLICE = 32768        # active pixels per current launch of a large request (serving form)

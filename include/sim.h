@@ -212,7 +212,7 @@ int sim_pixel_map(const sim_config *cfg, const sim_segments *seg, const sim_drif
  * the table read bilinearly at the folded transverse offset and linearly at
  * the fractional arrival tick a; summed over segments in increasing index
  * order.  current: FP32 [pix_cap][n_ticks]; rows [0, counts[1]) are written.
- * counts: device int64[5] counts block as written by sim_pixel_map ([1] =
+ * counts: device int64[6] counts block as written by sim_pixel_map ([1] =
  * active pixels, [3] = status); nothing is computed when the status word is
  * nonzero or counts[1] > pix_cap.
  * cfg->precision selects the arithmetic: 0 sums the terms in FP32 in the
@@ -223,7 +223,8 @@ int sim_pixel_map(const sim_config *cfg, const sim_segments *seg, const sim_drif
  * in fixed point (2^-12 e-) and rounded to the operand type, as is R; FP16 Q
  * cells saturate at 262016 e-.  Results are bitwise reproducible for a given
  * call; counts[4] receives the number of tensor-core MMA instructions
- * (M = 128, N = 32, K = 16) of the call, and SIM_STATUS_TIMEOUT is set if a
+ * (M = 128, N = 32, K = 16) of the call and counts[5] the number of nonzero
+ * charge cells Q[p, n, a] it contracted, and SIM_STATUS_TIMEOUT is set if a
  * bounded device-side wait gave up.
  * Workspace (scratch from byte 256 on): sim_workspace_size(cfg, 0, 0, 0,
  * pix_cap) bytes, sized for the current device (per-CTA record buffers; with

@@ -115,7 +115,7 @@ struct TcArgs {
     const Anchor *anch;
     const int32_t *active, *off, *segs;
     const int64_t *counts;
-    unsigned long long *status;             // counts[3]; counts[4] receives the MMA count
+    unsigned long long *status;             // counts[3]; counts[4], [5] receive the MMA and nonzero-cell counts
     int64_t pix_cap;
     float *current;
     uint64_t seed;
@@ -457,7 +457,7 @@ __device__ __forceinline__ int find_list(const int *off, int k)
 // an abort they stop at the next node.
 template <int FMT>
 __device__ void build_batches(const TcArgs &a, TcSmem *s, const Rec *sorted, const int *offt,
-                              const unsigned short *nodes, int nn, uint32_t &q)
+                              const unsigned short *nodes, int nn, uint32_t &q, unsigned long long &n_cells)
 {
     constexpr int U = 4;                                // records in flight per thread
     const int bt = threadIdx.x - 128, lane = bt & 31, cw = bt >> 5;
@@ -584,6 +584,8 @@ __device__ void build_batches(const TcArgs &a, TcSmem *s, const Rec *sorted, con
             for (int j = bt; j < count * kGroup * 2; j += 128) {
                 const int sl = j >> 6, p = j & (kGroup - 1), h = (j >> 5) & 1;
                 const int *ac = s->u.acc + (sl * kBlk + 8 * h) * kGroup + p;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) n_cells += ac[e * kGroup] != 0;   // nonzero charge cells
                 uint4 v;
                 v.x = pack2<FMT>((float)ac[0 * kGroup] * a.qscale, (float)ac[1 * kGroup] * a.qscale);
                 v.y = pack2<FMT>((float)ac[2 * kGroup] * a.qscale, (float)ac[3 * kGroup] * a.qscale);
@@ -878,6 +880,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_induced_current_tc(TcArgs a)
 
     uint32_t S = 0, q = 0, flushes = 0;     // node, batch and flush sequence numbers (barrier phases)
     unsigned long long n_mma = 0;           // MMAs issued by this thread
+    unsigned long long n_cells = 0;         // nonzero charge cells converted by this thread
     for (;;) {
         tc_fence_before();
         __syncthreads();
@@ -931,7 +934,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_induced_current_tc(TcArgs a)
                 for (int u0 = 0; u0 < nn; u0 += kFlushNodes) {
                     const int cnt = min(kFlushNodes, nn - u0);
                     if (warp >= 4) {
-                        build_batches<FMT>(a, s, sorted, offt, s->nodes + u0, cnt, q);
+                        build_batches<FMT>(a, s, sorted, offt, s->nodes + u0, cnt, q, n_cells);
                     } else if (lane == 0) {
                         issue_mmas(a, s, warp, s->nodes + u0, cnt, S, q, k0, n_mma);
                     }
@@ -956,6 +959,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_induced_current_tc(TcArgs a)
     __syncthreads();
     if (tid == 0 && s->abort) atomicOr(a.status, (unsigned long long)SIM_STATUS_TIMEOUT);
     if (warp < 4 && lane == 0 && n_mma) atomicAdd(a.status + 1, n_mma);
+    if (warp >= 4) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) n_cells += __shfl_down_sync(0xffffffffu, n_cells, o);
+        if (lane == 0 && n_cells) atomicAdd(a.status + 2, n_cells);
+    }
     if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kTmemCols) : "memory");
@@ -1092,7 +1100,7 @@ cudaError_t launch_induced_current_tc(const sim_config &c, const sim_segments &s
     a.offt = reinterpret_cast<int *>(p + lay.offt);
 
     cudaError_t e = cudaMemsetAsync(a.queue, 0, 32, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(a.status + 1, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.status + 1, 0, 2 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     // work plan
     const int64_t ng = (pix_cap + kGroup - 1) / kGroup;
