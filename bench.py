@@ -225,12 +225,29 @@ def batched_vs_plain(cfg, lut, dev, n_events=32, lo=1.0e3, hi=1.0e4, reps=2):
     total, big = sum(sizes), max(sizes)
     ids = list(range(1000, 1000 + n_events))
     from paper_2212_09807_gb300 import serve
-    plain = sim.EventRunner(cfg, lut, params.LUT["nt"], params.LUT["bins_per_pitch"], big, *serve._caps(big),
-                            device=dev)
-    batch_run = sim.EventRunner(cfg, lut, params.LUT["nt"], params.LUT["bins_per_pitch"], total,
-                                *serve._caps(total), device=dev, max_events=n_events)
     singles = [sim.Segments.from_numpy(e, i, dev) for e, i in zip(evs, ids)]
     batch = sim.Segments.batch_from_numpy(evs, ids, dev)
+
+    def fitted(n, caps, runs, max_events=0):
+        """Runner whose capacities fit every event of `runs` (untimed sizing pass)."""
+        while True:
+            r = sim.EventRunner(cfg, lut, params.LUT["nt"], params.LUT["bins_per_pitch"], n, *caps, device=dev,
+                                max_events=max_events)
+            worst = [0, 0, 0]
+            for sg in runs:
+                r.enqueue(sg)
+                torch.cuda.synchronize()
+                c = r.counts()
+                if c[3] != 0:
+                    worst = [max(w, x) for w, x in zip(worst, c[:3])]
+            if worst == [0, 0, 0]:
+                return r
+            caps = tuple(max(a, 2 * w) for a, w in zip(caps, worst))
+            del r
+            torch.cuda.empty_cache()
+
+    plain = fitted(big, serve._caps(big), singles)
+    batch_run = fitted(total, serve._caps(total), [batch], max_events=n_events)
     best_plain, best_batch, lat = None, None, None
     for _ in range(reps):
         marks = [torch.cuda.Event(enable_timing=True) for _ in range(n_events + 1)]
