@@ -51,7 +51,7 @@ def parse():
                     help="induced-current form of the headline: 0 FP32 direct, 1 BF16 / 2 FP16 tensor cores")
     ap.add_argument("--no-forms", action="store_true", help="skip timing the other induced-current forms")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-vs-plain request stream")
-    ap.add_argument("--serving-requests", type=int, default=12)
+    ap.add_argument("--serving-requests", type=int, default=10, help="requests per load point")
     ap.add_argument("--batched-events", type=int, default=32)
     ap.add_argument("--batched-hi", type=float, default=1.0e4, help="largest event of the batched comparison")
     return ap.parse_args()
@@ -387,12 +387,12 @@ def form_roofline(run, cfg, precision, a4_s, props, sm_mhz, dev):
 SLICE = 32768        # active pixels per current launch of a large request (serving form)
 
 
-def serving_vs_plain(precision, dev, n_requests=12, load=0.7, seed_off=20):
+def serving_vs_plain(precision, dev, n_requests=12, loads=(0.5, 0.7, 0.9), seed_off=20):
     """Serving form against the plain per-event form on the same Poisson
-    request stream: 80 % single interactions (~2e4 segments) and 20 % whole
+    request streams: 80 % single interactions (~2e4 segments) and 20 % whole
     spills (~1.2e6 segments) on the 35-module detector; the arrival rate is
-    `load` times the plain form's capacity (measured on one request of each
-    kind first)."""
+    each of `loads` times the plain form's capacity (measured on one request
+    of each kind first)."""
     import torch
     from paper_2212_09807_gb300 import serve
     cfg = params.spill_config(precision=precision)
@@ -408,24 +408,27 @@ def serving_vs_plain(precision, dev, n_requests=12, load=0.7, seed_off=20):
     t_int = res[1].done - res[1].admitted
     t_sp = res[2].done - res[2].admitted
     mean_service = 0.8 * t_int + 0.2 * t_sp
-    rate = load / mean_service
-    rng = np.random.default_rng(seed)
-    t, reqs = 0.0, []
-    for i in range(n_requests):
-        t += rng.exponential(1.0 / rate)
-        if rng.random() < 0.2:
-            reqs.append(serve.Request(i, 5000 + i, spill, t, "spill"))
-        else:
-            reqs.append(serve.Request(i, 5000 + i, inter[i % len(inter)], t, "interaction"))
-    plain = serve.summarize(serve.run_plain(cfg, lut, nt, bpp, reqs, device=dev))
-    torch.cuda.empty_cache()
-    srv = serve.Server(cfg, lut, nt, bpp, hbm_budget=120e9, slice_pixels=SLICE, max_jobs=8, device=dev)
-    serving = serve.summarize(srv.run(reqs))
-    torch.cuda.empty_cache()
-    return {"requests": n_requests, "mix": "80% interactions (~2e4 segments), 20% spills (~1.2e6 segments), "
-            "35-module detector", "load": load, "rate_per_s": rate,
-            "plain_service_ms": {"interaction": t_int * 1e3, "spill": t_sp * 1e3},
-            "hbm_budget_gb": 120, "slice_pixels": SLICE, "plain": plain, "serving": serving}
+    out = []
+    for li, load in enumerate(loads):
+        rate = load / mean_service
+        rng = np.random.default_rng(seed + li)
+        t, reqs = 0.0, []
+        for i in range(n_requests):
+            t += rng.exponential(1.0 / rate)
+            if rng.random() < 0.2:
+                reqs.append(serve.Request(i, 5000 + i, spill, t, "spill"))
+            else:
+                reqs.append(serve.Request(i, 5000 + i, inter[i % len(inter)], t, "interaction"))
+        plain = serve.summarize(serve.run_plain(cfg, lut, nt, bpp, reqs, device=dev))
+        torch.cuda.empty_cache()
+        srv = serve.Server(cfg, lut, nt, bpp, hbm_budget=120e9, slice_pixels=SLICE, max_jobs=8, device=dev)
+        serving = serve.summarize(srv.run(reqs))
+        del srv
+        torch.cuda.empty_cache()
+        out.append({"load": load, "rate_per_s": rate, "plain": plain, "serving": serving})
+    return {"requests_per_load": n_requests, "mix": "80% interactions (~2e4 segments), 20% spills (~1.2e6 "
+            "segments), 35-module detector", "plain_service_ms": {"interaction": t_int * 1e3, "spill": t_sp * 1e3},
+            "hbm_budget_gb": 120, "slice_pixels": SLICE, "loads": out}
 
 
 def run_ours(args):

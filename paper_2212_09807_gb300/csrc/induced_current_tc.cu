@@ -180,8 +180,10 @@ __device__ __forceinline__ void bar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
 }
 
-// Bounded wait for the completion of the phase with the given parity.
-__device__ __forceinline__ bool bar_wait(TcSmem *s, uint64_t *bar, uint32_t parity)
+// Bounded wait for the completion of the phase with the given parity.  After
+// an abort it returns false at once, unless honor_abort is false (teardown
+// waits for the CTA's own MMAs and copies, which always complete).
+__device__ __forceinline__ bool bar_wait(TcSmem *s, uint64_t *bar, uint32_t parity, bool honor_abort = true)
 {
     for (int it = 0; it < kMaxSpin; ++it) {
         uint32_t ok;
@@ -191,7 +193,7 @@ __device__ __forceinline__ bool bar_wait(TcSmem *s, uint64_t *bar, uint32_t pari
                      : "r"(saddr(bar)), "r"(parity)
                      : "memory");
         if (ok) return true;
-        if (*(volatile int *)&s->abort) return false;
+        if (honor_abort && *(volatile int *)&s->abort) return false;
     }
     atomicExch(&s->abort, 1);
     return false;
@@ -617,7 +619,7 @@ __device__ void build_batches(const TcArgs &a, TcSmem *s, const Rec *sorted, con
 
 // Issuer thread of warp w (0-3): MMAs of tiles t = w, w + 4, ... for every batch.
 __device__ void issue_mmas(const TcArgs &a, TcSmem *s, int w, const unsigned short *nodes, int nn, uint32_t S,
-                           uint32_t &q, int k0, unsigned long long &n_mma)
+                           uint32_t &q, int k0, unsigned long long &n_mma, int64_t (&im_last)[2])
 {
     const int T = a.c.n_ticks;
     const uint32_t tm = s->taddr;
@@ -626,6 +628,7 @@ __device__ void issue_mmas(const TcArgs &a, TcSmem *s, int w, const unsigned sho
         const int b = sn & 1;
         if (sn >= 2 && !bar_wait(s, &s->empty_im[b], ((sn - 2) >> 1) & 1)) return;
         bulk_load(s->im[b], a.table + (size_t)node * a.im_bytes, (uint32_t)a.im_bytes, &s->full_im[b]);
+        im_last[b] = sn;                                    // the buffer's latest copy (teardown waits for it)
     };
     if (w == 0 && nn > 0) load_im(S, nodes[0]);
     for (int u = 0; u < nn; ++u) {
@@ -880,6 +883,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_induced_current_tc(TcArgs a)
 
     uint32_t S = 0, q = 0, flushes = 0;     // node, batch and flush sequence numbers (barrier phases)
     unsigned long long n_mma = 0;           // MMAs issued by this thread
+    int64_t im_last[2] = {-1, -1};          // sequence number of the latest table copy into each buffer
     unsigned long long n_cells = 0;         // nonzero charge cells converted by this thread
     for (;;) {
         tc_fence_before();
@@ -936,7 +940,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_induced_current_tc(TcArgs a)
                     if (warp >= 4) {
                         build_batches<FMT>(a, s, sorted, offt, s->nodes + u0, cnt, q, n_cells);
                     } else if (lane == 0) {
-                        issue_mmas(a, s, warp, s->nodes + u0, cnt, S, q, k0, n_mma);
+                        issue_mmas(a, s, warp, s->nodes + u0, cnt, S, q, k0, n_mma, im_last);
                     }
                     S += cnt;
                     __syncthreads();
@@ -954,6 +958,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_induced_current_tc(TcArgs a)
                 __syncthreads();
             }
         }
+    }
+    // teardown: every MMA and bulk copy this CTA issued has landed before its tensor memory
+    // and shared memory go (after an abort some may still be in flight)
+    if (warp < 4) {
+        if (lane == 0) mma_commit(&s->done);
+        __syncwarp();
+        bar_wait(s, &s->done, flushes & 1, false);
+        if (lane == 0 && warp == 0)
+            for (int b = 0; b < 2; ++b)
+                if (im_last[b] >= 0) bar_wait(s, &s->full_im[b], (uint32_t)(im_last[b] >> 1) & 1, false);
     }
     tc_fence_before();
     __syncthreads();
