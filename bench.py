@@ -51,7 +51,7 @@ def parse():
                     help="induced-current form of the headline: 0 FP32 direct, 1 BF16 / 2 FP16 tensor cores")
     ap.add_argument("--no-forms", action="store_true", help="skip timing the other induced-current forms")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-vs-plain request stream")
-    ap.add_argument("--serving-requests", type=int, default=10, help="requests per load point")
+    ap.add_argument("--serving-requests", type=int, default=15, help="requests per load point")
     ap.add_argument("--batched-events", type=int, default=32)
     ap.add_argument("--batched-hi", type=float, default=1.0e4, help="largest event of the batched comparison")
     return ap.parse_args()
@@ -412,10 +412,12 @@ def serving_vs_plain(precision, dev, n_requests=12, loads=(0.5, 0.7, 0.9), seed_
     for li, load in enumerate(loads):
         rate = load / mean_service
         rng = np.random.default_rng(seed + li)
+        n_sp = max(1, round(0.2 * n_requests))                 # exactly 20 % spills, at random positions
+        kinds = rng.permutation(np.arange(n_requests) < n_sp)
         t, reqs = 0.0, []
         for i in range(n_requests):
             t += rng.exponential(1.0 / rate)
-            if rng.random() < 0.2:
+            if kinds[i]:
                 reqs.append(serve.Request(i, 5000 + i, spill, t, "spill"))
             else:
                 reqs.append(serve.Request(i, 5000 + i, inter[i % len(inter)], t, "interaction"))
