@@ -85,6 +85,10 @@ def lib():
         L.ora_electronics.argtypes = [P(_Cfg), C.c_uint64, C.c_int32, f64p, C.c_int64,
                                       i32p, i32p, i32p, f64p, C.c_double, i32p]
         L.ora_electronics.restype = C.c_int64
+        L.ora_hit_intervals.argtypes = [P(_Cfg), C.c_int64, i32p, i32p, i32p, i32p]
+        L.ora_hit_point.argtypes = [P(_Cfg), C.c_int32, C.c_int32, C.c_double, f64p]
+        L.ora_track_dqdx.argtypes = [C.c_int64, f64p, f64p, f64p, f64p, f64p, f64p, C.c_double, C.c_int32,
+                                     C.c_double, f64p, i64p, f64p]
         assert L.ora_cfg_size() == C.sizeof(_Cfg), "oracle config struct mismatch"
         _lib = L
     return _lib
@@ -264,3 +268,54 @@ class Oracle:
                                    _p(qv, C.c_double), float(band), _p(tie, C.c_int32))
         return dict(t_cross=tc[:n].copy(), t_adc=ta[:n].copy(), adc=ad[:n].copy(),
                     q=qv[:n].copy(), tie_tick=int(tie[0]))
+
+    # -- after step 5: per-hit charge truth, 3-D points, dQ/dx --------------
+    def hit_intervals(self, t_cross, t_adc):
+        """[k0, k1] tick interval each hit of one pixel digitises (Sec. 3.4)."""
+        tc = np.ascontiguousarray(t_cross, dtype=np.int32)
+        ta = np.ascontiguousarray(t_adc, dtype=np.int32)
+        k0 = np.zeros(len(tc), np.int32)
+        k1 = np.zeros(len(tc), np.int32)
+        self.L.ora_hit_intervals(C.byref(self.c), len(tc), _p(tc, C.c_int32), _p(ta, C.c_int32),
+                                 _p(k0, C.c_int32), _p(k1, C.c_int32))
+        return k0, k1
+
+    def hit_truth(self, seg: dict, dr: dict, pixel: int, segs, t_cross, t_adc, event_id: int = 0):
+        """Charge each mapped segment induced in each hit's interval.
+
+        Returns (Q [n_hits, n_segs] electrons, q_signal [n_hits], k0, k1):
+        Q[h, j] = sum over the interval of hit h of the current of segment
+        segs[j] alone (Eq. (current) restricted to one segment); q_signal is
+        the interval sum of the pixel's whole current."""
+        segs = np.asarray(segs, dtype=np.int64)
+        k0, k1 = self.hit_intervals(t_cross, t_adc)
+        cs = np.zeros((len(segs), int(self.c.n_ticks) + 1))
+        for j, s in enumerate(segs.tolist()):
+            cs[j, 1:] = np.cumsum(self.pixel_current(seg, dr, pixel, [s], event_id=event_id))
+        full = np.concatenate([[0.0], np.cumsum(self.pixel_current(seg, dr, pixel, segs, event_id=event_id))])
+        Q = cs[:, k1 + 1].T - cs[:, k0].T
+        return Q, full[k1 + 1] - full[k0], k0, k1
+
+    def hit_points(self, pixel, t_cross, t_event: float = 0.0):
+        """(x, y, z) [n, 3] of hits (Sec. 6): pixel centre, inverse of Eq. (drift)."""
+        out = np.zeros((len(pixel), 3))
+        for i, (p, k) in enumerate(zip(np.asarray(pixel).tolist(), np.asarray(t_cross).tolist())):
+            self.L.ora_hit_point(C.byref(self.c), int(p), int(k), float(t_event), _p(out[i], C.c_double))
+        return out
+
+    @staticmethod
+    def track_dqdx(points, q, origin, direction, dx: float, n_bins: int, r_max: float):
+        """(dq [n_bins], count [n_bins], margin [n]) of points along a known straight track (Sec. 6)."""
+        L = lib()
+        P = np.ascontiguousarray(points, dtype=np.float64)
+        x, y, z = (np.ascontiguousarray(P[:, i]) for i in range(3))
+        qq = np.ascontiguousarray(q, dtype=np.float64)
+        o = np.ascontiguousarray(origin, dtype=np.float64)
+        u = np.ascontiguousarray(direction, dtype=np.float64)
+        dq = np.zeros(n_bins)
+        cnt = np.zeros(n_bins, np.int64)
+        mg = np.zeros(len(qq))
+        L.ora_track_dqdx(len(qq), _p(x, C.c_double), _p(y, C.c_double), _p(z, C.c_double), _p(qq, C.c_double),
+                         _p(o, C.c_double), _p(u, C.c_double), float(dx), int(n_bins), float(r_max),
+                         _p(dq, C.c_double), _p(cnt, C.c_int64), _p(mg, C.c_double))
+        return dq, cnt, mg

@@ -20,6 +20,13 @@
  *                       Sec. 3.3.1 interpolated trilinearly
  *   ora_electronics     Sec. 3.4 (CSA integration, discriminator with noise,
  *                       hold, ADC, reset)
+ *   ora_hit_intervals   Sec. 3.4: the ticks whose current a hit digitises
+ *                       (per-hit charge truth: the per-segment sums over these
+ *                       intervals are formed from ora_pixel_current of each
+ *                       segment alone, in oracle/__init__.py)
+ *   ora_hit_point       Sec. 6: hit -> 3-D point (pixel centre, inverse of
+ *                       Eq. (drift))
+ *   ora_track_dqdx      Sec. 6: dQ/dx in pieces of a known straight track
  *   ora_philox4x32_10   counter-based generator of Salmon et al., SC'11
  *                       ("Parallel random numbers: as easy as 1, 2, 3")
  *
@@ -587,4 +594,82 @@ int64_t ora_electronics(const ora_cfg *c, uint64_t event_id, int32_t pixel, cons
     }
     if (tie_tick) *tie_tick = tie;
     return nh;
+}
+
+/* ------------------------------------------------- per-hit charge truth -- */
+
+/* Integration interval [k0, k1] of each hit of one pixel, hits in tick order
+ * (Sec. 3.4: the CSA integrates the current from its last reset until the
+ * ADC samples it).  The interval ends at the hit's ADC tick.  It starts after
+ * the previous hit's ADC tick (that conversion reset the CSA), or at the
+ * window start for the pixel's first hit, or, when periodic resets are on, at
+ * the latest reset tick r = j * period (0 < r <= the crossing tick) after it:
+ * a reset at tick r clears the charge before tick r's current is added, and
+ * resets only happen while the front end is idle, i.e. before the crossing. */
+void ora_hit_intervals(const ora_cfg *c, int64_t n, const int32_t *t_cross, const int32_t *t_adc,
+                       int32_t *k0, int32_t *k1)
+{
+    int64_t prev_end = -1;
+    for (int64_t h = 0; h < n; ++h) {
+        int64_t start = prev_end + 1;
+        if (c->periodic > 0) {
+            int64_t r = ((int64_t)t_cross[h] / c->periodic) * c->periodic;
+            if (r > 0 && r > start) start = r;
+        }
+        k0[h] = (int32_t)start;
+        k1[h] = t_adc[h];
+        prev_end = t_adc[h];
+    }
+}
+
+/* ------------------------------------------------------ hits -> 3-D points -- */
+
+/* 3-D point of a hit (Sec. 6, the reconstruction's input): x and y at the
+ * centre of the hit's pixel, z from the hit's crossing tick by the inverse of
+ * Eq. (drift): the tick starts at t = t_w0 + t_cross * tick, the charge
+ * drifted for t - t_event, and z = z_anode + v_d (t - t_event) for the anode
+ * at z = 0 (TPC 0), z_anode - v_d (t - t_event) for the anode at z = 2D. */
+void ora_hit_point(const ora_cfg *c, int32_t pixel, int32_t t_cross, double t_event, double out[3])
+{
+    double xc, yc, za;
+    int32_t anode;
+    ora_pixel_centre(c, pixel, &xc, &yc, &za, &anode);
+    double t = c->t_w0 + (double)t_cross * c->tick;
+    double dz = c->vdrift * (t - t_event);
+    out[0] = xc;
+    out[1] = yc;
+    out[2] = za == 0.0 ? za + dz : za - dz;
+}
+
+/* dQ/dx along a known straight track (Sec. 6: the charge of the hits of a
+ * track per unit length, in pieces of fixed length).  The track starts at o
+ * with unit direction u; a point p at arc length s = (p - o) . u and distance
+ * d = |p - o - s u| from the line belongs to piece floor(s / dx) when
+ * 0 <= s < n_bins dx and d <= r_max.  dq[b] = sum of the charges of piece b,
+ * cnt[b] = its points; margin[i] = distance (cm) of point i's decisions from
+ * the nearest edge (a piece boundary or r_max), so that tests can exclude
+ * points whose assignment a rounding could flip. */
+void ora_track_dqdx(int64_t n, const double *x, const double *y, const double *z, const double *q,
+                    const double o[3], const double u[3], double dx, int32_t n_bins, double r_max,
+                    double *dq, int64_t *cnt, double *margin)
+{
+    for (int32_t b = 0; b < n_bins; ++b) {
+        dq[b] = 0.0;
+        cnt[b] = 0;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        double px = x[i] - o[0], py = y[i] - o[1], pz = z[i] - o[2];
+        double s = px * u[0] + py * u[1] + pz * u[2];
+        double ex = px - s * u[0], ey = py - s * u[1], ez = pz - s * u[2];
+        double d = sqrt(ex * ex + ey * ey + ez * ez);
+        double fb = floor(s / dx);
+        double m = fabs(d - r_max);
+        double ms = fmin(fabs(s - fb * dx), fabs((fb + 1.0) * dx - s));
+        if (ms < m) m = ms;
+        margin[i] = m;
+        if (d > r_max || s < 0.0 || fb >= (double)n_bins) continue;
+        int32_t b = (int32_t)fb;
+        dq[b] += q[i];
+        cnt[b] += 1;
+    }
 }
