@@ -51,6 +51,7 @@ def parse():
                     help="induced-current form of the headline: 0 FP32 direct, 1 BF16 / 2 FP16 tensor cores")
     ap.add_argument("--no-forms", action="store_true", help="skip timing the other induced-current forms")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-vs-plain request stream")
+    ap.add_argument("--no-post", action="store_true", help="skip timing truth, hit points and dQ/dx")
     ap.add_argument("--serving-requests", type=int, default=15, help="requests per load point")
     ap.add_argument("--batched-events", type=int, default=32)
     ap.add_argument("--batched-hi", type=float, default=1.0e4, help="largest event of the batched comparison")
@@ -344,6 +345,69 @@ def time_form(cfg, seg, lut, dev, precision, steps, warmup, rank):
     return run, per, counts_now
 
 
+def post_hit_steps(run, cfg, dev, reps=5):
+    """Times the steps after the front end on the event held by `run` (its last
+    sim_event): per-hit charge truth (5 entries per hit), hits -> 3-D points and
+    dQ/dx in 1 cm pieces along a line through the detector (L2 flushed before
+    each launch; CUDA events on the launching stream)."""
+    import torch
+    from paper_2212_09807_gb300 import sim
+    S = run.segs.n
+    n_pairs, n_pix, n_hits, status = run.counts()
+    assert status == 0
+    v = run.view(S)
+    A = sim._alias
+    dr = sim.Drifted.wrap(v.dr)
+    active = A(v.active_pixels, run.max_pixels, torch.int32, dev)
+    pix_seg_off = A(v.pix_seg_off, run.max_pixels + 1, torch.int32, dev)
+    pix_seg_ids = A(v.pix_seg_ids, run.max_pairs, torch.int32, dev)
+    counts = run.ws[:6]
+    cum = sim.sim_response_cumulative(run.resp)
+    tr = sim.Truth(run.hits.capacity, 5, device=dev)
+    cap = run.hits.capacity
+    x, y, z = (torch.empty(cap, dtype=torch.float32, device=dev) for _ in range(3))
+    g = params.geometry(cfg)
+    o = (0.0, g["y_max"] / 2, g["z_max"] / 2)
+    n_pieces = int(np.ceil(g["x_max"])) + 1
+    dq = torch.empty(n_pieces, dtype=torch.float64, device=dev)
+    cnt = torch.empty(n_pieces, dtype=torch.int32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)
+    calls = {
+        # warm-up calls size the cell capacity (a synchronising retry); timed calls do not retry
+        "hit_truth": lambda retry=False: sim.sim_hit_truth(run.cfg, run.segs, dr, run.resp, cum, active,
+                                                           pix_seg_off, pix_seg_ids, counts, run.max_pixels,
+                                                           run.hits, tr, retry=retry),
+        "hit_points": lambda: sim.sim_hit_points(run.cfg, run.hits, x, y, z),
+        "track_dqdx": lambda: sim.sim_track_dqdx(x, y, z, run.hits.q, run.hits.n_out, o, (1.0, 0.0, 0.0), 1.0,
+                                                 n_pieces, 1.0e4, dq, cnt),
+    }
+    out = {}
+    for name, f in calls.items():
+        for _ in range(2):
+            f(retry=True) if name == "hit_truth" else f()
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            f()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        out[name] = {"ms": float(np.mean(ms)), "hits": n_hits, "hits_per_s": n_hits / (float(np.mean(ms)) / 1e3)}
+    hbm = measured_peaks().get("hbm_gbs", 6800.0)
+    for name, per_hit in (("hit_points", 20), ("track_dqdx", 16)):
+        gbs = per_hit * n_hits / (out[name]["ms"] / 1e3) / 1e9
+        out[name]["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                                 "bytes_per_hit": per_hit}
+    out["hit_truth"]["k"] = 5
+    cells, runs, units, status = tr.counts()
+    assert status == 0
+    out["hit_truth"].update({"hit_pixels": runs, "units": units, "cells": cells})
+    out["track_dqdx"]["points_in_pieces"] = int(cnt.sum().item())
+    return out
+
+
 def form_roofline(run, cfg, precision, a4_s, props, sm_mhz, dev):
     """Roofline of the induced-current kernel of one form: FP32 direct against
     the FP32 FMA peak; tensor-core forms against the measured dense 16-bit
@@ -517,6 +581,7 @@ def run_ours(args):
         e2e_s = float(t.item())
     e2e = {"value": world * S * args.steps / e2e_s, "unit": "segments/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
+    post = post_hit_steps(run, cfg, dev) if not args.no_post else None
     del run, io
     torch.cuda.empty_cache()
 
@@ -546,7 +611,7 @@ def run_ours(args):
                                   "induced_current": float(per[:, 2].mean()),
                                   "electronics": float(per[:, 3].mean())},
             "roofline": roofline, "forms": forms, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,
-            "serving": serving,
+            "serving": serving, "after_front_end": post,
             "gpu_launches": KERNELS_PER_STEP[args.precision] * args.steps, "clocks": clocks,
         }))
     if pg:

@@ -309,6 +309,86 @@ int sim_event_view_of(const sim_config *cfg, int64_t max_events, int64_t n_segme
                       int64_t max_pairs, int64_t max_pixels, void *ws, size_t ws_bytes,
                       sim_event_view *view);
 
+/* ---------------------------------------------- after the front end ---- */
+
+/* Running sums of the response table rows, for sim_hit_truth, stored as quads
+ * of the four rows a bilinear read combines: cum is FP32 [nb][nb][ld][4] (16 *
+ * nb * nb * ld bytes, 16-byte aligned) and cum[bx][by][j][c] = sum over
+ * j' <= j of resp->lut[bx + dx][by + dy][j'], (dx, dy) = (c & 1, c >> 1), for
+ * j < nt (accumulated in FP64, rounded to FP32; 0 for rows beyond the table;
+ * positions [nt, ld) are not written).  Compute it once per table. */
+int sim_response_cumulative(const sim_response *resp, float *cum, void *stream);
+
+/* Per-hit charge truth written by sim_hit_truth (device arrays; the caller
+ * owns them): for hit h (the hit list's order), entries h*k .. h*k+k-1 of
+ * `segment` and `q` list the segments that induced the largest |charge| on
+ * the hit's pixel during the ticks the hit digitises, in decreasing |charge|
+ * (ties: lower segment index first), as indices into the call's segment
+ * arrays and electrons; unused entries hold -1 and 0.  q_signal[h] is the
+ * charge of all the pixel's segments in those ticks (the hit's signal,
+ * without front-end noise and pedestal).  tick_first (optional, NULL = not
+ * written) receives the first tick of each hit's interval. */
+#define SIM_TRUTH_MAX_K 16
+typedef struct sim_truth {
+    int32_t k;                 /* entries per hit, 1 .. SIM_TRUTH_MAX_K */
+    int32_t *segment;          /* [capacity * k] */
+    float *q;                  /* [capacity * k] */
+    float *q_signal;           /* [capacity] */
+    int32_t *tick_first;       /* [capacity] or NULL */
+    int64_t capacity;          /* hits */
+} sim_truth;
+
+/* Charge truth of every hit (Sec. 3.4 with the truth scheme of Sec. 4.4
+ * applied to the charge readout).  A hit digitises the current of ticks
+ * [k0, k1]: k1 is its ADC tick; k0 the tick after the previous hit's ADC tick
+ * on the same pixel (0 for the first), or the latest periodic reset tick
+ * r = j * periodic_reset_ticks with k0 < r <= its crossing tick.  The charge
+ * segment s put there is sum_{k=k0}^{k1} of the terms of Eq. (current) that
+ * come from s, the same terms sim_induced_current sums (for any precision
+ * setting they are evaluated in FP32 from the table's running sums `cum`,
+ * sim_response_cumulative), summed exactly in fixed point (2^-16 e-) per
+ * (hit, segment).  Inputs: the segment, drift and map outputs of the event (or
+ * batch) and the hit list of sim_electronics / sim_event (pixel ids, crossing
+ * and ADC ticks, ordered by pixel then tick; *hits->n_out hits, at most
+ * min(hits->capacity, out->capacity) processed).
+ * Workspace: sim_hit_truth_workspace_size(min(hits->capacity, out->capacity),
+ * max_cells) bytes; its first 256 bytes hold int64 counts: [0] cells needed
+ * (sum over the hits' pixels of hits x mapped segments), [1] runs (hit pixels),
+ * [2] work units, [3] status (bit 1: more than max_cells cells; nothing was
+ * computed and q_signal is 0).  Nothing is computed either when counts[3] of
+ * the map reports an overflow.  Results are bitwise reproducible. */
+int sim_hit_truth_workspace_size(int64_t max_hits, int64_t max_cells, size_t *bytes);
+int sim_hit_truth(const sim_config *cfg, const sim_segments *seg, const sim_drifted *dr,
+                  const sim_response *resp, const float *cum, const int32_t *active_pixels,
+                  const int32_t *pix_seg_off, const int32_t *pix_seg_ids, const int64_t *counts,
+                  int64_t pix_cap, const sim_hits *hits, const sim_truth *out, int64_t max_cells,
+                  void *ws, size_t ws_bytes, void *stream);
+
+/* Hits -> 3-D points (Sec. 6): x, y = centre of the hit's pixel (global cm),
+ * z from the crossing tick by the inverse of Eq. (drift): the tick starts at
+ * t = t_window0 + t_cross * tick, and z = z_anode + v_d (t - t_event) for an
+ * anode at z = 0, z_anode - v_d (t - t_event) for the anode at 2 drift_len.
+ * t_event: device FP32 array with the event time of each event slot of the
+ * hits' (virtual) pixel ids, or NULL (all events at t = 0).  Writes x, y, z
+ * [hits->capacity] for the first min(*hits->n_out, capacity) hits, evaluated
+ * in FP64 and rounded to FP32. */
+int sim_hit_points(const sim_config *cfg, const sim_hits *hits, const float *t_event, float *x, float *y,
+                   float *z, void *stream);
+
+/* dQ/dx along a known straight track (Sec. 6, the charge per unit length of a
+ * track's hits, in pieces of length piece_cm): point i (x, y, z: device FP32
+ * arrays of `capacity`, *n_points of them used, n_points a device int64) at
+ * arc length s = (p - origin) . direction (direction: unit vector) and
+ * distance d from the line belongs to piece floor(s / piece_cm) when
+ * 0 <= s < n_pieces piece_cm and d <= r_max_cm; dq[b] (device FP64) receives
+ * the sum of charges q (device FP32) of piece b and count[b] (device int32)
+ * its points.  Decisions are IEEE FP64 evaluations of these expressions;
+ * charges are summed exactly in fixed point (2^-16 e-).  origin, direction:
+ * host arrays of 3. */
+int sim_track_dqdx(const float *x, const float *y, const float *z, const float *q, const int64_t *n_points,
+                   int64_t capacity, const double *origin, const double *direction, double piece_cm,
+                   int32_t n_pieces, double r_max_cm, double *dq, int32_t *count, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

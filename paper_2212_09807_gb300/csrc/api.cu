@@ -304,4 +304,63 @@ int sim_event(const sim_config *cfg, const sim_segments *seg, const sim_response
     return SIM_OK;
 }
 
+int sim_response_cumulative(const sim_response *resp, float *cum, void *stream)
+{
+    if (!resp_ok(resp, true) || !cum || (reinterpret_cast<uintptr_t>(cum) & 15) != 0) return SIM_ERR_INVALID_ARG;
+    const cudaError_t e = launch_response_cumulative(*resp, cum, (cudaStream_t)stream);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e);
+}
+
+int sim_hit_truth_workspace_size(int64_t max_hits, int64_t max_cells, size_t *bytes)
+{
+    if (max_hits < 0 || max_hits >= ((int64_t)1 << 31) || max_cells < 0 || max_cells >= ((int64_t)1 << 31) || !bytes)
+        return SIM_ERR_INVALID_ARG;
+    *bytes = hit_truth_workspace_bytes(max_hits, max_cells);
+    return SIM_OK;
+}
+
+int sim_hit_truth(const sim_config *cfg, const sim_segments *seg, const sim_drifted *dr, const sim_response *resp,
+                  const float *cum, const int32_t *active_pixels, const int32_t *pix_seg_off,
+                  const int32_t *pix_seg_ids, const int64_t *counts, int64_t pix_cap, const sim_hits *hits,
+                  const sim_truth *out, int64_t max_cells, void *ws, size_t ws_bytes, void *stream)
+{
+    if (!cfg_ok(cfg) || !seg_ok(seg) || !events_ok(cfg, seg) || !resp_ok(resp, false) || !cum || !counts ||
+        pix_cap < 0 || !hits_ok(hits) || !hits->n_out || !out || !ws || max_cells < 0 ||
+        max_cells >= ((int64_t)1 << 31) || (reinterpret_cast<uintptr_t>(cum) & 15) != 0)
+        return SIM_ERR_INVALID_ARG;
+    if (out->k < 1 || out->k > SIM_TRUTH_MAX_K || out->capacity < 0 || out->capacity >= ((int64_t)1 << 31))
+        return SIM_ERR_INVALID_ARG;
+    if (out->capacity > 0 && (!out->segment || !out->q || !out->q_signal)) return SIM_ERR_INVALID_ARG;
+    if (pix_cap > 0 && (!active_pixels || !pix_seg_off || !pix_seg_ids)) return SIM_ERR_INVALID_ARG;
+    if (seg->n > 0 && !drifted_ok(dr)) return SIM_ERR_INVALID_ARG;
+    const int64_t hcap = hits->capacity < out->capacity ? hits->capacity : out->capacity;
+    if (ws_bytes < hit_truth_workspace_bytes(hcap, max_cells)) return SIM_ERR_CAPACITY;
+    const sim_drifted d0 = dr ? *dr : sim_drifted{};
+    const cudaError_t e = launch_hit_truth(*cfg, *seg, d0, *resp, cum, active_pixels, pix_seg_off, pix_seg_ids,
+                                           counts, pix_cap, *hits, *out, max_cells, ws, (cudaStream_t)stream);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e);
+}
+
+int sim_hit_points(const sim_config *cfg, const sim_hits *hits, const float *t_event, float *x, float *y, float *z,
+                   void *stream)
+{
+    if (!cfg_ok(cfg) || !hits_ok(hits) || !hits->n_out) return SIM_ERR_INVALID_ARG;
+    if (hits->capacity > 0 && (!x || !y || !z)) return SIM_ERR_INVALID_ARG;
+    const cudaError_t e = launch_hit_points(*cfg, *hits, t_event, x, y, z, (cudaStream_t)stream);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e);
+}
+
+int sim_track_dqdx(const float *x, const float *y, const float *z, const float *q, const int64_t *n_points,
+                   int64_t capacity, const double *origin, const double *direction, double piece_cm,
+                   int32_t n_pieces, double r_max_cm, double *dq, int32_t *count, void *stream)
+{
+    if (!n_points || capacity < 0 || !origin || !direction || !(piece_cm > 0.0) || n_pieces < 1 ||
+        !(r_max_cm >= 0.0) || !dq || !count)
+        return SIM_ERR_INVALID_ARG;
+    if (capacity > 0 && (!x || !y || !z || !q)) return SIM_ERR_INVALID_ARG;
+    const cudaError_t e = launch_track_dqdx(x, y, z, q, n_points, capacity, origin, direction, piece_cm, n_pieces,
+                                            r_max_cm, dq, count, (cudaStream_t)stream);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e);
+}
+
 }  // extern "C"

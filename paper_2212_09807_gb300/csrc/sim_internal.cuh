@@ -187,6 +187,21 @@ cudaError_t launch_electronics(const sim_config &c, const EventInfo &ev, const i
                                const float *current, int64_t *counts, int64_t pix_cap,
                                const sim_hits &out, void *scratch, cudaStream_t st);
 
+// After the front end: table running sums, per-hit charge truth, hit points,
+// track dQ/dx.
+cudaError_t launch_response_cumulative(const sim_response &r, float *cum, cudaStream_t st);
+cudaError_t launch_hit_truth(const sim_config &c, const sim_segments &s, const sim_drifted &d,
+                             const sim_response &r, const float *cum, const int32_t *active,
+                             const int32_t *pix_seg_off, const int32_t *pix_seg_ids, const int64_t *counts,
+                             int64_t pix_cap, const sim_hits &hits, const sim_truth &out, int64_t max_cells,
+                             void *ws, cudaStream_t st);
+size_t hit_truth_workspace_bytes(int64_t hit_cap, int64_t max_cells);
+cudaError_t launch_hit_points(const sim_config &c, const sim_hits &h, const float *t_event, float *x, float *y,
+                              float *z, cudaStream_t st);
+cudaError_t launch_track_dqdx(const float *x, const float *y, const float *z, const float *q, const int64_t *n,
+                              int64_t cap, const double origin[3], const double dir[3], double piece, int32_t n_bins,
+                              double r_max, double *dq, int32_t *count, cudaStream_t st);
+
 // Exclusive scan of int32 `in[0..n)` into `out[0..n]` (out[n] = total) with
 // the total also stored to *total64 when non-null.  In place allowed.
 size_t scan_scratch_bytes(int64_t n);

@@ -80,6 +80,11 @@ class SimHits(C.Structure):
         ("capacity", C.c_int64), ("n_out", _P)]
 
 
+class SimTruth(C.Structure):
+    _fields_ = [("k", C.c_int32), ("segment", _P), ("q", _P), ("q_signal", _P), ("tick_first", _P),
+                ("capacity", C.c_int64)]
+
+
 class SimEventView(C.Structure):
     _fields_ = [("dr", SimDrifted)] + [(k, _P) for k in (
         "seg_pix_off", "seg_pix_ids", "active_pixels", "pix_seg_off", "pix_seg_ids", "current", "counts")]
@@ -117,8 +122,17 @@ def lib():
                                         C.c_size_t, cp(SimEventView)]
         L.sim_pixel_map_noalloc.argtypes = [cp(SimConfig), cp(SimSegments), cp(SimDrifted), cp(SimResponse),
                                             _P, _P, C.c_int64, _P, _P, _P, C.c_int64, _P, _P]
+        L.sim_response_cumulative.argtypes = [cp(SimResponse), _P, _P]
+        L.sim_hit_truth_workspace_size.argtypes = [C.c_int64, C.c_int64, cp(C.c_size_t)]
+        L.sim_hit_truth.argtypes = [cp(SimConfig), cp(SimSegments), cp(SimDrifted), cp(SimResponse), _P, _P, _P,
+                                    _P, _P, C.c_int64, cp(SimHits), cp(SimTruth), C.c_int64, _P, C.c_size_t, _P]
+        L.sim_hit_points.argtypes = [cp(SimConfig), cp(SimHits), _P, _P, _P, _P, _P]
+        L.sim_track_dqdx.argtypes = [_P, _P, _P, _P, _P, C.c_int64, cp(C.c_double), cp(C.c_double), C.c_double,
+                                     C.c_int32, C.c_double, _P, _P, _P]
         for f in ("sim_workspace_size", "sim_quench_drift", "sim_pixel_map", "sim_induced_current",
-                  "sim_induced_current_range", "sim_electronics", "sim_event", "sim_event_view_of", "sim_pixel_map_noalloc"):
+                  "sim_induced_current_range", "sim_electronics", "sim_event", "sim_event_view_of",
+                  "sim_pixel_map_noalloc", "sim_response_cumulative", "sim_hit_truth_workspace_size", "sim_hit_truth", "sim_hit_points",
+                  "sim_track_dqdx"):
             getattr(L, f).restype = C.c_int
         sizes = (C.c_int64 * 5)()
         L.sim_abi_sizes(sizes)
@@ -345,6 +359,89 @@ def sim_event(cfg: SimConfig, seg: Segments, resp: Response, max_pairs: int, max
     s, r, h = seg.struct(), resp.struct(), hits.struct()
     _check(lib().sim_event(C.byref(cfg), C.byref(s), C.byref(r), int(max_pairs), int(max_pixels), C.byref(h),
                            _ptr(ws), int(ws.numel() * ws.element_size()), _stream(stream)), "sim_event")
+
+
+def sim_response_cumulative(resp: Response, stream=None):
+    """Running sums of the table rows as corner quads ([nb][nb][ld][4]), for sim_hit_truth."""
+    import torch
+    cum = torch.zeros(*resp.t.shape, 4, dtype=torch.float32, device=resp.t.device)
+    r = resp.struct()
+    _check(lib().sim_response_cumulative(C.byref(r), _ptr(cum), _stream(stream)), "sim_response_cumulative")
+    return cum
+
+
+class Truth:
+    """Per-hit charge truth buffers (k entries per hit) and the call's workspace.
+
+    ``max_cells`` bounds the sum over hit pixels of hits x mapped segments;
+    :func:`sim_hit_truth` grows it (and retries) when the device reports more."""
+
+    def __init__(self, capacity: int, k: int = 5, max_cells: int = 1 << 20, device="cuda"):
+        import torch
+        self.capacity, self.k = int(capacity), int(k)
+        self.device = device
+        n = max(self.capacity, 1)
+        self.segment = torch.empty(n * self.k, dtype=torch.int32, device=device)
+        self.q = torch.empty(n * self.k, dtype=torch.float32, device=device)
+        self.q_signal = torch.empty(n, dtype=torch.float32, device=device)
+        self.tick_first = torch.empty(n, dtype=torch.int32, device=device)
+        self.reserve(max_cells)
+
+    def reserve(self, max_cells: int):
+        import torch
+        self.max_cells = int(max_cells)
+        b = C.c_size_t()
+        _check(lib().sim_hit_truth_workspace_size(self.capacity, self.max_cells, C.byref(b)),
+               "sim_hit_truth_workspace_size")
+        self.ws = torch.empty((int(b.value) + 7) // 8, dtype=torch.int64, device=self.device)
+
+    def counts(self):
+        """(cells needed, runs, units, status) of the last call, after the stream has run."""
+        return [int(x) for x in self.ws[:4].cpu().tolist()]
+
+    def struct(self) -> SimTruth:
+        t = SimTruth()
+        t.k, t.capacity = self.k, self.capacity
+        t.segment, t.q, t.q_signal, t.tick_first = (_ptr(self.segment), _ptr(self.q), _ptr(self.q_signal),
+                                                    _ptr(self.tick_first))
+        return t
+
+
+def sim_hit_truth(cfg: SimConfig, seg: Segments, dr: Drifted, resp: Response, cum, active_pixels, pix_seg_off,
+                  pix_seg_ids, counts, pix_cap: int, hits: Hits, out: Truth, stream=None, retry: bool = True):
+    """Enqueues the truth step; with ``retry`` it synchronises, and re-runs with a
+    larger cell capacity when the device reports more cells than ``out.max_cells``."""
+    import torch
+    s, d, r, h, t = seg.struct(), dr.struct(), resp.struct(), hits.struct(), out.struct()
+    for _ in range(2):
+        _check(lib().sim_hit_truth(C.byref(cfg), C.byref(s), C.byref(d), C.byref(r), _ptr(cum),
+                                   _ptr(active_pixels), _ptr(pix_seg_off), _ptr(pix_seg_ids), _ptr(counts),
+                                   int(pix_cap), C.byref(h), C.byref(t), out.max_cells, _ptr(out.ws),
+                                   int(out.ws.numel() * 8), _stream(stream)), "sim_hit_truth")
+        if not retry:
+            return
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        cells, _, _, status = out.counts()
+        if status == 0:
+            return
+        out.reserve(max(2 * out.max_cells, cells + cells // 4))
+    raise RuntimeError("sim_hit_truth: cell capacity still too small")
+
+
+def sim_hit_points(cfg: SimConfig, hits: Hits, x, y, z, t_event=None, stream=None):
+    h = hits.struct()
+    _check(lib().sim_hit_points(C.byref(cfg), C.byref(h), _ptr(t_event), _ptr(x), _ptr(y), _ptr(z),
+                                _stream(stream)), "sim_hit_points")
+
+
+def sim_track_dqdx(x, y, z, q, n_points, origin, direction, piece_cm: float, n_pieces: int, r_max_cm: float,
+                   dq, count, stream=None):
+    """``n_points``: device int64 tensor holding the number of points; dq FP64 and count int32 [n_pieces]."""
+    o = (C.c_double * 3)(*[float(v) for v in origin])
+    u = (C.c_double * 3)(*[float(v) for v in direction])
+    _check(lib().sim_track_dqdx(_ptr(x), _ptr(y), _ptr(z), _ptr(q), _ptr(n_points), int(x.numel()), o, u,
+                                float(piece_cm), int(n_pieces), float(r_max_cm), _ptr(dq), _ptr(count),
+                                _stream(stream)), "sim_track_dqdx")
 
 
 def sim_event_view_of(cfg: SimConfig, n_segments: int, max_pairs: int, max_pixels: int, ws,

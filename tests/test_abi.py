@@ -80,3 +80,23 @@ def test_workspace_grows_with_capacities(L):
     a = sim.workspace_size(cfg, 1000, 10000, 1000)
     b = sim.workspace_size(cfg, 1000, 10000, 2000)
     assert b - a >= 1000 * 2000 * 4      # the current array [pixels][ticks] is inside
+
+
+def test_post_hit_entry_points_check_arguments(L):
+    from paper_2212_09807_gb300 import sim
+    from synth import params
+    cfg = sim.make_config(params.module_config())
+    seg, d, r, h = sim.SimSegments(), sim.SimDrifted(), sim.SimResponse(), sim.SimHits()
+    r.nb, r.nt, r.ld, r.bins_per_pitch = 45, 1950, 1952, 30
+    t = sim.SimTruth()
+    t.k = 0                                         # k outside 1 .. SIM_TRUTH_MAX_K
+    fake = C.c_void_p(16)                           # never dereferenced: the checks fail first
+    assert L.sim_hit_truth(C.byref(cfg), C.byref(seg), C.byref(d), C.byref(r), fake, None, None, None, fake, 0,
+                           C.byref(h), C.byref(t), 0, fake, 1 << 20, None) == -1
+    b = C.c_size_t()
+    assert L.sim_hit_truth_workspace_size(1000, 10000, C.byref(b)) == 0 and b.value > 8 * 10000
+    assert L.sim_hit_truth_workspace_size(1000, 1 << 31, C.byref(b)) == -1
+    assert L.sim_hit_points(C.byref(cfg), C.byref(h), None, None, None, None, None) == -1   # no n_out
+    o = (C.c_double * 3)(0, 0, 0)
+    assert L.sim_track_dqdx(None, None, None, None, fake, 0, o, o, 0.0, 4, 1.0, fake, fake, None) == -1
+    assert L.sim_response_cumulative(C.byref(r), None, None) == -1
