@@ -319,3 +319,129 @@ class Oracle:
                          _p(o, C.c_double), _p(u, C.c_double), float(dx), int(n_bins), float(r_max),
                          _p(dq, C.c_double), _p(cnt, C.c_int64), _p(mg, C.c_double))
         return dq, cnt, mg
+
+
+# ================================================================= light ==
+
+class _Light(C.Structure):
+    _fields_ = [(k, C.c_int32) for k in ("nvx", "nvy", "nvz", "n_det", "nt", "n_ticks", "n_trunc", "n_resp",
+                                         "noise_block", "adc_bits")] + \
+               [(k, C.c_double) for k in ("vox", "w_ph", "tick", "t_start", "fast_frac", "tau_fast", "tau_slow",
+                                          "poisson_max", "sample", "pedestal")]
+
+
+def light_derived(L: dict, n_ticks: int):
+    """(n_trunc, ratio, n_samples) of a light configuration: the truncation of
+    the scintillation sum (trunc_taus tau_slow in ticks, rounded), the
+    sampling period in ticks and the number of samples of the window."""
+    tick = _f32(L["tick_us"])
+    n_trunc = int(np.floor(_f32(L["trunc_taus"]) * _f32(L["tau_slow_us"]) / tick + 0.5))
+    ratio = _f32(L["sample_us"]) / tick
+    n_samples = int(np.floor((n_ticks - 1) / ratio)) + 1
+    return n_trunc, ratio, n_samples
+
+
+class LightOracle:
+    """FP64 oracle of the light path (Sec. 4) for one configuration, light
+    parameters, FP32 tables (synth.light.tables) and time window."""
+
+    def __init__(self, cfg: dict, L: dict, tab: dict, t_start_us: float, n_ticks: int):
+        self.lib = lib()
+        f64p, i32p, f32p = C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_float)
+        self.lib.ora_light_size.restype = C.c_size_t
+        assert self.lib.ora_light_size() == C.sizeof(_Light)
+        self.lib.ora_light_segment.argtypes = [C.POINTER(_Cfg), C.POINTER(_Light), f32p, C.c_double, C.c_int32,
+                                               f64p, f64p, f64p, i32p, i32p]
+        self.lib.ora_light_segment.restype = C.c_int
+        self.lib.ora_light_photocurrent.argtypes = [C.POINTER(_Light), C.c_int64, f64p, i32p, i32p, i32p, f64p,
+                                                    C.c_int32, C.c_int32, f64p]
+        self.lib.ora_light_scintillation.argtypes = [C.POINTER(_Light), f64p, f64p]
+        self.lib.ora_light_fluctuate.argtypes = [C.POINTER(_Cfg), C.POINTER(_Light), C.c_uint64, C.c_int32, f64p,
+                                                 f64p, f64p]
+        self.lib.ora_light_electronics.argtypes = [C.POINTER(_Cfg), C.POINTER(_Light), C.c_uint64, C.c_int32,
+                                                   C.c_double, f64p, f64p, f64p, C.c_double, C.c_int32, f64p, f64p,
+                                                   i32p, f64p]
+        self.c = make_cfg(cfg, dict(nb=1, nt=1, bins_per_pitch=1))
+        l = _Light()
+        nvx, nvy, nvz, nd, nt = tab["tdist"].shape
+        l.nvx, l.nvy, l.nvz, l.n_det, l.nt = nvx, nvy, nvz, nd, nt
+        l.n_ticks = int(n_ticks)
+        self.n_trunc, self.ratio, self.n_samples = light_derived(L, n_ticks)
+        l.n_trunc = self.n_trunc
+        l.n_resp = len(tab["resp"])
+        l.noise_block = int(L["noise_block"])
+        l.adc_bits = int(L["adc_bits"])
+        l.vox, l.w_ph, l.tick = _f32(L["vox_cm"]), _f32(L["w_ph_MeV"]), _f32(L["tick_us"])
+        l.t_start = _f32(t_start_us)
+        l.fast_frac, l.tau_fast, l.tau_slow = _f32(L["fast_frac"]), _f32(L["tau_fast_us"]), _f32(L["tau_slow_us"])
+        l.poisson_max, l.sample, l.pedestal = _f32(L["poisson_max_mean"]), _f32(L["sample_us"]), _f32(L["pedestal"])
+        self.l = l
+        self.n_det = nd
+        self.vis = np.ascontiguousarray(tab["vis"].reshape(-1), dtype=np.float64)
+        self.tdist = np.ascontiguousarray(tab["tdist"].reshape(-1), dtype=np.float64)
+        self.eff = np.ascontiguousarray(tab["eff"], dtype=np.float64)
+        self.gain = np.ascontiguousarray(tab["gain"], dtype=np.float64)
+        self.resp = np.ascontiguousarray(tab["resp"], dtype=np.float64)
+        self.amp = np.ascontiguousarray(tab["noise"], dtype=np.float64)
+
+    def segments(self, seg: dict, dr: dict):
+        """(npe [n, n_det], tick [n], vox [n]) of every segment (Sec. 4.1)."""
+        n = len(seg["x0"])
+        cols = np.stack([np.asarray(seg[k], dtype=np.float32) for k in
+                         ("x0", "y0", "z0", "t0", "x1", "y1", "z1", "t1", "dE")], axis=1)
+        cols = np.ascontiguousarray(cols)
+        npe = np.zeros((n, self.n_det))
+        tick = np.zeros(n, np.int32)
+        vox = np.zeros(n, np.int32)
+        for j in range(n):
+            row = np.zeros(self.n_det)
+            t = C.c_int32()
+            v = C.c_int32()
+            self.lib.ora_light_segment(C.byref(self.c), C.byref(self.l), _p(cols[j], C.c_float),
+                                       float(dr["QR"][j]), int(dr["anode"][j]), _p(self.vis, C.c_double),
+                                       _p(self.eff, C.c_double), _p(row, C.c_double), C.byref(t), C.byref(v))
+            npe[j] = row
+            tick[j] = t.value
+            vox[j] = v.value
+        return npe, tick, vox
+
+    def photocurrent(self, npe, tick, vox, anode, det: int):
+        """Expected photoelectrons per tick of global photosensor det (Sec. 4.2)."""
+        npe = np.ascontiguousarray(npe, dtype=np.float64)
+        tick = np.ascontiguousarray(tick, dtype=np.int32)
+        vox = np.ascontiguousarray(vox, dtype=np.int32)
+        anode = np.ascontiguousarray(anode, dtype=np.int32)
+        I = np.zeros(self.l.n_ticks)
+        self.lib.ora_light_photocurrent(C.byref(self.l), len(tick), _p(npe, C.c_double), _p(tick, C.c_int32),
+                                        _p(vox, C.c_int32), _p(anode, C.c_int32), _p(self.tdist, C.c_double),
+                                        det // self.n_det, det % self.n_det, _p(I, C.c_double))
+        return I
+
+    def scintillation(self, I):
+        I = np.ascontiguousarray(I, dtype=np.float64)
+        S = np.zeros(self.l.n_ticks)
+        self.lib.ora_light_scintillation(C.byref(self.l), _p(I, C.c_double), _p(S, C.c_double))
+        return S
+
+    def fluctuate(self, S, det: int, event_id: int = 0):
+        S = np.ascontiguousarray(S, dtype=np.float64)
+        n = np.zeros(self.l.n_ticks)
+        mg = np.zeros(self.l.n_ticks)
+        self.lib.ora_light_fluctuate(C.byref(self.c), C.byref(self.l), event_id, int(det), _p(S, C.c_double),
+                                     _p(n, C.c_double), _p(mg, C.c_double))
+        return n, mg
+
+    def electronics(self, n, det: int, event_id: int = 0):
+        """(V [n_ticks], samples, ADC codes, code margins) of global photosensor det."""
+        n = np.ascontiguousarray(n, dtype=np.float64)
+        T = self.l.n_ticks
+        V = np.zeros(T)
+        vs = np.zeros(self.n_samples)
+        code = np.zeros(self.n_samples, np.int32)
+        mg = np.zeros(self.n_samples)
+        self.lib.ora_light_electronics(C.byref(self.c), C.byref(self.l), event_id, int(det),
+                                       float(self.gain[det % self.n_det]), _p(n, C.c_double),
+                                       _p(self.resp, C.c_double), _p(self.amp, C.c_double), float(self.ratio),
+                                       self.n_samples, _p(V, C.c_double), _p(vs, C.c_double), _p(code, C.c_int32),
+                                       _p(mg, C.c_double))
+        return V, vs, code, mg

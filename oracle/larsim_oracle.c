@@ -673,3 +673,197 @@ void ora_track_dqdx(int64_t n, const double *x, const double *y, const double *z
         cnt[b] += 1;
     }
 }
+
+/* ================================================================ light == */
+/* Sec. 4: scintillation light on the same segments.  Tables (synthetic
+ * stand-ins for the Geant4 visibility / arrival-time tables) are inputs:
+ * vis [nv][n_det], tdist [nv][n_det][nt] with nv = nvx * nvy * nvz voxels of
+ * one TPC in local coordinates (x, y from the module corner, z = distance
+ * from the anode). */
+typedef struct ora_light {
+    int32_t nvx, nvy, nvz, n_det, nt, n_ticks, n_trunc, n_resp, noise_block, adc_bits;
+    double vox, w_ph, tick, t_start;
+    double fast_frac, tau_fast, tau_slow, poisson_max;
+    double sample, pedestal;
+} ora_light;
+
+size_t ora_light_size(void) { return sizeof(ora_light); }
+
+/* Sec. 4.1: photons of one segment, N_gamma = (1/W_ph - R/W_ion) dE, i.e.
+ * dE / W_ph - Q_R (Q_R = R dE / W_ion, the quenched ionisation of Sec. 3.1),
+ * and the photoelectrons of each photosensor of its TPC,
+ * N_pe,i = eps_i V_i[voxel] N_gamma, with the voxel of the segment's
+ * midpoint; the arrival tick shift floor((t_mid - t_start) / tick) of its
+ * midpoint time.  The voxel and the tick are integer decisions taken in FP32
+ * (the precision the GPU decides them in) with IEEE single operations in the
+ * order written.  Returns 0 for an inactive segment (anode < 0). */
+int ora_light_segment(const ora_cfg *c, const ora_light *L, const float *p /* x0 y0 z0 t0 x1 y1 z1 t1 dE */,
+                      double QR, int32_t anode, const double *vis, const double *eff, double *npe,
+                      int32_t *tick, int32_t *vox)
+{
+    for (int k = 0; k < L->n_det; ++k) npe[k] = 0.0;
+    *tick = 0;
+    *vox = -1;
+    if (anode < 0) return 0;
+    int32_t tpc = anode % c->n_tpc, m = anode / c->n_tpc;
+    int32_t mx = m % c->n_mod_x, my = m / c->n_mod_x;
+    float pitch = (float)c->pitch, D = (float)c->drift_len;
+    float Wx = (float)(c->tiles_x * c->px_per_tile) * pitch;
+    float Wy = (float)(c->tiles_y * c->px_per_tile) * pitch;
+    float xm = 0.5f * (p[0] + p[4]), ym = 0.5f * (p[1] + p[5]), zm = 0.5f * (p[2] + p[6]);
+    float tm = 0.5f * (p[3] + p[7]);
+    float xl = xm - (float)mx * Wx, yl = ym - (float)my * Wy;
+    float za = tpc == 0 ? 0.0f : 2.0f * D;
+    float zl = fabsf(zm - za);
+    float vx = (float)L->vox;
+    int ix = (int)floorf(xl / vx), iy = (int)floorf(yl / vx), iz = (int)floorf(zl / vx);
+    if (ix < 0) ix = 0;
+    if (ix > L->nvx - 1) ix = L->nvx - 1;
+    if (iy < 0) iy = 0;
+    if (iy > L->nvy - 1) iy = L->nvy - 1;
+    if (iz < 0) iz = 0;
+    if (iz > L->nvz - 1) iz = L->nvz - 1;
+    int v = (ix * L->nvy + iy) * L->nvz + iz;
+    *vox = v;
+    *tick = (int32_t)floorf((tm - (float)L->t_start) / (float)L->tick);
+    double ngam = (double)p[8] / L->w_ph - QR;
+    if (ngam < 0.0) ngam = 0.0;
+    for (int k = 0; k < L->n_det; ++k) npe[k] = eff[k] * vis[(size_t)v * L->n_det + k] * ngam;
+    return 1;
+}
+
+/* Sec. 4.2, Eq. (photocurrent) with equal table and simulation ticks: the
+ * expected photoelectrons of photosensor k of anode a arriving in tick t,
+ * I[t] = sum over the anode's segments j of f[vox_j][k][t - tick_j] N_pe,jk,
+ * for 0 <= t - tick_j < nt; summed in segment order. */
+void ora_light_photocurrent(const ora_light *L, int64_t n, const double *npe, const int32_t *tick,
+                            const int32_t *vox, const int32_t *anode, const double *tdist, int32_t a, int32_t k,
+                            double *I)
+{
+    for (int t = 0; t < L->n_ticks; ++t) I[t] = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        if (anode[j] != a || vox[j] < 0) continue;
+        double q = npe[j * L->n_det + k];
+        const double *f = tdist + ((size_t)vox[j] * L->n_det + k) * L->nt;
+        for (int u = 0; u < L->nt; ++u) {
+            int64_t t = (int64_t)tick[j] + u;
+            if (t >= 0 && t < L->n_ticks) I[t] += q * f[u];
+        }
+    }
+}
+
+/* Sec. 4.2, the truncated scintillation convolution:
+ * S[t] = sum_{u=0}^{min(t, n_trunc)} I[t - u] f_scint(u tick), with
+ * f_scint(t) = f_p / tau_p e^(-t / tau_p) + (1 - f_p) / tau_s e^(-t / tau_s)
+ * (a rate: photoelectrons per us). */
+void ora_light_scintillation(const ora_light *L, const double *I, double *S)
+{
+    for (int t = 0; t < L->n_ticks; ++t) {
+        double s = 0.0;
+        int umax = t < L->n_trunc ? t : L->n_trunc;
+        for (int u = 0; u <= umax; ++u) {
+            double tu = (double)u * L->tick;
+            double f = L->fast_frac / L->tau_fast * exp(-tu / L->tau_fast) +
+                       (1.0 - L->fast_frac) / L->tau_slow * exp(-tu / L->tau_slow);
+            s += I[t - u] * f;
+        }
+        S[t] = s;
+    }
+}
+
+/* Sec. 4.2, counting fluctuations: the observed photoelectrons of tick t of
+ * photosensor `det` (global id), from the mean lambda = S[t] tick: for
+ * lambda <= poisson_max, inverse transform sampling of the Poisson law with
+ * the uniform u of Philox block (det, t, 5, 0) (the smallest n with
+ * u <= F(n), F the Poisson CDF accumulated term by term, at most 1000 terms);
+ * above, a normal N(lambda, sqrt(lambda)) from the Box-Muller pair of block
+ * (det, t, 6, 0), floored at 0.  margin[t]: the distance of the decisions
+ * from their thresholds (|u - F| at the last two comparisons; |lambda - max|). */
+void ora_light_fluctuate(const ora_cfg *c, const ora_light *L, uint64_t event_id, int32_t det, const double *S,
+                         double *nout, double *margin)
+{
+    uint32_t key[2] = {(uint32_t)((c->seed ^ event_id) & 0xFFFFFFFFu), (uint32_t)((c->seed ^ event_id) >> 32)};
+    for (int t = 0; t < L->n_ticks; ++t) {
+        double lam = S[t] * L->tick;
+        double mg = fabs(lam - L->poisson_max);
+        if (lam <= L->poisson_max) {
+            uint32_t ctr[4] = {(uint32_t)det, (uint32_t)t, 5u, 0u}, x[4];
+            ora_philox4x32_10(ctr, key, x);
+            double u = ora_u01(x[0]);
+            double pk = exp(-lam), F = pk;
+            int k = 0;
+            double m2 = fabs(u - F);
+            while (u > F && k < 1000) {
+                ++k;
+                pk *= lam / (double)k;
+                F += pk;
+                double d = fabs(u - F);
+                m2 = d;
+                if (k >= 1) {
+                    /* the previous comparison (u > F_prev) also decided */
+                    double dp = fabs(u - (F - pk));
+                    if (dp < m2) m2 = dp;
+                }
+            }
+            if (m2 < mg) mg = m2;
+            nout[t] = (double)k;
+        } else {
+            double nn[4];
+            ora_normals(c->seed, event_id, (uint32_t)det, (uint32_t)t, 6u, 0u, nn);
+            double v = lam + sqrt(lam) * nn[0];
+            nout[t] = v > 0.0 ? v : 0.0;
+        }
+        margin[t] = mg;
+    }
+}
+
+/* Sec. 4.3, Eq. (light response) with equal response and simulation ticks:
+ * V[t] = noise(t) + G sum_{u=0}^{n_resp-1} n[t - u] resp[u], and the noise of
+ * each block of noise_block ticks, b = t / N, tau = t - b N:
+ * noise(t) = sum_{k=0}^{N/2} A_k cos(2 pi k tau / N + phi_k), phi_k = 2 pi u
+ * with u of Philox block (det, b, 7, k).  Then the digitiser: sample m at
+ * position p = m * ratio (ratio = sampling period / tick) read linearly
+ * between ticks floor(p) and floor(p) + 1, code = clamp(floor(v + pedestal +
+ * 1/2), 0, 2^bits - 1); margin[m] = distance of v + pedestal + 1/2 from the
+ * nearest integer. */
+void ora_light_electronics(const ora_cfg *c, const ora_light *L, uint64_t event_id, int32_t det, double gain,
+                           const double *n, const double *resp, const double *amp, double ratio,
+                           int32_t n_samples, double *V, double *vs, int32_t *code, double *margin)
+{
+    uint32_t key[2] = {(uint32_t)((c->seed ^ event_id) & 0xFFFFFFFFu), (uint32_t)((c->seed ^ event_id) >> 32)};
+    int N = L->noise_block;
+    int nblk = (L->n_ticks + N - 1) / N;
+    double *phi = (double *)malloc(sizeof(double) * (size_t)(N / 2 + 1));
+    for (int b = 0; b < nblk; ++b) {
+        for (int k = 0; k <= N / 2; ++k) {
+            uint32_t ctr[4] = {(uint32_t)det, (uint32_t)b, 7u, (uint32_t)k}, x[4];
+            ora_philox4x32_10(ctr, key, x);
+            phi[k] = 2.0 * ORA_PI * ora_u01(x[0]);
+        }
+        for (int tau = 0; tau < N; ++tau) {
+            int t = b * N + tau;
+            if (t >= L->n_ticks) break;
+            double s = 0.0;
+            for (int k = 0; k <= N / 2; ++k) s += amp[k] * cos(2.0 * ORA_PI * (double)k * (double)tau / (double)N + phi[k]);
+            double r = 0.0;
+            for (int u = 0; u < L->n_resp && u <= t; ++u) r += n[t - u] * resp[u];
+            V[t] = s + gain * r;
+        }
+    }
+    free(phi);
+    double top = (double)((1 << L->adc_bits) - 1);
+    for (int m = 0; m < n_samples; ++m) {
+        double p = (double)m * ratio;
+        double fl = floor(p);
+        int i = (int)fl;
+        double fr = p - fl;
+        double v = i + 1 < L->n_ticks ? (1.0 - fr) * V[i] + fr * V[i + 1] : V[i];
+        vs[m] = v;
+        double w = v + L->pedestal + 0.5;
+        double cd = floor(w);
+        margin[m] = fmin(w - cd, cd + 1.0 - w);
+        if (cd < 0.0) cd = 0.0;
+        if (cd > top) cd = top;
+        code[m] = (int32_t)cd;
+    }
+}
