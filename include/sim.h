@@ -389,6 +389,93 @@ int sim_track_dqdx(const float *x, const float *y, const float *z, const float *
                    int64_t capacity, const double *origin, const double *direction, double piece_cm,
                    int32_t n_pieces, double r_max_cm, double *dq, int32_t *count, void *stream);
 
+/* ------------------------------------------------------------ light ---- */
+/* Light path of Sec. 4 on the same segments: photon yield and photoelectrons
+ * per photosensor (Sec. 4.1), photocurrent from the arrival-time table
+ * (Sec. 4.2), the truncated scintillation convolution, counting fluctuations,
+ * and the electronics response with noise, sampling and ADC (Sec. 4.3).
+ * Photosensor ids: det = anode * n_det + k (anode as in sim_drifted.anode),
+ * n_det photosensors per TPC; a call covers all n_anodes * n_det of them
+ * (n_anodes = n_mod_x * n_mod_y * n_tpc; single events only).  Tables describe
+ * one TPC in local coordinates: x, y from the module corner, z = distance from
+ * the anode, cubic voxels of vox_cm from that corner. */
+typedef struct sim_light_config {
+    const float *vis;          /* [nvx][nvy][nvz][n_det] visibility V_i */
+    const float *tdist;        /* [nvx][nvy][nvz][n_det][nt] arrival-time fractions per tick (rows sum to 1) */
+    const float *eff;          /* [n_det] detection efficiency eps_i */
+    const float *gain;         /* [n_det] G_i, ADC per photoelectron */
+    const float *resp;         /* [n_resp] impulse response, unit sum, one tick per bin */
+    const float *noise_amp;    /* [noise_block / 2 + 1] amplitudes A_k of the noise spectrum (ADC) */
+    int32_t nvx, nvy, nvz, n_det, nt, n_resp, noise_block, adc_bits;
+    float vox_cm, w_ph_MeV;    /* voxel edge; energy per photon at zero field */
+    float tick_us, t_start_us; /* light tick and window start */
+    int32_t n_ticks, pad0;     /* window length */
+    float fast_frac, tau_fast_us, tau_slow_us, trunc_taus, poisson_max_mean;
+    float sample_us, pedestal_adc;
+} sim_light_config;
+
+/* Number of digitiser samples of the window: floor((n_ticks - 1) tick_us /
+ * sample_us) + 1 (ratio formed in FP64 from the FP32 fields). */
+int sim_light_n_samples(const sim_light_config *lc, int64_t *n_samples);
+
+/* Sec. 4.1 per segment (thread per segment): photons N_gamma = dE / W_ph - Q_R
+ * (Q_R = Q_a e^(t_drift / lifetime), the quenched ionisation of Sec. 3.1;
+ * floored at 0), photoelectrons npe[i][k] = eff[k] vis[voxel][k] N_gamma at
+ * the voxel of the midpoint, and tick[i] = floor((t_mid - t_start) / tick)
+ * of the midpoint time; voxel and tick are decided with IEEE FP32 operations
+ * in that order (voxel indices clamped to the table).  Inactive segments
+ * (anode < 0): npe 0, vox -1.  npe: FP32 [n][n_det]; tick, vox: int32 [n]. */
+int sim_light_yield(const sim_config *cfg, const sim_light_config *lc, const sim_segments *seg,
+                    const sim_drifted *dr, float *npe, int32_t *tick, int32_t *vox, void *stream);
+
+/* Sec. 4.2, Eq. (photocurrent) with table and simulation ticks equal:
+ * pe[det][t] = sum over the segments j of det's anode of
+ * tdist[vox_j][k][t - tick_j] npe[j][k] (0 <= t - tick_j < nt), as 64-bit
+ * fixed point of 2^-16 photoelectrons (each term rounded once; the sum is
+ * exact, hence independent of order).  pe_fix: int64 [n_anodes * n_det][n_ticks],
+ * overwritten.  Limits: n_det <= 32, nt <= 256. */
+int sim_light_photocurrent(const sim_config *cfg, const sim_light_config *lc, const sim_segments *seg,
+                           const sim_drifted *dr, const float *npe, const int32_t *tick, const int32_t *vox,
+                           int64_t *pe_fix, void *stream);
+
+/* Sec. 4.2, the truncated scintillation convolution
+ * S[t] = sum_{u=0}^{min(t, N)} pe[t - u] f_scint(u tick),
+ * f_scint(t) = f_p / tau_p e^(-t / tau_p) + (1 - f_p) / tau_s e^(-t / tau_s),
+ * N = floor(trunc_taus tau_s / tick + 1/2), computed as the exactly
+ * equivalent pair of first-order recurrences (one per component) with the
+ * truncated tail subtracted.  scint: FP32 [n_anodes * n_det][n_ticks]
+ * (photoelectrons per us). */
+int sim_light_scintillation(const sim_config *cfg, const sim_light_config *lc, const int64_t *pe_fix,
+                            float *scint, void *stream);
+
+/* Sec. 4.2, counting fluctuations per tick: lambda = S[t] tick; lambda <=
+ * poisson_max_mean: the smallest n with u <= F(n) (Poisson CDF accumulated in
+ * FP64, at most 1000 terms), u from Philox block (det, t, 5, 0); above: a
+ * normal lambda + sqrt(lambda) z (Philox block (det, t, 6, 0)), floored at 0.
+ * Key seed ^ event_id.  pe_obs: FP32 [n_anodes * n_det][n_ticks]. */
+int sim_light_fluctuate(const sim_config *cfg, const sim_light_config *lc, uint64_t event_id, const float *scint,
+                        float *pe_obs, void *stream);
+
+/* Sec. 4.3: V[t] = noise(t) + gain[k] sum_{u < n_resp} pe_obs[t - u] resp[u],
+ * noise on blocks of noise_block ticks (b = t / N, tau = t - b N):
+ * sum_{k <= N/2} A_k cos(2 pi k tau / N + phi_k), phi_k = 2 pi u of Philox
+ * block (det, b, 7, k) (an inverse FFT per block); then sample m at
+ * p = m sample_us / tick_us, read linearly between ticks floor(p) and
+ * floor(p) + 1, code = clamp(floor(v + pedestal + 1/2), 0, 2^adc_bits - 1).
+ * v: FP32 [n_anodes * n_det][n_ticks], overwritten (the analog waveform);
+ * wave: uint16 [n_anodes * n_det][n_samples].  noise_block: a power of two,
+ * 64 .. 4096; n_resp <= 2048. */
+int sim_light_electronics(const sim_config *cfg, const sim_light_config *lc, uint64_t event_id,
+                          const float *pe_obs, float *v, uint16_t *wave, void *stream);
+
+/* The whole light path for one event after sim_quench_drift: yield,
+ * photocurrent, scintillation, fluctuation and electronics, intermediates in
+ * the workspace (sim_light_workspace_size); wave as above. */
+int sim_light_workspace_size(const sim_config *cfg, const sim_light_config *lc, int64_t n_segments,
+                             size_t *bytes);
+int sim_light_event(const sim_config *cfg, const sim_light_config *lc, const sim_segments *seg,
+                    const sim_drifted *dr, uint16_t *wave, void *ws, size_t ws_bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

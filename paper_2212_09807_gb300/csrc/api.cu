@@ -363,4 +363,128 @@ int sim_track_dqdx(const float *x, const float *y, const float *z, const float *
     return e == cudaSuccess ? SIM_OK : cuda_fail(e);
 }
 
+static bool light_ok(const sim_config *c, const sim_light_config *lc)
+{
+    if (!cfg_ok(c) || !lc) return false;
+    if (!lc->vis || !lc->tdist || !lc->eff || !lc->gain || !lc->resp || !lc->noise_amp) return false;
+    if (lc->nvx < 1 || lc->nvy < 1 || lc->nvz < 1 || lc->n_det < 1 || lc->n_det > 32 || lc->nt < 1 || lc->nt > 256)
+        return false;
+    if (lc->n_resp < 1 || lc->n_resp > 2048 || lc->adc_bits < 1 || lc->adc_bits > 16) return false;
+    if (lc->noise_block < 64 || lc->noise_block > 4096 || (lc->noise_block & (lc->noise_block - 1)) != 0) return false;
+    if (!(lc->vox_cm > 0.f) || !(lc->w_ph_MeV > 0.f) || !(lc->tick_us > 0.f) || lc->n_ticks < 1) return false;
+    if (!(lc->tau_fast_us > 0.f) || !(lc->tau_slow_us > 0.f) || !(lc->trunc_taus >= 0.f) || !(lc->sample_us > 0.f))
+        return false;
+    if (!(lc->fast_frac >= 0.f && lc->fast_frac <= 1.f)) return false;
+    return (int64_t)light_n_det_total(*c, *lc) * lc->n_ticks < ((int64_t)1 << 40);
+}
+
+int sim_light_n_samples(const sim_light_config *lc, int64_t *n_samples)
+{
+    if (!lc || !n_samples || !(lc->sample_us > 0.f) || !(lc->tick_us > 0.f) || lc->n_ticks < 1)
+        return SIM_ERR_INVALID_ARG;
+    *n_samples = light_n_samples(*lc, nullptr);
+    return SIM_OK;
+}
+
+int sim_light_yield(const sim_config *cfg, const sim_light_config *lc, const sim_segments *seg, const sim_drifted *dr,
+                    float *npe, int32_t *tick, int32_t *vox, void *stream)
+{
+    if (!light_ok(cfg, lc) || !seg_ok(seg) || seg->n_events != 0) return SIM_ERR_INVALID_ARG;
+    if (seg->n > 0 && (!drifted_ok(dr) || !npe || !tick || !vox)) return SIM_ERR_INVALID_ARG;
+    const sim_drifted d0 = dr ? *dr : sim_drifted{};
+    const cudaError_t e = launch_light_yield(*cfg, *lc, *seg, d0, npe, tick, vox, (cudaStream_t)stream);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e);
+}
+
+int sim_light_photocurrent(const sim_config *cfg, const sim_light_config *lc, const sim_segments *seg,
+                           const sim_drifted *dr, const float *npe, const int32_t *tick, const int32_t *vox,
+                           int64_t *pe_fix, void *stream)
+{
+    if (!light_ok(cfg, lc) || !seg_ok(seg) || seg->n_events != 0 || !pe_fix) return SIM_ERR_INVALID_ARG;
+    if (seg->n > 0 && (!drifted_ok(dr) || !npe || !tick || !vox)) return SIM_ERR_INVALID_ARG;
+    const sim_drifted d0 = dr ? *dr : sim_drifted{};
+    const cudaError_t e = launch_light_photocurrent(*cfg, *lc, *seg, d0, npe, tick, vox, pe_fix, (cudaStream_t)stream);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e);
+}
+
+int sim_light_scintillation(const sim_config *cfg, const sim_light_config *lc, const int64_t *pe_fix, float *scint,
+                            void *stream)
+{
+    if (!light_ok(cfg, lc) || !pe_fix || !scint) return SIM_ERR_INVALID_ARG;
+    const cudaError_t e = launch_light_scint(*cfg, *lc, pe_fix, scint, (cudaStream_t)stream);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e);
+}
+
+int sim_light_fluctuate(const sim_config *cfg, const sim_light_config *lc, uint64_t event_id, const float *scint,
+                        float *pe_obs, void *stream)
+{
+    if (!light_ok(cfg, lc) || !scint || !pe_obs) return SIM_ERR_INVALID_ARG;
+    const cudaError_t e = launch_light_fluct(*cfg, *lc, event_id, scint, pe_obs, (cudaStream_t)stream);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e);
+}
+
+int sim_light_electronics(const sim_config *cfg, const sim_light_config *lc, uint64_t event_id, const float *pe_obs,
+                          float *v, uint16_t *wave, void *stream)
+{
+    if (!light_ok(cfg, lc) || !pe_obs || !v || !wave) return SIM_ERR_INVALID_ARG;
+    const cudaError_t e = launch_light_electronics(*cfg, *lc, event_id, pe_obs, v, wave, (cudaStream_t)stream);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e);
+}
+
+namespace {
+struct LightLayout {
+    size_t npe, tick, vox, pe, scint, obs, v, total;
+};
+LightLayout light_layout(const sim_config &c, const sim_light_config &lc, int64_t n)
+{
+    LightLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o += align256(bytes);
+        return at;
+    };
+    const size_t rows = (size_t)light_n_det_total(c, lc) * (size_t)lc.n_ticks;
+    L.npe = take(4 * (size_t)n * lc.n_det);
+    L.tick = take(4 * (size_t)n);
+    L.vox = take(4 * (size_t)n);
+    L.pe = take(8 * rows);
+    L.scint = take(4 * rows);
+    L.obs = take(4 * rows);
+    L.v = take(4 * rows);
+    L.total = o;
+    return L;
+}
+}  // namespace
+
+int sim_light_workspace_size(const sim_config *cfg, const sim_light_config *lc, int64_t n_segments, size_t *bytes)
+{
+    if (!light_ok(cfg, lc) || n_segments < 0 || !bytes) return SIM_ERR_INVALID_ARG;
+    *bytes = light_layout(*cfg, *lc, n_segments).total;
+    return SIM_OK;
+}
+
+int sim_light_event(const sim_config *cfg, const sim_light_config *lc, const sim_segments *seg, const sim_drifted *dr,
+                    uint16_t *wave, void *ws, size_t ws_bytes, void *stream)
+{
+    if (!light_ok(cfg, lc) || !seg_ok(seg) || seg->n_events != 0 || !wave || !ws) return SIM_ERR_INVALID_ARG;
+    if (seg->n > 0 && !drifted_ok(dr)) return SIM_ERR_INVALID_ARG;
+    const LightLayout L = light_layout(*cfg, *lc, seg->n);
+    if (ws_bytes < L.total) return SIM_ERR_CAPACITY;
+    char *w = reinterpret_cast<char *>(ws);
+    const cudaStream_t st = (cudaStream_t)stream;
+    const sim_drifted d0 = dr ? *dr : sim_drifted{};
+    float *npe = reinterpret_cast<float *>(w + L.npe);
+    int32_t *tick = reinterpret_cast<int32_t *>(w + L.tick), *vox = reinterpret_cast<int32_t *>(w + L.vox);
+    int64_t *pe = reinterpret_cast<int64_t *>(w + L.pe);
+    float *scint = reinterpret_cast<float *>(w + L.scint), *obs = reinterpret_cast<float *>(w + L.obs);
+    float *v = reinterpret_cast<float *>(w + L.v);
+    cudaError_t e = launch_light_yield(*cfg, *lc, *seg, d0, npe, tick, vox, st);
+    if (e == cudaSuccess) e = launch_light_photocurrent(*cfg, *lc, *seg, d0, npe, tick, vox, pe, st);
+    if (e == cudaSuccess) e = launch_light_scint(*cfg, *lc, pe, scint, st);
+    if (e == cudaSuccess) e = launch_light_fluct(*cfg, *lc, seg->event_id, scint, obs, st);
+    if (e == cudaSuccess) e = launch_light_electronics(*cfg, *lc, seg->event_id, obs, v, wave, st);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e);
+}
+
 }  // extern "C"

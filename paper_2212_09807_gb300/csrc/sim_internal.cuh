@@ -202,6 +202,22 @@ cudaError_t launch_track_dqdx(const float *x, const float *y, const float *z, co
                               int64_t cap, const double origin[3], const double dir[3], double piece, int32_t n_bins,
                               double r_max, double *dq, int32_t *count, cudaStream_t st);
 
+// Light path (light.cu).
+int light_n_det_total(const sim_config &c, const sim_light_config &lc);
+int64_t light_n_samples(const sim_light_config &lc, double *ratio);
+int light_n_trunc(const sim_light_config &lc);
+cudaError_t launch_light_yield(const sim_config &c, const sim_light_config &lc, const sim_segments &s,
+                               const sim_drifted &d, float *npe, int32_t *tick, int32_t *vox, cudaStream_t st);
+cudaError_t launch_light_photocurrent(const sim_config &c, const sim_light_config &lc, const sim_segments &s,
+                                      const sim_drifted &d, const float *npe, const int32_t *tick,
+                                      const int32_t *vox, int64_t *pe, cudaStream_t st);
+cudaError_t launch_light_scint(const sim_config &c, const sim_light_config &lc, const int64_t *pe, float *S,
+                               cudaStream_t st);
+cudaError_t launch_light_fluct(const sim_config &c, const sim_light_config &lc, uint64_t event_id, const float *S,
+                               float *out, cudaStream_t st);
+cudaError_t launch_light_electronics(const sim_config &c, const sim_light_config &lc, uint64_t event_id,
+                                     const float *pe_obs, float *V, uint16_t *wave, cudaStream_t st);
+
 // Exclusive scan of int32 `in[0..n)` into `out[0..n]` (out[n] = total) with
 // the total also stored to *total64 when non-null.  In place allowed.
 size_t scan_scratch_bytes(int64_t n);

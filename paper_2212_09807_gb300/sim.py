@@ -85,6 +85,15 @@ class SimTruth(C.Structure):
                 ("capacity", C.c_int64)]
 
 
+class SimLightConfig(C.Structure):
+    _fields_ = [(k, _P) for k in ("vis", "tdist", "eff", "gain", "resp", "noise_amp")] + \
+               [(k, C.c_int32) for k in ("nvx", "nvy", "nvz", "n_det", "nt", "n_resp", "noise_block", "adc_bits")] + \
+               [("vox_cm", C.c_float), ("w_ph_MeV", C.c_float), ("tick_us", C.c_float), ("t_start_us", C.c_float),
+                ("n_ticks", C.c_int32), ("pad0", C.c_int32)] + \
+               [(k, C.c_float) for k in ("fast_frac", "tau_fast_us", "tau_slow_us", "trunc_taus", "poisson_max_mean",
+                                         "sample_us", "pedestal_adc")]
+
+
 class SimEventView(C.Structure):
     _fields_ = [("dr", SimDrifted)] + [(k, _P) for k in (
         "seg_pix_off", "seg_pix_ids", "active_pixels", "pix_seg_off", "pix_seg_ids", "current", "counts")]
@@ -129,6 +138,20 @@ def lib():
         L.sim_hit_points.argtypes = [cp(SimConfig), cp(SimHits), _P, _P, _P, _P, _P]
         L.sim_track_dqdx.argtypes = [_P, _P, _P, _P, _P, C.c_int64, cp(C.c_double), cp(C.c_double), C.c_double,
                                      C.c_int32, C.c_double, _P, _P, _P]
+        L.sim_light_n_samples.argtypes = [cp(SimLightConfig), cp(C.c_int64)]
+        L.sim_light_yield.argtypes = [cp(SimConfig), cp(SimLightConfig), cp(SimSegments), cp(SimDrifted), _P, _P, _P,
+                                      _P]
+        L.sim_light_photocurrent.argtypes = [cp(SimConfig), cp(SimLightConfig), cp(SimSegments), cp(SimDrifted), _P,
+                                             _P, _P, _P, _P]
+        L.sim_light_scintillation.argtypes = [cp(SimConfig), cp(SimLightConfig), _P, _P, _P]
+        L.sim_light_fluctuate.argtypes = [cp(SimConfig), cp(SimLightConfig), C.c_uint64, _P, _P, _P]
+        L.sim_light_electronics.argtypes = [cp(SimConfig), cp(SimLightConfig), C.c_uint64, _P, _P, _P, _P]
+        L.sim_light_workspace_size.argtypes = [cp(SimConfig), cp(SimLightConfig), C.c_int64, cp(C.c_size_t)]
+        L.sim_light_event.argtypes = [cp(SimConfig), cp(SimLightConfig), cp(SimSegments), cp(SimDrifted), _P, _P,
+                                      C.c_size_t, _P]
+        for f in ("sim_light_n_samples", "sim_light_yield", "sim_light_photocurrent", "sim_light_scintillation",
+                  "sim_light_fluctuate", "sim_light_electronics", "sim_light_workspace_size", "sim_light_event"):
+            getattr(L, f).restype = C.c_int
         for f in ("sim_workspace_size", "sim_quench_drift", "sim_pixel_map", "sim_induced_current",
                   "sim_induced_current_range", "sim_electronics", "sim_event", "sim_event_view_of",
                   "sim_pixel_map_noalloc", "sim_response_cumulative", "sim_hit_truth_workspace_size", "sim_hit_truth", "sim_hit_points",
@@ -564,3 +587,80 @@ class EventIO:
             d2h += nh * src.element_size()
         torch.cuda.current_stream().synchronize()
         return out, counts, 9 * 4 * n, d2h
+
+
+# ------------------------------------------------------------------ light --
+
+class Light:
+    """Light-path configuration with its tables on the device (Sec. 4).
+
+    ``params``: the light parameters (synth.light.LIGHT layout); ``tables``:
+    FP32 numpy tables (vis, tdist, eff, gain, resp, noise); the window is
+    [t_start_us, t_start_us + n_ticks * tick_us)."""
+
+    def __init__(self, params: dict, tables: dict, t_start_us: float, n_ticks: int, device="cuda"):
+        import torch
+        self.t = {k: torch.as_tensor(np.ascontiguousarray(v, dtype=np.float32), device=device)
+                  for k, v in tables.items()}
+        nvx, nvy, nvz, nd, nt = tables["tdist"].shape
+        c = SimLightConfig()
+        c.vis, c.tdist, c.eff, c.gain = (_ptr(self.t[k]) for k in ("vis", "tdist", "eff", "gain"))
+        c.resp, c.noise_amp = _ptr(self.t["resp"]), _ptr(self.t["noise"])
+        c.nvx, c.nvy, c.nvz, c.n_det, c.nt = nvx, nvy, nvz, nd, nt
+        c.n_resp, c.noise_block, c.adc_bits = len(tables["resp"]), int(params["noise_block"]), int(params["adc_bits"])
+        c.vox_cm, c.w_ph_MeV, c.tick_us = params["vox_cm"], params["w_ph_MeV"], params["tick_us"]
+        c.t_start_us, c.n_ticks = float(t_start_us), int(n_ticks)
+        c.fast_frac, c.tau_fast_us, c.tau_slow_us = params["fast_frac"], params["tau_fast_us"], params["tau_slow_us"]
+        c.trunc_taus, c.poisson_max_mean = params["trunc_taus"], params["poisson_max_mean"]
+        c.sample_us, c.pedestal_adc = params["sample_us"], params["pedestal"]
+        self.c = c
+        self.n_det = nd
+        self.n_ticks = int(n_ticks)
+        ns = C.c_int64()
+        _check(lib().sim_light_n_samples(C.byref(c), C.byref(ns)), "sim_light_n_samples")
+        self.n_samples = int(ns.value)
+
+    def n_det_total(self, cfg: SimConfig) -> int:
+        return cfg.n_mod_x * cfg.n_mod_y * cfg.n_tpc * self.n_det
+
+
+def sim_light_yield(cfg: SimConfig, light: Light, seg: Segments, dr: Drifted, npe, tick, vox, stream=None):
+    s, d = seg.struct(), dr.struct()
+    _check(lib().sim_light_yield(C.byref(cfg), C.byref(light.c), C.byref(s), C.byref(d), _ptr(npe), _ptr(tick),
+                                 _ptr(vox), _stream(stream)), "sim_light_yield")
+
+
+def sim_light_photocurrent(cfg: SimConfig, light: Light, seg: Segments, dr: Drifted, npe, tick, vox, pe_fix,
+                           stream=None):
+    s, d = seg.struct(), dr.struct()
+    _check(lib().sim_light_photocurrent(C.byref(cfg), C.byref(light.c), C.byref(s), C.byref(d), _ptr(npe),
+                                        _ptr(tick), _ptr(vox), _ptr(pe_fix), _stream(stream)),
+           "sim_light_photocurrent")
+
+
+def sim_light_scintillation(cfg: SimConfig, light: Light, pe_fix, scint, stream=None):
+    _check(lib().sim_light_scintillation(C.byref(cfg), C.byref(light.c), _ptr(pe_fix), _ptr(scint),
+                                         _stream(stream)), "sim_light_scintillation")
+
+
+def sim_light_fluctuate(cfg: SimConfig, light: Light, event_id: int, scint, pe_obs, stream=None):
+    _check(lib().sim_light_fluctuate(C.byref(cfg), C.byref(light.c), int(event_id), _ptr(scint), _ptr(pe_obs),
+                                     _stream(stream)), "sim_light_fluctuate")
+
+
+def sim_light_electronics(cfg: SimConfig, light: Light, event_id: int, pe_obs, v, wave, stream=None):
+    _check(lib().sim_light_electronics(C.byref(cfg), C.byref(light.c), int(event_id), _ptr(pe_obs), _ptr(v),
+                                       _ptr(wave), _stream(stream)), "sim_light_electronics")
+
+
+def light_workspace_size(cfg: SimConfig, light: Light, n_segments: int) -> int:
+    b = C.c_size_t()
+    _check(lib().sim_light_workspace_size(C.byref(cfg), C.byref(light.c), int(n_segments), C.byref(b)),
+           "sim_light_workspace_size")
+    return int(b.value)
+
+
+def sim_light_event(cfg: SimConfig, light: Light, seg: Segments, dr: Drifted, wave, ws, stream=None):
+    s, d = seg.struct(), dr.struct()
+    _check(lib().sim_light_event(C.byref(cfg), C.byref(light.c), C.byref(s), C.byref(d), _ptr(wave), _ptr(ws),
+                                 int(ws.numel() * ws.element_size()), _stream(stream)), "sim_light_event")
