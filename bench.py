@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip timing the other induced-current forms")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-vs-plain request stream")
     ap.add_argument("--no-post", action="store_true", help="skip timing truth, hit points and dQ/dx")
+    ap.add_argument("--no-light", action="store_true", help="skip timing the light path")
     ap.add_argument("--serving-requests", type=int, default=15, help="requests per load point")
     ap.add_argument("--batched-events", type=int, default=32)
     ap.add_argument("--batched-hi", type=float, default=1.0e4, help="largest event of the batched comparison")
@@ -408,6 +409,97 @@ def post_hit_steps(run, cfg, dev, reps=5):
     return out
 
 
+def light_path(dev, names=("module", "spill"), reps=5):
+    """Times the light path (Sec. 4) on the segments of a workload: each entry
+    point (yield, photocurrent, scintillation, fluctuation, electronics) with
+    CUDA events on the launching stream, L2 flushed before every pass, and the
+    whole path through sim_light_event."""
+    import torch
+    from paper_2212_09807_gb300 import sim
+    from synth import light
+    out = {}
+    props = torch.cuda.get_device_properties(dev)
+    hbm = measured_peaks().get("hbm_gbs", 6800.0)
+    sm_mhz = measured_peaks().get("sm_max_mhz", 2070.0)
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12      # TFLOP/s, FMA lanes x clock
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)
+    for name in names:
+        cfg, seg, desc = workload(name)
+        L = dict(light.LIGHT)
+        tab = light.tables(cfg, L)
+        t0, T = light.window(float(seg["t0"].min()), float(seg["t1"].max()))
+        lt = sim.Light(L, tab, t0, T, dev)
+        c = sim.make_config(cfg)
+        segs = sim.Segments.from_numpy(seg, 1, dev)
+        n = segs.n
+        dr = sim.Drifted(n, dev)
+        sim.sim_quench_drift(c, segs, dr)
+        ndt = lt.n_det_total(c)
+        f32 = dict(dtype=torch.float32, device=dev)
+        npe = torch.empty(n * lt.n_det, **f32)
+        tick = torch.empty(n, dtype=torch.int32, device=dev)
+        vox = torch.empty(n, dtype=torch.int32, device=dev)
+        pe = torch.empty(ndt * T, dtype=torch.int64, device=dev)
+        S, obs, V = (torch.empty(ndt * T, **f32) for _ in range(3))
+        wave = torch.empty(ndt * lt.n_samples, dtype=torch.uint16, device=dev)
+        calls = [("yield", lambda: sim.sim_light_yield(c, lt, segs, dr, npe, tick, vox)),
+                 ("photocurrent", lambda: sim.sim_light_photocurrent(c, lt, segs, dr, npe, tick, vox, pe)),
+                 ("scintillation", lambda: sim.sim_light_scintillation(c, lt, pe, S)),
+                 ("fluctuate", lambda: sim.sim_light_fluctuate(c, lt, 1, S, obs)),
+                 ("electronics", lambda: sim.sim_light_electronics(c, lt, 1, obs, V, wave))]
+        ws = torch.empty((sim.light_workspace_size(c, lt, n) + 7) // 8, dtype=torch.int64, device=dev)
+        wave2 = torch.empty_like(wave)
+        for _ in range(2):
+            for _, f in calls:
+                f()
+            sim.sim_light_event(c, lt, segs, dr, wave2, ws)
+        torch.cuda.synchronize()
+        per = np.zeros((reps, len(calls)))
+        whole = []
+        for r in range(reps):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(calls) + 1)]
+            ev[0].record()
+            for i, (_, f) in enumerate(calls):
+                f()
+                ev[i + 1].record()
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sim.sim_light_event(c, lt, segs, dr, wave2, ws)
+            e1.record()
+            torch.cuda.synchronize()
+            per[r] = [ev[i].elapsed_time(ev[i + 1]) for i in range(len(calls))]
+            whole.append(e0.elapsed_time(e1))
+        assert torch.equal(wave, wave2)
+        ms = {k: float(per[:, i].mean()) for i, (k, _) in enumerate(calls)}
+        ticks = ndt * T
+        act = int((dr.anode >= 0).sum().item())
+        terms = act * lt.n_det * L["nt"]
+        rl = {
+            "scintillation": {"bound": "hbm", "bytes_per_tick": 20,
+                              "achieved": 20 * ticks / (ms["scintillation"] / 1e3) / 1e9, "peak": hbm,
+                              "unit": "GB/s"},
+            "fluctuate": {"bound": "hbm", "bytes_per_tick": 8,
+                          "achieved": 8 * ticks / (ms["fluctuate"] / 1e3) / 1e9, "peak": hbm, "unit": "GB/s"},
+            "electronics": {"bound": "alu", "flop_per_tick": 2 * L["n_resp"],
+                            "achieved": 2 * L["n_resp"] * ticks / (ms["electronics"] / 1e3) / 1e12,
+                            "peak": fp32_peak, "unit": "TFLOP/s",
+                            "peak_note": "FP32 FMA lanes x SMs x max SM clock (derived, not measured)"},
+            "photocurrent": {"terms": terms, "terms_per_s": terms / (ms["photocurrent"] / 1e3)},
+        }
+        for v in rl.values():
+            if "peak" in v:
+                v["frac"] = v["achieved"] / v["peak"]
+        out[name] = {"workload": desc, "segments": n, "photosensors": ndt, "ticks": T,
+                     "window_us": [t0, t0 + T * float(np.float32(L["tick_us"]))], "samples": lt.n_samples,
+                     "ms": ms, "ms_whole_path": float(np.mean(whole)),
+                     "segments_per_s": n / (float(np.mean(whole)) / 1e3), "roofline": rl}
+        del npe, pe, S, obs, V, wave, wave2, ws
+        torch.cuda.empty_cache()
+    return out
+
+
 def form_roofline(run, cfg, precision, a4_s, props, sm_mhz, dev):
     """Roofline of the induced-current kernel of one form: FP32 direct against
     the FP32 FMA peak; tensor-core forms against the measured dense 16-bit
@@ -584,6 +676,8 @@ def run_ours(args):
     post = post_hit_steps(run, cfg, dev) if not args.no_post else None
     del run, io
     torch.cuda.empty_cache()
+    light_res = light_path(dev) if not args.no_light else None
+    torch.cuda.empty_cache()
 
     batched = (batched_vs_plain(cfg, lut, dev, args.batched_events, 1.0e3, args.batched_hi,
                                 reps=1 if args.batched_events > 64 else 2) if not args.no_batched else None)
@@ -611,7 +705,7 @@ def run_ours(args):
                                   "induced_current": float(per[:, 2].mean()),
                                   "electronics": float(per[:, 3].mean())},
             "roofline": roofline, "forms": forms, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,
-            "serving": serving, "after_front_end": post,
+            "serving": serving, "after_front_end": post, "light": light_res,
             "gpu_launches": KERNELS_PER_STEP[args.precision] * args.steps, "clocks": clocks,
         }))
     if pg:
