@@ -468,6 +468,15 @@ int sim_light_fluctuate(const sim_config *cfg, const sim_light_config *lc, uint6
 int sim_light_electronics(const sim_config *cfg, const sim_light_config *lc, uint64_t event_id,
                           const float *pe_obs, float *v, uint16_t *wave, void *stream);
 
+/* Sec. 4.4, the default light truth: for each segment and photosensor k of
+ * its TPC, the photoelectrons npe[i][k] of sim_light_yield and their mean
+ * arrival time (us) on the simulation's tick grid, before the scintillation
+ * delay: t_arrival[i][k] = t_start + (tick[i] + sum_u (u + 1/2)
+ * tdist[vox[i]][k][u]) tick (FP64, rounded to FP32; 0 for vox < 0).
+ * tick, vox: from sim_light_yield; t_arrival: FP32 [n_segments][n_det]. */
+int sim_light_truth(const sim_config *cfg, const sim_light_config *lc, int64_t n_segments, const int32_t *tick,
+                    const int32_t *vox, float *t_arrival, void *stream);
+
 /* The whole light path for one event after sim_quench_drift: yield,
  * photocurrent, scintillation, fluctuation and electronics, intermediates in
  * the workspace (sim_light_workspace_size); wave as above. */

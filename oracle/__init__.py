@@ -1,4 +1,6 @@
-"""FP64 CPU oracle of the pixelated-LArTPC charge path (arXiv:2212.09807, Sec. 3).
+"""FP64 CPU oracle of the pixelated-LArTPC simulation (arXiv:2212.09807: the
+charge path of Sec. 3, the light path of Sec. 4, and the per-hit steps after
+the front end).
 
 TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the
 benchmark's CPU-baseline leg, never by the CUDA path.  The arithmetic lives in
@@ -361,6 +363,7 @@ class LightOracle:
         self.lib.ora_light_electronics.argtypes = [C.POINTER(_Cfg), C.POINTER(_Light), C.c_uint64, C.c_int32,
                                                    C.c_double, f64p, f64p, f64p, C.c_double, C.c_int32, f64p, f64p,
                                                    i32p, f64p]
+        self.lib.ora_light_truth.argtypes = [C.POINTER(_Light), C.c_int64, i32p, i32p, f64p, f64p]
         self.c = make_cfg(cfg, dict(nb=1, nt=1, bins_per_pitch=1))
         l = _Light()
         nvx, nvy, nvz, nd, nt = tab["tdist"].shape
@@ -416,6 +419,15 @@ class LightOracle:
                                         _p(vox, C.c_int32), _p(anode, C.c_int32), _p(self.tdist, C.c_double),
                                         det // self.n_det, det % self.n_det, _p(I, C.c_double))
         return I
+
+    def truth(self, tick, vox):
+        """Mean arrival time (us) of each segment's photoelectrons at each photosensor (Sec. 4.4)."""
+        tick = np.ascontiguousarray(tick, dtype=np.int32)
+        vox = np.ascontiguousarray(vox, dtype=np.int32)
+        out = np.zeros((len(tick), self.n_det))
+        self.lib.ora_light_truth(C.byref(self.l), len(tick), _p(tick, C.c_int32), _p(vox, C.c_int32),
+                                 _p(self.tdist, C.c_double), _p(out, C.c_double))
+        return out
 
     def scintillation(self, I):
         I = np.ascontiguousarray(I, dtype=np.float64)

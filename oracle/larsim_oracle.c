@@ -27,6 +27,12 @@
  *   ora_hit_point       Sec. 6: hit -> 3-D point (pixel centre, inverse of
  *                       Eq. (drift))
  *   ora_track_dqdx      Sec. 6: dQ/dx in pieces of a known straight track
+ *   ora_light_segment   Sec. 4.1: photons and photoelectrons per photosensor
+ *   ora_light_photocurrent  Sec. 4.2, Eq. (photocurrent)
+ *   ora_light_scintillation Sec. 4.2, the truncated scintillation convolution
+ *   ora_light_fluctuate Sec. 4.2, Poisson / normal counting fluctuations
+ *   ora_light_electronics   Sec. 4.3, response, noise, sampling, ADC
+ *   ora_light_truth     Sec. 4.4, mean arrival time per segment and photosensor
  *   ora_philox4x32_10   counter-based generator of Salmon et al., SC'11
  *                       ("Parallel random numbers: as easy as 1, 2, 3")
  *
@@ -865,5 +871,27 @@ void ora_light_electronics(const ora_cfg *c, const ora_light *L, uint64_t event_
         if (cd < 0.0) cd = 0.0;
         if (cd > top) cd = top;
         code[m] = (int32_t)cd;
+    }
+}
+
+/* Sec. 4.4 (the default light truth): with the photoelectrons of each
+ * segment and photosensor (ora_light_segment), their mean arrival time on the
+ * simulation's tick grid, before the scintillation delay:
+ * t = t_start + (tick_j + sum_u (u + 1/2) f[vox_j][k][u]) tick.  Inactive
+ * segments (vox < 0) get 0. */
+void ora_light_truth(const ora_light *L, int64_t n, const int32_t *tick, const int32_t *vox, const double *tdist,
+                     double *t_arr)
+{
+    for (int64_t j = 0; j < n; ++j) {
+        for (int k = 0; k < L->n_det; ++k) {
+            if (vox[j] < 0) {
+                t_arr[j * L->n_det + k] = 0.0;
+                continue;
+            }
+            const double *f = tdist + ((size_t)vox[j] * L->n_det + k) * L->nt;
+            double m = 0.0;
+            for (int u = 0; u < L->nt; ++u) m += ((double)u + 0.5) * f[u];
+            t_arr[j * L->n_det + k] = L->t_start + ((double)tick[j] + m) * L->tick;
+        }
     }
 }

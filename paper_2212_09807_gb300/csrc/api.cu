@@ -431,6 +431,15 @@ int sim_light_electronics(const sim_config *cfg, const sim_light_config *lc, uin
     return e == cudaSuccess ? SIM_OK : cuda_fail(e);
 }
 
+int sim_light_truth(const sim_config *cfg, const sim_light_config *lc, int64_t n_segments, const int32_t *tick,
+                    const int32_t *vox, float *t_arrival, void *stream)
+{
+    if (!light_ok(cfg, lc) || n_segments < 0) return SIM_ERR_INVALID_ARG;
+    if (n_segments > 0 && (!tick || !vox || !t_arrival)) return SIM_ERR_INVALID_ARG;
+    const cudaError_t e = launch_light_truth(*lc, n_segments, tick, vox, t_arrival, (cudaStream_t)stream);
+    return e == cudaSuccess ? SIM_OK : cuda_fail(e);
+}
+
 namespace {
 struct LightLayout {
     size_t npe, tick, vox, pe, scint, obs, v, total;

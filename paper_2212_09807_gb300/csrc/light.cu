@@ -27,6 +27,9 @@
 //  * k_light_response: one CTA per (photosensor, 1024 ticks): the input span
 //    and the response in shared memory, four outputs per thread.
 //  * k_light_digitize: one thread per sample.
+//  * k_light_truth: one thread per (segment, photosensor): the mean arrival
+//    time of the segment's photoelectrons (Sec. 4.4 default truth, with the
+//    photoelectrons of k_light_yield).
 #include "sim_internal.cuh"
 
 namespace larsim {
@@ -406,6 +409,27 @@ __global__ void __launch_bounds__(256) k_light_digitize(sim_light_config lc, int
     }
 }
 
+// Sec. 4.4 default truth: mean arrival time of each segment's photoelectrons
+// at each photosensor, t_start + (tick + sum_u (u + 1/2) f[u]) tick.
+__global__ void __launch_bounds__(256) k_light_truth(sim_light_config lc, int64_t n, const int32_t *tick,
+                                                     const int32_t *vox, float *t_arr)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nd = lc.n_det;
+    if (i >= n * nd) return;
+    const int64_t j = i / nd;
+    const int k = (int)(i - j * nd);
+    const int v = vox[j];
+    if (v < 0) {
+        t_arr[i] = 0.f;
+        return;
+    }
+    const float *f = lc.tdist + ((size_t)v * nd + k) * lc.nt;
+    double m = 0.0;
+    for (int u = 0; u < lc.nt; ++u) m += ((double)u + 0.5) * (double)__ldg(f + u);
+    t_arr[i] = (float)((double)lc.t_start_us + ((double)tick[j] + m) * (double)lc.tick_us);
+}
+
 int sm_count()
 {
     int dev = 0, sms = 0;
@@ -439,6 +463,15 @@ cudaError_t launch_light_yield(const sim_config &c, const sim_light_config &lc, 
     if (s.n == 0) return cudaSuccess;
     k_light_yield<<<(unsigned)((s.n + 255) / 256), 256, 0, st>>>(lc, light_geo(c), c.lifetime_us, s, d, npe, tick,
                                                                    vox);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_light_truth(const sim_light_config &lc, int64_t n, const int32_t *tick, const int32_t *vox,
+                               float *t_arr, cudaStream_t st)
+{
+    const int64_t tot = n * lc.n_det;
+    if (tot == 0) return cudaSuccess;
+    k_light_truth<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(lc, n, tick, vox, t_arr);
     return cudaGetLastError();
 }
 

@@ -215,6 +215,8 @@ cudaError_t launch_light_scint(const sim_config &c, const sim_light_config &lc, 
                                cudaStream_t st);
 cudaError_t launch_light_fluct(const sim_config &c, const sim_light_config &lc, uint64_t event_id, const float *S,
                                float *out, cudaStream_t st);
+cudaError_t launch_light_truth(const sim_light_config &lc, int64_t n, const int32_t *tick, const int32_t *vox,
+                               float *t_arr, cudaStream_t st);
 cudaError_t launch_light_electronics(const sim_config &c, const sim_light_config &lc, uint64_t event_id,
                                      const float *pe_obs, float *V, uint16_t *wave, cudaStream_t st);
 

@@ -146,11 +146,13 @@ def lib():
         L.sim_light_scintillation.argtypes = [cp(SimConfig), cp(SimLightConfig), _P, _P, _P]
         L.sim_light_fluctuate.argtypes = [cp(SimConfig), cp(SimLightConfig), C.c_uint64, _P, _P, _P]
         L.sim_light_electronics.argtypes = [cp(SimConfig), cp(SimLightConfig), C.c_uint64, _P, _P, _P, _P]
+        L.sim_light_truth.argtypes = [cp(SimConfig), cp(SimLightConfig), C.c_int64, _P, _P, _P, _P]
         L.sim_light_workspace_size.argtypes = [cp(SimConfig), cp(SimLightConfig), C.c_int64, cp(C.c_size_t)]
         L.sim_light_event.argtypes = [cp(SimConfig), cp(SimLightConfig), cp(SimSegments), cp(SimDrifted), _P, _P,
                                       C.c_size_t, _P]
         for f in ("sim_light_n_samples", "sim_light_yield", "sim_light_photocurrent", "sim_light_scintillation",
-                  "sim_light_fluctuate", "sim_light_electronics", "sim_light_workspace_size", "sim_light_event"):
+                  "sim_light_fluctuate", "sim_light_electronics", "sim_light_workspace_size", "sim_light_event",
+                  "sim_light_truth"):
             getattr(L, f).restype = C.c_int
         for f in ("sim_workspace_size", "sim_quench_drift", "sim_pixel_map", "sim_induced_current",
                   "sim_induced_current_range", "sim_electronics", "sim_event", "sim_event_view_of",
@@ -651,6 +653,11 @@ def sim_light_fluctuate(cfg: SimConfig, light: Light, event_id: int, scint, pe_o
 def sim_light_electronics(cfg: SimConfig, light: Light, event_id: int, pe_obs, v, wave, stream=None):
     _check(lib().sim_light_electronics(C.byref(cfg), C.byref(light.c), int(event_id), _ptr(pe_obs), _ptr(v),
                                        _ptr(wave), _stream(stream)), "sim_light_electronics")
+
+
+def sim_light_truth(cfg: SimConfig, light: Light, n_segments: int, tick, vox, t_arrival, stream=None):
+    _check(lib().sim_light_truth(C.byref(cfg), C.byref(light.c), int(n_segments), _ptr(tick), _ptr(vox),
+                                 _ptr(t_arrival), _stream(stream)), "sim_light_truth")
 
 
 def light_workspace_size(cfg: SimConfig, light: Light, n_segments: int) -> int:

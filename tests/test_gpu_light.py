@@ -80,6 +80,14 @@ def _check_steps(cfg, seg, lr, g, dets, lo):
     act = d["anode"] >= 0
     assert np.array_equal(g["vox"][act], vox[act]) and np.array_equal(g["tick"][act], tick[act])
     assert np.allclose(g["npe"], npe, rtol=1e-6, atol=1e-9 * max(1.0, npe.max()))
+    # light truth: mean arrival time per (segment, photosensor)
+    n = lr.seg.n
+    t_arr = torch.empty(max(n, 1) * lr.light.n_det, dtype=torch.float32, device="cuda:0")
+    sim.sim_light_truth(lr.c, lr.light, n, lr.tick, lr.vox, t_arr)
+    torch.cuda.synchronize()
+    ref_t = lo.truth(tick, vox)
+    got_t = t_arr[: n * lr.light.n_det].cpu().numpy().reshape(n, -1)
+    assert np.allclose(got_t, ref_t, rtol=1e-6, atol=1e-6)
     nd = lr.light.n_det
     n_cmp = n_pois = 0
     for det in dets:

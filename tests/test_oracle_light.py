@@ -200,3 +200,24 @@ def test_digitiser_samples_a_ramp():
     exp = np.clip(np.floor(vs + ped + 0.5), 0, 2 ** L["adc_bits"] - 1)
     assert np.array_equal(code, exp.astype(np.int32))
     assert lo2.n_samples == int(np.floor(2047 / lo2.ratio)) + 1
+
+
+def test_light_truth_arrival_time_of_a_one_bin_row():
+    """A table row concentrated in bin b gives the mean arrival time
+    t_start + (tick + b + 1/2) tick; a general row gives its mean."""
+    cfg, L, tab, lo = _setup()
+    tab2 = dict(tab)
+    td = np.zeros_like(tab["tdist"])
+    td[..., 0, 5] = 1.0
+    td[..., 1, :] = tab["tdist"][..., 1, :]
+    tab2["tdist"] = td
+    lo2 = oracle.LightOracle(cfg, L, tab2, -0.05, 4096)
+    tick = np.array([100, -3, 7], np.int32)
+    vox = np.array([4, 9, -1], np.int32)
+    t = lo2.truth(tick, vox)
+    dt, t0 = float(np.float32(L["tick_us"])), float(np.float32(-0.05))
+    assert t[0, 0] == pytest.approx(t0 + (100 + 5.5) * dt, rel=1e-14)
+    assert t[1, 0] == pytest.approx(t0 + (-3 + 5.5) * dt, rel=1e-14)
+    f = tab["tdist"].reshape(-1, L["n_det"], L["nt"]).astype(np.float64)[4, 1]
+    assert t[0, 1] == pytest.approx(t0 + (100 + ((np.arange(L["nt"]) + 0.5) * f).sum()) * dt, rel=1e-14)
+    assert np.all(t[2] == 0.0)
