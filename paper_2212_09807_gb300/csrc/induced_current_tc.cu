@@ -129,6 +129,7 @@ struct TcArgs {
     float *slices;                          // partial currents [slice][kGroup][n_ticks]
     Rec *recs, *sorted;                     // [grid][kRecCap]
     int *offt;                              // [grid][kGroup][kMaxBins + 1]
+    uint32_t *bmask;                        // [grid][kGroup][kMaxBins][8]: arrival blocks of each (pixel, bin)
 };
 
 // ----------------------------------------------------- PTX wrappers ----
@@ -304,10 +305,12 @@ struct GenState {
 
 // Generates the records of the group's pixels from the cursor on, until the
 // chunk buffer is full or the group is done; sorts each pixel's part by bin
-// into `sorted`, writes its bin offsets to offt, marks the nodes it touches.
-// Returns the number of records of the chunk; st.gp == npg when done.
+// into `sorted`, writes its bin offsets to offt and, for each (pixel, bin)
+// holding records, the 256-bit mask of the arrival blocks its records' two
+// ticks fall in (relative to the pass start k0) to bmask; marks the nodes it
+// touches.  Returns the number of records of the chunk; st.gp == npg when done.
 __device__ int gen_chunk(const TcArgs &a, TcSmem *s, GenState &st, int64_t pi0, int npg, int bx_lo, int bx_hi,
-                         Rec *recs, Rec *sorted, int *offt)
+                         Rec *recs, Rec *sorted, int *offt, uint32_t *bmask, int k0)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nb = a.nb, nb2 = nb * nb, M = a.c.mc_per_sample;
@@ -406,6 +409,11 @@ __device__ int gen_chunk(const TcArgs &a, TcSmem *s, GenState &st, int64_t pi0, 
                 if (b < nb2) {
                     orow[b] = pv;
                     s->u.g.hist[b] = pv;
+                    if (v[i] > 0) {
+                        uint4 *mk = reinterpret_cast<uint4 *>(bmask + ((size_t)st.gp * kMaxBins + b) * 8);
+                        mk[0] = make_uint4(0u, 0u, 0u, 0u);
+                        mk[1] = make_uint4(0u, 0u, 0u, 0u);
+                    }
                     if (v[i] > 0) {                 // the bin's corner nodes within the unit's range
                         const int bx = b / nb, by = b - bx * nb;
                         const bool in0 = bx >= bx_lo && bx < bx_hi;
@@ -423,9 +431,15 @@ __device__ int gen_chunk(const TcArgs &a, TcSmem *s, GenState &st, int64_t pi0, 
                 s->pin[st.gp] = 1;
             }
             __syncthreads();
+            uint32_t *bmp = bmask + (size_t)st.gp * kMaxBins * 8;
             for (int i = start + tid; i < nrec; i += kThreads) {
                 const Rec r = recs[i];
                 sorted[atomicAdd(&s->u.g.hist[r.b0], 1)] = r;
+                // blocks of the record's two ticks (a zero-weight tap may mark a block: it only adds zeros)
+                const int rel = r.A - k0;
+                const int b0k = rel >> 4, b1k = (rel + 1) >> 4;
+                if (b0k >= 0 && b0k < 256) atomicOr(bmp + r.b0 * 8 + (b0k >> 5), 1u << (b0k & 31));
+                if (b1k != b0k && b1k >= 0 && b1k < 256) atomicOr(bmp + r.b0 * 8 + (b1k >> 5), 1u << (b1k & 31));
             }
             __syncthreads();
             for (int b = tid; b < nb2; b += kThreads) s->u.g.hist[b] = 0;
@@ -458,10 +472,10 @@ __device__ __forceinline__ int find_list(const int *off, int k)
 // Control flow is uniform across the builders (their named barriers); after
 // an abort they stop at the next node.
 template <int FMT>
-__device__ void build_batches(const TcArgs &a, TcSmem *s, const Rec *sorted, const int *offt,
+__device__ void build_batches(const TcArgs &a, TcSmem *s, const Rec *sorted, const int *offt, const uint32_t *bmask,
                               const unsigned short *nodes, int nn, uint32_t &q, unsigned long long &n_cells)
 {
-    constexpr int U = 4;                                // records in flight per thread
+    constexpr int U = 8;                                // records in flight per thread
     const int bt = threadIdx.x - 128, lane = bt & 31, cw = bt >> 5;
     const int nb = a.nb;
     for (int u = 0; u < nn; ++u) {
@@ -469,12 +483,19 @@ __device__ void build_batches(const TcArgs &a, TcSmem *s, const Rec *sorted, con
         const int n = nodes[u];
         const int nx = n / nb, ny = n - nx * nb;
         const int bx = nx - (cw & 1), by = ny - (cw >> 1);
-        int beg = 0, len = 0;
+        int beg = 0, len = 0, b = 0;
         if (s->pin[lane] && bx >= 0 && by >= 0) {
             const int *orow = offt + (size_t)lane * (kMaxBins + 1);
-            const int b = bx * nb + by;
+            b = bx * nb + by;
             beg = orow[b];
             len = orow[b + 1] - beg;
+        }
+        // arrival blocks present: OR of the 128 lists' masks (written when the records were sorted)
+        uint4 mk0 = make_uint4(0u, 0u, 0u, 0u), mk1 = mk0;
+        if (len > 0) {
+            const uint4 *mk = reinterpret_cast<const uint4 *>(bmask + ((size_t)lane * kMaxBins + b) * 8);
+            mk0 = mk[0];
+            mk1 = mk[1];
         }
         int x = len;
 #pragma unroll
@@ -485,6 +506,14 @@ __device__ void build_batches(const TcArgs &a, TcSmem *s, const Rec *sorted, con
         if (lane == 31) s->lst_wsum[cw] = x;
         if (bt < 8) s->blkmask[bt] = 0;
         builders_sync();
+        {
+            const uint32_t w8[8] = {mk0.x, mk0.y, mk0.z, mk0.w, mk1.x, mk1.y, mk1.z, mk1.w};
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const uint32_t o = __reduce_or_sync(0xffffffffu, w8[j]);
+                if (lane == 0 && o) atomicOr(&s->blkmask[j], o);
+            }
+        }
         int R = 0, pre = 0;
 #pragma unroll
         for (int w2 = 0; w2 < 4; ++w2) {
@@ -497,34 +526,6 @@ __device__ void build_batches(const TcArgs &a, TcSmem *s, const Rec *sorted, con
         // each builder takes a contiguous slice of the concatenated lists
         const int k_lo = (R * bt) >> 7, k_hi = (R * (bt + 1)) >> 7;
         const int L_lo = k_lo < k_hi ? find_list(s->lst_off, k_lo) : 0;
-        // pass 1: blocks present in this pass's window (arrival ticks are relative to the pass start)
-        int L = L_lo;
-        for (int k0 = k_lo; k0 < k_hi; k0 += U) {
-            int4 h[U];
-            float w[U];
-#pragma unroll
-            for (int j = 0; j < U; ++j) {
-                const int k = k0 + j;
-                h[j] = make_int4(0, 0, 0, 0);
-                w[j] = 0.f;
-                if (k < k_hi) {
-                    while (L < 127 && s->lst_off[L + 1] <= k) ++L;
-                    const Rec *r = sorted + s->lst_beg[L] + (k - s->lst_off[L]);
-                    h[j] = *reinterpret_cast<const int4 *>(r);
-                    w[j] = reinterpret_cast<const float *>(&r->w)[L >> 5];
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < U; ++j) {
-                const float f = __int_as_float(h[j].z);
-#pragma unroll
-                for (int tap = 0; tap < 2; ++tap) {
-                    const float val = tap ? f * w[j] : (1.f - f) * w[j];
-                    const int rb = (h[j].x + tap) >> 4;
-                    if (val != 0.f && rb >= 0 && rb < 256) atomicOr(&s->blkmask[rb >> 5], 1u << (rb & 31));
-                }
-            }
-        }
         builders_sync();
         uint32_t m[8];
         int pw[8], nblk = 0;
@@ -911,7 +912,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_induced_current_tc(TcArgs a)
                 if (tid < kGroup) s->pin[tid] = 0;
                 __syncthreads();
                 // records keep arrival ticks relative to the pass start
-                const int nrec = gen_chunk(a, s, st, pi0, npg, bx_lo, bx_hi, recs, sorted, offt);
+                uint32_t *bmask = a.bmask + (size_t)blockIdx.x * kGroup * kMaxBins * 8;
+                const int nrec = gen_chunk(a, s, st, pi0, npg, bx_lo, bx_hi, recs, sorted, offt, bmask, k0);
                 {
                     constexpr int kB = kMaxBins / kThreads;
                     int fl[kB], sf = 0;
@@ -938,7 +940,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_induced_current_tc(TcArgs a)
                 for (int u0 = 0; u0 < nn; u0 += kFlushNodes) {
                     const int cnt = min(kFlushNodes, nn - u0);
                     if (warp >= 4) {
-                        build_batches<FMT>(a, s, sorted, offt, s->nodes + u0, cnt, q, n_cells);
+                        build_batches<FMT>(a, s, sorted, offt, bmask, s->nodes + u0, cnt, q, n_cells);
                     } else if (lane == 0) {
                         issue_mmas(a, s, warp, s->nodes + u0, cnt, S, q, k0, n_mma, im_last);
                     }
@@ -1019,7 +1021,7 @@ int tc_grid()
 int rho0_of(int L) { return 16 * ((L + 126) / 16); }
 
 struct TcLayout {
-    size_t queue, table, recs, sorted, offt, pwork, nsub, pos, nslice, spos, units, order, slices, scan, total;
+    size_t queue, table, recs, sorted, offt, bmask, pwork, nsub, pos, nslice, spos, units, order, slices, scan, total;
 };
 
 TcLayout tc_layout(int grid, int64_t pix_cap, int T)
@@ -1048,6 +1050,7 @@ TcLayout tc_layout(int grid, int64_t pix_cap, int T)
     t.recs = take((size_t)grid * kRecCap * sizeof(Rec));
     t.sorted = take((size_t)grid * kRecCap * sizeof(Rec));
     t.offt = take((size_t)grid * kGroup * (kMaxBins + 1) * sizeof(int));
+    t.bmask = take((size_t)grid * kGroup * kMaxBins * 8 * sizeof(uint32_t));
     t.total = o;
     return t;
 }
@@ -1112,6 +1115,7 @@ cudaError_t launch_induced_current_tc(const sim_config &c, const sim_segments &s
     a.recs = reinterpret_cast<Rec *>(p + lay.recs);
     a.sorted = reinterpret_cast<Rec *>(p + lay.sorted);
     a.offt = reinterpret_cast<int *>(p + lay.offt);
+    a.bmask = reinterpret_cast<uint32_t *>(p + lay.bmask);
 
     cudaError_t e = cudaMemsetAsync(a.queue, 0, 32, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.status + 1, 0, 2 * sizeof(unsigned long long), st);

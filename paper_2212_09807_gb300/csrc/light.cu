@@ -150,9 +150,15 @@ __global__ void __launch_bounds__(256) k_light_photocurrent(sim_light_config lc,
                 const float *q = npe + (b0 + j) * nd;
                 for (int p = tid; p < nd * nt; p += blockDim.x) {
                     const int k = p / nt, u = p - k * nt;
-                    const float term = __ldg(q + k) * __ldg(f + p) * 65536.0f;
+                    const float term = __fmul_rn(__fmul_rn(__ldg(q + k), __ldg(f + p)), 65536.0f);
                     if (term != 0.f) {
-                        const long long fx = fabsf(term) < 2.0e9f ? (long long)__float2int_rn(term) : __float2ll_rn(term);
+                        long long fx;
+                        if (fabsf(term) < 4194304.0f) {
+                            // round to nearest even by adding 1.5 * 2^23 (FP32 add, no conversion unit)
+                            fx = (long long)(__float_as_int(__fadd_rn(term, 12582912.0f)) - 0x4B400000);
+                        } else {
+                            fx = __float2ll_rn(term);                  // terms of 64 p.e. and more: rare
+                        }
                         atomicAdd(&acc[k * W + off + u], (unsigned long long)fx);
                     }
                 }
@@ -284,15 +290,23 @@ __global__ void __launch_bounds__(256) k_light_fluct(sim_light_config lc, uint64
         if (lam <= lmax) {
             const u32x4 x = philox4x32_10(u32x4{(uint32_t)det, (uint32_t)t, 5u, 0u}, (uint32_t)key,
                                           (uint32_t)(key >> 32));
-            const double u = __dadd_rn(__dmul_rn((double)x.x, 0x1p-32), 0x1p-33);
-            double pk = exp(-lam), F = pk;
-            int k = 0;
-            while (u > F && k < 1000) {
-                ++k;
-                pk = __dmul_rn(pk, __ddiv_rn(lam, (double)k));
-                F = __dadd_rn(F, pk);
+            // k = 0 iff u <= e^-lambda, i.e. lambda <= -ln u: decided in FP32 when lambda is clear of
+            // -ln u by 1e-6 relative plus 3e-7 absolute (the FP32 uniform is within 2^-23 relative of
+            // the FP64 one, and the FP32 logarithm within a few ulp), else in FP64 below
+            const float nlu = -logf(u01f(x.x));
+            if ((float)lam < nlu * 0.999999f - 3e-7f) {
+                n = 0.f;
+            } else {
+                const double u = __dadd_rn(__dmul_rn((double)x.x, 0x1p-32), 0x1p-33);
+                double pk = exp(-lam), F = pk;
+                int k = 0;
+                while (u > F && k < 1000) {
+                    ++k;
+                    pk = __dmul_rn(pk, __ddiv_rn(lam, (double)k));
+                    F = __dadd_rn(F, pk);
+                }
+                n = (float)k;
             }
-            n = (float)k;
         } else {
             const float2 z = normals2(key, (uint32_t)det, (uint32_t)t, 6u);
             const float l = (float)lam;
@@ -477,9 +491,10 @@ cudaError_t launch_light_truth(const sim_light_config &lc, int64_t n, const int3
 
 size_t light_photocurrent_smem(const sim_light_config &lc, int *W)
 {
-    // window: as long as possible within 96 KB of accumulators, at least 2 nt
-    int w = (96 * 1024) / (8 * lc.n_det);
+    // window: 36 KB of accumulators (several CTAs per SM), at least 2 nt
+    int w = (36 * 1024) / (8 * lc.n_det);
     w = (w / 64) * 64;
+    if (w < 2 * lc.nt) w = ((2 * lc.nt + 63) / 64) * 64;
     if (W) *W = w;
     return ((sizeof(PcSmem) + 15) & ~(size_t)15) + (size_t)8 * lc.n_det * w;
 }
