@@ -270,9 +270,26 @@ def batched_vs_plain(cfg, lut, dev, n_events=32, lo=1.0e3, hi=1.0e4, reps=2):
             best_plain, lat = t_plain, per
         best_batch = t_batch if best_batch is None else min(best_batch, t_batch)
     assert batch_run.counts()[3] == 0
+    # the plain loop again, each event a replay of one CUDA graph of the whole step (sim.GraphRunner)
+    g = sim.GraphRunner(plain)
+    best_graph, glat = None, None
+    for _ in range(reps):
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(n_events + 1)]
+        marks[0].record()
+        for k, sg in enumerate(singles):
+            g.load(sg.cols, sg.n, sg.event_id)
+            g.replay()
+            marks[k + 1].record()
+        torch.cuda.synchronize()
+        t_graph = marks[0].elapsed_time(marks[-1])
+        if best_graph is None or t_graph < best_graph:
+            best_graph, glat = t_graph, [marks[k].elapsed_time(marks[k + 1]) for k in range(n_events)]
+    assert plain.counts()[3] == 0
     return {"events": n_events, "segments": total, "sizes": f"log-uniform [{lo:.0f}, {hi:.0f}] segments",
             "plain_segments_per_s": total / (best_plain / 1e3), "batched_segments_per_s": total / (best_batch / 1e3),
+            "graph_segments_per_s": total / (best_graph / 1e3),
             "plain_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "graph_latency_ms": {"p50": float(np.percentile(glat, 50)), "p99": float(np.percentile(glat, 99))},
             "batched_completion_ms": best_batch}
 
 

@@ -671,3 +671,66 @@ def sim_light_event(cfg: SimConfig, light: Light, seg: Segments, dr: Drifted, wa
     s, d = seg.struct(), dr.struct()
     _check(lib().sim_light_event(C.byref(cfg), C.byref(light.c), C.byref(s), C.byref(d), _ptr(wave), _ptr(ws),
                                  int(ws.numel() * ws.element_size()), _stream(stream)), "sim_light_event")
+
+
+class GraphRunner:
+    """One event step (sim_event) captured once in a CUDA graph and replayed.
+
+    The graph is recorded at a fixed segment capacity with the batch form of
+    sim_segments (one event slot whose id is read from device memory), so that
+    any event of up to ``max_segments`` segments and any event id replay the
+    same graph: the event's columns are copied into the graph's input buffers
+    and the rest is filled with inactive segments (zero length: no charge, no
+    pixels), which leaves the results of the real segments unchanged (their
+    random numbers are keyed by their own indices).  Replaying skips the ~30
+    kernel launches of a step, which matters for small events."""
+
+    FILL = dict(x0=-1.0e4, y0=-1.0e4, z0=-1.0e4, t0=0.0, x1=-1.0e4, y1=-1.0e4, z1=-1.0e4, t1=0.0, dE=0.0)
+
+    def __init__(self, runner: EventRunner, stream=None):
+        import torch
+        self.r = runner
+        dev = runner.device
+        n = runner.max_segments
+        self.cols = {k: torch.full((n,), self.FILL[k], dtype=torch.float32, device=dev) for k in Segments.KEYS}
+        self.fill = {k: v.clone() for k, v in self.cols.items()}          # padding source (device copies only)
+        self.offsets = torch.tensor([0, n], dtype=torch.int64, device=dev)
+        self.ids = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.ids_host = torch.zeros(64, dtype=torch.int64).pin_memory()   # ring of pinned id slots
+        self.k = 0
+        self.seg = Segments(self.cols, 0, self.offsets, self.ids)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
+        # warm up on the capture stream (lazy module loading, attributes), then capture
+        self.stream.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(self.stream):
+            runner.enqueue(self.seg, self.stream)
+        self.stream.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=self.stream, capture_error_mode="thread_local"):
+            runner.enqueue(self.seg, self.stream)
+        self.stream.synchronize()
+
+    def load(self, cols: dict, n: int, event_id: int):
+        """Enqueues the copies of an event (device or pinned host columns, n
+        segments) and of its id into the graph's inputs (copies only, no kernels)."""
+        if n > self.r.max_segments:
+            raise ValueError("event larger than the graph's capacity")
+        N = self.r.max_segments
+        for k in Segments.KEYS:
+            if n > 0:
+                self.cols[k][:n].copy_(cols[k][:n], non_blocking=True)
+            if n < N:
+                self.cols[k][n:].copy_(self.fill[k][n:], non_blocking=True)
+        slot = self.ids_host[self.k % 64: self.k % 64 + 1]
+        self.k += 1
+        slot.fill_(int(np.uint64(event_id & 0xFFFFFFFFFFFFFFFF).astype(np.int64)))
+        self.ids.copy_(slot, non_blocking=True)
+
+    def replay(self):
+        """Runs the captured step after the work already on the current stream (the
+        inputs' copies); the current stream then waits for it."""
+        import torch
+        self.stream.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(self.stream):
+            self.graph.replay()
+        torch.cuda.current_stream().wait_stream(self.stream)
