@@ -138,6 +138,7 @@ __global__ void k_plan_check(TruthArgs a)
 struct UnitSmem {
     unsigned long long acc[kHC][kSegU];
     int pre[kSegU + 1];
+    int ilo[kSegU];                            // first point of each segment that can reach the pixel
     int klo[kHC], khi[kHC];                    // hit j covers ticks (klo[j], khi[j]]
 };
 
@@ -215,7 +216,15 @@ __global__ void __launch_bounds__(kThreads) k_truth_units(TruthArgs a)
             int carry = 0;
             for (int i0 = 0; i0 < ns; i0 += 32) {
                 const int i = i0 + lane;
-                const int v = i < ns ? a.anch[a.segs[eb + i]].N * M : 0;
+                int v = 0;
+                if (i < ns) {                                   // the points that can reach this pixel
+                    const Anchor A = a.anch[a.segs[eb + i]];
+                    int i_lo, i_hi;
+                    point_range(A, M, (float)(ix - A.ix_ref) + 0.5f, (float)(iy - A.iy_ref) + 0.5f, fbpp, nb, clip,
+                                i_lo, i_hi);
+                    v = i_hi - i_lo;
+                    sm.ilo[i] = i_lo;
+                }
                 int x = v;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
@@ -262,7 +271,8 @@ __global__ void __launch_bounds__(kThreads) k_truth_units(TruthArgs a)
                     cx = (float)(ix - A.ix_ref) + 0.5f;
                     cy = (float)(iy - A.iy_ref) + 0.5f;
                 }
-                const PointPos pp = point_position(A, f - sm.pre[cur], M, key, (uint32_t)(sg - seg0), clip, a.dp);
+                const PointPos pp = point_position(A, sm.ilo[cur] + f - sm.pre[cur], M, key, (uint32_t)(sg - seg0),
+                                                   clip, a.dp);
                 Rec rc;
                 if (!point_record(A, pp, cx, cy, fbpp, nb, a.c.nearest_lut, rc)) continue;
                 const float4 *row = a.cum + (size_t)rc.b0 * a.ld;
