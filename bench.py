@@ -363,6 +363,22 @@ def time_form(cfg, seg, lut, dev, precision, steps, warmup, rank):
     return run, per, counts_now
 
 
+def step_rooflines(per, S, n_pairs, n_pix, T):
+    """The other steps of the path against their bounds (per-step CUDA-event means):
+    quench + drift 36 B in + 88 B out per segment (HBM); electronics 4 B of
+    current per pixel-tick read (HBM; its Philox noise makes it ALU-heavy); the
+    pixel map as pairs per second (latency of its sort, not bandwidth)."""
+    hbm = measured_peaks().get("hbm_gbs", 6800.0)
+    q_ms, m_ms, e_ms = (float(per[:, i].mean()) for i in (0, 1, 3))
+    q = 124.0 * S / (q_ms / 1e3) / 1e9
+    e = 4.0 * n_pix * T / (e_ms / 1e3) / 1e9
+    return {"quench_drift": {"bound": "hbm", "bytes_per_segment": 124, "achieved": q, "peak": hbm, "unit": "GB/s",
+                             "frac": q / hbm},
+            "electronics": {"bound": "hbm", "bytes_per_pixel_tick": 4, "achieved": e, "peak": hbm, "unit": "GB/s",
+                            "frac": e / hbm},
+            "pixel_map": {"pairs": n_pairs, "pairs_per_s": n_pairs / (m_ms / 1e3)}}
+
+
 def post_hit_steps(run, cfg, dev, reps=5):
     """Times the steps after the front end on the event held by `run` (its last
     sim_event): per-hit charge truth (5 entries per hit), hits -> 3-D points and
@@ -721,7 +737,8 @@ def run_ours(args):
             "step_breakdown_ms": {"quench_drift": float(per[:, 0].mean()), "pixel_map": float(per[:, 1].mean()),
                                   "induced_current": float(per[:, 2].mean()),
                                   "electronics": float(per[:, 3].mean())},
-            "roofline": roofline, "forms": forms, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,
+            "roofline": roofline, "step_rooflines": step_rooflines(per, S, n_pairs, n_pix, T),
+            "forms": forms, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,
             "serving": serving, "after_front_end": post, "light": light_res,
             "gpu_launches": KERNELS_PER_STEP[args.precision] * args.steps, "clocks": clocks,
         }))
