@@ -78,10 +78,32 @@ def workload(name):
 
 
 def dist():
+    """(world size, rank, local rank) from the launcher's environment (1, 0, 0 alone)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(x: float, pg=None, device="cpu") -> float:
+    """Largest value of x over the job's ranks (x itself without a process group)."""
+    if pg is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, slowest_s: float) -> float:
+    """Whole-job rate of replicas (weak scaling): the units all ranks processed
+    over the slowest rank's time."""
+    return world * units_per_rank / slowest_s
+
+
+def replica_event_id(rank: int) -> int:
+    """Event id of a rank's replica: the same synthetic event, its own random numbers."""
+    return rank
 
 
 class ClockSampler:
@@ -669,17 +691,14 @@ def run_ours(args):
     clk.start()
     time.sleep(0.15)
     run, per, (n_pairs, n_pix, n_hits, status) = time_form(cfg, seg, lut, dev, args.precision, args.steps,
-                                                           args.warmup, rank)
+                                                           args.warmup, replica_event_id(rank))
     clocks = clk.stop()
     step_ms = per.sum(axis=1)
     total_ms = float(step_ms.sum())
-    if pg:
-        t = torch.tensor([total_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * S * args.steps / (total_ms / 1e3)
-    a45_ms = float(per[:, 2:].sum())
-    pix_ticks = world * n_pix * T * args.steps / (a45_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, pg, dev)
+    value = job_rate(world, S * args.steps, total_ms / 1e3)
+    a45_ms = max_over_ranks(float(per[:, 2:].sum()), pg, dev)
+    pix_ticks = job_rate(world, n_pix * T * args.steps, a45_ms / 1e3)
     sm_mhz = clocks.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
     roofline, samples = form_roofline(run, cfg, args.precision, float(per[:, 2].mean()) / 1e3, props, sm_mhz, dev)
     forms[FORMS[args.precision][0]] = {"dtype": FORMS[args.precision][1], "ms_per_step": total_ms / args.steps,
@@ -690,21 +709,18 @@ def run_ours(args):
     io = sim.EventIO(run)
     host = {k: torch.as_tensor(np.ascontiguousarray(seg[k], dtype=np.float32)).pin_memory() for k in seg}
     for _ in range(max(1, args.warmup)):
-        io.simulate(host, S, rank)
+        io.simulate(host, S, replica_event_id(rank))
     torch.cuda.synchronize()
     if pg:
         pg.barrier()
     t0 = time.perf_counter()
     h2d = d2h = 0
     for _ in range(args.steps):
-        _, _, hb, db = io.simulate(host, S, rank)
+        _, _, hb, db = io.simulate(host, S, replica_event_id(rank))
         h2d, d2h = hb, db
     e2e_s = time.perf_counter() - t0
-    if pg:
-        t = torch.tensor([e2e_s], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * S * args.steps / e2e_s, "unit": "segments/s", "h2d_bytes_per_step": h2d,
+    e2e_s = max_over_ranks(e2e_s, pg, dev)
+    e2e = {"value": job_rate(world, S * args.steps, e2e_s), "unit": "segments/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
     post = post_hit_steps(run, cfg, dev) if not args.no_post else None
     del run, io
