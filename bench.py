@@ -271,7 +271,21 @@ def batched_vs_plain(cfg, lut, dev, n_events=32, lo=1.0e3, hi=1.0e4, reps=2):
             torch.cuda.empty_cache()
 
     plain = fitted(big, serve._caps(big), singles)
+    # autotuned scheduling shapes for the batched call, timed on a batch of the first 16 events (untimed here)
+    from paper_2212_09807_gb300 import tune
+    ns = min(16, n_events)
+    sample = sim.Segments.batch_from_numpy(evs[:ns], ids[:ns], dev)
+    s_tot = sum(sizes[:ns])
+    probe = fitted(s_tot, serve._caps(s_tot), [sample], max_events=ns)
+    s_caps = (probe.max_pairs, probe.max_pixels, probe.hits.capacity)
+    del probe
+    chosen, table = tune.autotune(cfg, lut, params.LUT["nt"], params.LUT["bins_per_pitch"], sample, s_caps,
+                                  device=dev)
+    tuned_cfg = dict(cfg, **chosen)
+    cfg_keep = cfg
+    cfg = tuned_cfg
     batch_run = fitted(total, serve._caps(total), [batch], max_events=n_events)
+    cfg = cfg_keep
     best_plain, best_batch, lat = None, None, None
     for _ in range(reps):
         marks = [torch.cuda.Event(enable_timing=True) for _ in range(n_events + 1)]
@@ -312,7 +326,9 @@ def batched_vs_plain(cfg, lut, dev, n_events=32, lo=1.0e3, hi=1.0e4, reps=2):
             "graph_segments_per_s": total / (best_graph / 1e3),
             "plain_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
             "graph_latency_ms": {"p50": float(np.percentile(glat, 50)), "p99": float(np.percentile(glat, 99))},
-            "batched_completion_ms": best_batch}
+            "batched_completion_ms": best_batch,
+            "tuning": {"sample": f"batch of the first {ns} events", "chosen": chosen,
+                       "candidates_ms": [[c, round(ms, 3)] for c, ms in table]}}
 
 
 

@@ -344,12 +344,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a)
     }
 }
 
-int grid_for(int64_t pix_cap)
+int grid_for(int64_t pix_cap, int ctas_per_sm = 3)
 {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int64_t g = (int64_t)sms * 3;
+    int64_t g = (int64_t)sms * ctas_per_sm;
     if (g > pix_cap) g = pix_cap;
     return (int)(g < 1 ? 1 : g);
 }
@@ -392,7 +392,7 @@ cudaError_t launch_induced_current(const sim_config &c, const sim_segments &s, c
     a.ev = events_of(s);
     a.g = geo_of(c);
     a.dp = drift_par_of(c);
-    const int grid = grid_for(pix_cap);
+    const int grid = grid_for(pix_cap, c.direct_ctas_per_sm > 0 ? c.direct_ctas_per_sm : 3);
     char *p = reinterpret_cast<char *>(scratch);
     a.recs = reinterpret_cast<Rec *>(p);
     a.sorted = reinterpret_cast<Rec *>(p + align256((size_t)grid * kRecCap * sizeof(Rec)));

@@ -60,8 +60,8 @@ constexpr int kSlots = 16;                  // blocks per operand batch
 constexpr int kMaxBins = 2048;              // nb * nb <= kMaxBins
 constexpr int kMaxRows = 2304;              // im2col rows: rho0 + 128 for nt <= 2048
 constexpr int kRowBytes = 32;               // 16 FP16 per im2col row
-constexpr int kRecCap = 1 << 18;            // records per chunk per CTA
-constexpr int kSubsPerSm = 2;               // work-balanced units per SM (target)
+constexpr int kRecCap = 1 << 18;            // records per chunk per CTA (buffer size; a chunk may be shorter)
+constexpr int kSubsPerSm = 2;               // work-balanced units per SM (target), unless tuned
 constexpr int kMaxSplit = 16;               // table-node ranges a pixel group may be cut into
 constexpr int kFlushNodes = 64;             // nodes per accumulation window (see flush_acc)
 constexpr float kFix = 4096.f;              // fixed-point scale of the charge accumulators (2^-12 e-)
@@ -128,6 +128,7 @@ struct TcArgs {
     const int64_t *n_units;
     float *slices;                          // partial currents [slice][kGroup][n_ticks]
     Rec *recs, *sorted;                     // [grid][kRecCap]
+    int rec_cap;                            // records per chunk (<= kRecCap)
     int *offt;                              // [grid][kGroup][kMaxBins + 1]
     uint32_t *bmask;                        // [grid][kGroup][kMaxBins][8]: arrival blocks of each (pixel, bin)
 };
@@ -377,7 +378,7 @@ __device__ int gen_chunk(const TcArgs &a, TcSmem *s, GenState &st, int64_t pi0, 
                 nq += c2;
             }
             __syncthreads();
-            if (nrec + nq > kRecCap) {      // chunk full: this batch is redone in the next chunk
+            if (nrec + nq > a.rec_cap) {    // chunk full: this batch is redone in the next chunk
                 full = true;
                 break;
             }
@@ -1024,7 +1025,7 @@ struct TcLayout {
     size_t queue, table, recs, sorted, offt, bmask, pwork, nsub, pos, nslice, spos, units, order, slices, scan, total;
 };
 
-TcLayout tc_layout(int grid, int64_t pix_cap, int T)
+TcLayout tc_layout(int grid, int64_t pix_cap, int T, int units_per_sm)
 {
     TcLayout t;
     size_t o = 0;
@@ -1043,7 +1044,7 @@ TcLayout tc_layout(int grid, int64_t pix_cap, int T)
     t.units = take(sizeof(Unit) * (size_t)ng * kMaxSplit);
     t.order = take(sizeof(int32_t) * (size_t)ng * kMaxSplit);
     // split units number fewer than 2 * target (wcap rounded up), at most 16 per group
-    const int64_t max_slices = std::min<int64_t>(2 * (int64_t)kSubsPerSm * grid, ng * kMaxSplit);
+    const int64_t max_slices = std::min<int64_t>(2 * (int64_t)units_per_sm * grid, ng * kMaxSplit);
     t.slices = take(sizeof(float) * (size_t)max_slices * kGroup * (size_t)T);
     t.scan = take(scan_scratch_bytes(ng));
     t.table = take((size_t)kMaxBins * kMaxRows * kRowBytes);
@@ -1057,9 +1058,9 @@ TcLayout tc_layout(int grid, int64_t pix_cap, int T)
 
 }  // namespace
 
-size_t current_tc_scratch_bytes(int64_t pix_cap, int T)
+size_t current_tc_scratch_bytes(int64_t pix_cap, int T, int units_per_sm)
 {
-    return tc_layout(tc_grid(), pix_cap > 0 ? pix_cap : 1, T).total;
+    return tc_layout(tc_grid(), pix_cap > 0 ? pix_cap : 1, T, units_per_sm > 0 ? units_per_sm : kSubsPerSm).total;
 }
 
 // Operand scales.  FP16: charge tiles in units of 4 e- (the fixed-point
@@ -1077,7 +1078,8 @@ cudaError_t launch_induced_current_tc(const sim_config &c, const sim_segments &s
     if (pix_cap <= 0) return cudaSuccess;
     const int fmt = c.precision == 1 ? 1 : 0;      // 1: BF16, 2: FP16
     const int grid = tc_grid();
-    const TcLayout lay = tc_layout(grid, pix_cap, c.n_ticks);
+    const int units_per_sm = c.tc_units_per_sm > 0 ? c.tc_units_per_sm : kSubsPerSm;
+    const TcLayout lay = tc_layout(grid, pix_cap, c.n_ticks, units_per_sm);
     char *p = reinterpret_cast<char *>(scratch);
     TcArgs a;
     a.c = c;
@@ -1116,6 +1118,7 @@ cudaError_t launch_induced_current_tc(const sim_config &c, const sim_segments &s
     a.sorted = reinterpret_cast<Rec *>(p + lay.sorted);
     a.offt = reinterpret_cast<int *>(p + lay.offt);
     a.bmask = reinterpret_cast<uint32_t *>(p + lay.bmask);
+    a.rec_cap = c.tc_record_chunk > 0 ? c.tc_record_chunk : kRecCap;
 
     cudaError_t e = cudaMemsetAsync(a.queue, 0, 32, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.status + 1, 0, 2 * sizeof(unsigned long long), st);
@@ -1131,7 +1134,7 @@ cudaError_t launch_induced_current_tc(const sim_config &c, const sim_segments &s
                                                                     pix_seg_ids, d.n_samples, c.mc_per_sample, pwork,
                                                                     wtotal);
     k_plan_split<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(counts, pix_cap, pix_begin, pix_end, pwork, wtotal,
-                                                               kSubsPerSm * grid, nsub, nslice, ng);
+                                                               units_per_sm * grid, nsub, nslice, ng);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_exclusive_scan(nsub, pos, ng, n_units, p + lay.scan, st);
     if (e == cudaSuccess) e = launch_exclusive_scan(nslice, spos, ng, n_slices, p + lay.scan, st);

@@ -54,6 +54,8 @@ class SimConfig(C.Structure):
         ("seed", C.c_uint64),
         ("precision", C.c_int32), ("fp64_charge", C.c_int32), ("disabled_pixels", C.c_void_p),
         ("per_point_drift", C.c_int32), ("nearest_lut", C.c_int32),
+        ("tc_units_per_sm", C.c_int32), ("tc_record_chunk", C.c_int32), ("direct_ctas_per_sm", C.c_int32),
+        ("tune_pad", C.c_int32),
     ]
 
 
@@ -182,7 +184,8 @@ def make_config(cfg: dict) -> SimConfig:
             m = cfg.get(name)
             c.disabled_pixels = None if m is None else int(m.data_ptr())
             continue
-        v = cfg.get(name, 0) if name in ("precision", "fp64_charge", "per_point_drift", "nearest_lut") else cfg[name]
+        v = cfg.get(name, 0) if name in ("precision", "fp64_charge", "per_point_drift", "nearest_lut", "tc_units_per_sm",
+                                         "tc_record_chunk", "direct_ctas_per_sm", "tune_pad") else cfg[name]
         setattr(c, name, int(v) & 0xFFFFFFFFFFFFFFFF if name == "seed" else (float(v) if ct is C.c_float else int(v)))
     return c
 

@@ -100,3 +100,15 @@ def test_post_hit_entry_points_check_arguments(L):
     o = (C.c_double * 3)(0, 0, 0)
     assert L.sim_track_dqdx(None, None, None, None, fake, 0, o, o, 0.0, 4, 1.0, fake, fake, None) == -1
     assert L.sim_response_cumulative(C.byref(r), None, None) == -1
+
+
+def test_tuning_fields_are_checked(L):
+    from paper_2212_09807_gb300 import sim
+    from synth import params
+    b = C.c_size_t()
+    for bad in (dict(tc_units_per_sm=17), dict(tc_record_chunk=5000), dict(tc_record_chunk=1 << 19),
+                dict(direct_ctas_per_sm=4)):
+        cfg = sim.make_config(params.module_config(**bad))
+        assert L.sim_workspace_size(C.byref(cfg), 0, 100, 1000, 100, C.byref(b)) == -1, bad
+    cfg = sim.make_config(params.module_config(precision=2, tc_units_per_sm=8, tc_record_chunk=1 << 16))
+    assert L.sim_workspace_size(C.byref(cfg), 0, 100, 1000, 100, C.byref(b)) == 0

@@ -70,7 +70,7 @@ def _check_truth(o, seg, d, m, h, tr, n_hits, event_id, max_pixels=None, rng=Non
     return n_cmp
 
 
-@pytest.mark.parametrize("case", ["plain", "periodic", "M2", "nearest"])
+@pytest.mark.parametrize("case", ["plain", "periodic", "M2", "nearest", "per_point"])
 def test_hit_truth_against_oracle(case):
     over = dict(thr_e=3000.0)
     if case == "periodic":
@@ -79,6 +79,8 @@ def test_hit_truth_against_oracle(case):
         over["mc_per_sample"] = 2
     elif case == "nearest":
         over["nearest_lut"] = 1
+    elif case == "per_point":
+        over["per_point_drift"] = 1
     cfg = params.small_config(**over)
     seg = events.scatter_event(cfg, 404, 40, max_len=0.6)
     lut_dev, lut64 = lut_pair(cfg)
@@ -171,3 +173,57 @@ def test_track_dqdx_on_the_tile_muon():
     d = np.linalg.norm(np.cross(P - a, u), axis=1)
     print(f"hits {nh}, within 1 cm of the line {ref_cnt.sum()}, median distance {np.median(d):.3f} cm")
     assert ref_cnt.sum() > 0.3 * nh
+
+
+def test_hit_truth_and_points_of_a_batch_equal_the_events_alone():
+    """Truth and 3-D points of a batch of events: each event's hits carry the
+    truth of the event alone (segment indices offset by the event's first
+    segment) and the same points (its own event time)."""
+    cfg = params.small_config(thr_e=3000.0)
+    lut_dev, _ = lut_pair(cfg)
+    evs = [events.scatter_event(cfg, 70 + i, n, max_len=0.6) for i, n in enumerate((30, 0, 45))]
+    ids = [4, 9, 13]
+    det_px = params.geometry(cfg)["n_pixels"]
+    dev = torch.device("cuda:0")
+
+    def truth_and_points(seg, max_events, t_ev):
+        n = max(seg.n, 1)
+        run = sim.EventRunner(cfg, lut_dev, params.LUT["nt"], params.LUT["bins_per_pitch"], n, 64 * n, 40 * n,
+                              200000, max_events=max_events)
+        run.enqueue(seg)
+        torch.cuda.synchronize()
+        c = run.counts()
+        assert c[3] == 0
+        v = run.view(seg.n)
+        A = sim._alias
+        tr = sim.Truth(run.hits.capacity, 4, device=dev)
+        sim.sim_hit_truth(run.cfg, seg, sim.Drifted.wrap(v.dr), run.resp, sim.sim_response_cumulative(run.resp),
+                          A(v.active_pixels, run.max_pixels, torch.int32, dev),
+                          A(v.pix_seg_off, run.max_pixels + 1, torch.int32, dev),
+                          A(v.pix_seg_ids, run.max_pairs, torch.int32, dev), run.ws[:6], run.max_pixels, run.hits, tr)
+        x, y, z = (torch.empty(run.hits.capacity, dtype=torch.float32, device=dev) for _ in range(3))
+        sim.sim_hit_points(run.cfg, run.hits, x, y, z, t_event=t_ev)
+        torch.cuda.synchronize()
+        nh = c[2]
+        h = run.hits.to_numpy(nh)
+        return (h, tr.segment[: nh * 4].cpu().numpy().reshape(nh, 4), tr.q[: nh * 4].cpu().numpy().reshape(nh, 4),
+                tr.q_signal[:nh].cpu().numpy(), np.stack([x[:nh].cpu().numpy(), y[:nh].cpu().numpy(),
+                                                          z[:nh].cpu().numpy()], 1))
+
+    t0s = [0.25, 0.0, 1.5]
+    batch = sim.Segments.batch_from_numpy(evs, ids)
+    hb, sb, qb, sigb, pb = truth_and_points(batch, len(evs), torch.tensor(t0s, dtype=torch.float32, device=dev))
+    first = np.concatenate([[0], np.cumsum([len(e["x0"]) for e in evs])])
+    n_cmp = 0
+    for e, (ev, i) in enumerate(zip(evs, ids)):
+        if len(ev["x0"]) == 0:
+            continue
+        ha, sa, qa, siga, pa = truth_and_points(sim.Segments.from_numpy(ev, i), 0,
+                                                torch.tensor([t0s[e]], dtype=torch.float32, device=dev))
+        m = hb["pixel"] // det_px == e
+        assert np.array_equal(hb["pixel"][m] - e * det_px, ha["pixel"])
+        assert np.array_equal(sb[m], np.where(sa >= 0, sa + first[e], -1))
+        assert np.array_equal(qb[m], qa) and np.array_equal(sigb[m], siga)
+        assert np.array_equal(pb[m], pa)
+        n_cmp += int(m.sum())
+    assert n_cmp > 5
