@@ -427,6 +427,18 @@ class Truth:
         """(cells needed, runs, units, status) of the last call, after the stream has run."""
         return [int(x) for x in self.ws[:4].cpu().tolist()]
 
+    def to_numpy(self, n_hits: int) -> dict:
+        """segment [n, k], q [n, k], q_signal [n], tick_first [n] and the fraction
+        of each listed segment in its hit's signal (q / q_signal; 0 where the
+        signal is 0) for the first n_hits hits."""
+        n = int(n_hits)
+        seg = self.segment[: n * self.k].cpu().numpy().reshape(n, self.k)
+        q = self.q[: n * self.k].cpu().numpy().reshape(n, self.k)
+        sig = self.q_signal[:n].cpu().numpy()
+        with np.errstate(divide="ignore", invalid="ignore"):
+            frac = np.where(sig[:, None] != 0, q / sig[:, None], 0.0)
+        return dict(segment=seg, q=q, q_signal=sig, tick_first=self.tick_first[:n].cpu().numpy(), fraction=frac)
+
     def struct(self) -> SimTruth:
         t = SimTruth()
         t.k, t.capacity = self.k, self.capacity

@@ -93,6 +93,11 @@ def test_hit_truth_against_oracle(case):
     d = o.quench_drift(seg)
     n = _check_truth(o, seg, d, m, h, tr, n_hits, 9)
     assert n == n_hits
+    t = tr.to_numpy(n_hits)                      # fractions of the listed segments in each hit's signal
+    ok = np.abs(t["q_signal"]) > 1.0
+    assert np.allclose(t["fraction"][ok] * t["q_signal"][ok, None], t["q"][ok], rtol=1e-6, atol=1e-6)
+    if case != "bipolar":
+        assert np.all(t["fraction"][ok].sum(axis=1) <= 1.0 + 1e-5)
 
 
 def test_hit_truth_module_event_sampled_and_signal_sums():
