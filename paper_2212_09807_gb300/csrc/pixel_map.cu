@@ -122,22 +122,71 @@ __global__ void __launch_bounds__(256) k_map_fill(MapArgs m, const int64_t *coun
 }
 
 // Insertion sort of each pixel's segment list (lists are short: O(10-100)).
+constexpr int kSortMax = 8192;                  // longest list sorted in shared memory
+
+// Each pixel's segment list in increasing order (the current is summed in this
+// order).  A CTA takes 256 pixels: lists of up to 32 entries are sorted by
+// their own thread (insertion sort), longer ones by the whole CTA, one after
+// the other, with a bitonic sort in shared memory (lists beyond kSortMax,
+// which the configurations here never reach, fall back to the thread's
+// insertion sort).  The sorted order is unique: the result is deterministic.
 __global__ void __launch_bounds__(256) k_map_sort(const int64_t *counts, const int32_t *pix_seg_off,
                                                   int32_t *pix_seg_ids)
 {
+    __shared__ int32_t buf[kSortMax];
+    __shared__ int long_list[256];
+    __shared__ int n_long;
     if (counts[3] != 0) return;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= counts[1]) return;
-    int32_t *v = pix_seg_ids + pix_seg_off[i];
-    const int n = pix_seg_off[i + 1] - pix_seg_off[i];
-    for (int a = 1; a < n; ++a) {
-        const int32_t x = v[a];
-        int b = a - 1;
-        while (b >= 0 && v[b] > x) {
-            v[b + 1] = v[b];
-            --b;
+    const int64_t np = counts[1];
+    const int tid = threadIdx.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < np; base += (int64_t)gridDim.x * blockDim.x) {
+        if (tid == 0) n_long = 0;
+        __syncthreads();
+        const int64_t i = base + tid;
+        if (i < np) {
+            int32_t *v = pix_seg_ids + pix_seg_off[i];
+            const int n = pix_seg_off[i + 1] - pix_seg_off[i];
+            if (n > 32 && n <= kSortMax) {
+                long_list[atomicAdd(&n_long, 1)] = tid;
+            } else {
+                for (int a = 1; a < n; ++a) {
+                    const int32_t x = v[a];
+                    int b = a - 1;
+                    while (b >= 0 && v[b] > x) {
+                        v[b + 1] = v[b];
+                        --b;
+                    }
+                    v[b + 1] = x;
+                }
+            }
         }
-        v[b + 1] = x;
+        __syncthreads();
+        for (int q = 0; q < n_long; ++q) {
+            const int64_t pi = base + long_list[q];
+            int32_t *v = pix_seg_ids + pix_seg_off[pi];
+            const int n = pix_seg_off[pi + 1] - pix_seg_off[pi];
+            int P = 64;
+            while (P < n) P <<= 1;
+            for (int j = tid; j < P; j += blockDim.x) buf[j] = j < n ? v[j] : INT_MAX;
+            __syncthreads();
+            for (int k = 2; k <= P; k <<= 1) {
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    for (int t = tid; t < P; t += blockDim.x) {
+                        const int u = t ^ j;
+                        if (u > t) {
+                            const int32_t x = buf[t], y = buf[u];
+                            if (((t & k) == 0) == (x > y)) {
+                                buf[t] = y;
+                                buf[u] = x;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            for (int j = tid; j < n; j += blockDim.x) v[j] = buf[j];
+            __syncthreads();
+        }
     }
 }
 
