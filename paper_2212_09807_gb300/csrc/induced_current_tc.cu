@@ -465,6 +465,53 @@ __device__ __forceinline__ int find_list(const int *off, int k)
     return lo;
 }
 
+// Loads the records k0 .. min(k0 + U, k_hi) - 1 of a builder's slice of the
+// node's concatenated lists (list cursor L2 advances); absent ones get weight 0.
+template <int U>
+__device__ __forceinline__ void load_recs(const TcSmem *s, const Rec *sorted, int k0, int k_hi, int &L2, int4 (&h)[U],
+                                          float (&w)[U], int (&px)[U])
+{
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+        const int k = k0 + j;
+        h[j] = make_int4(0, 0, 0, 0);
+        w[j] = 0.f;
+        px[j] = 0;
+        if (k < k_hi) {
+            while (L2 < 127 && s->lst_off[L2 + 1] <= k) ++L2;
+            const int L = L2;
+            const Rec *r = sorted + s->lst_beg[L] + (k - s->lst_off[L]);
+            h[j] = *reinterpret_cast<const int4 *>(r);
+            w[j] = reinterpret_cast<const float *>(&r->w)[L >> 5];
+            px[j] = L & 31;
+        }
+    }
+}
+
+// Adds the two ticks of each record whose arrival block falls in operand batch
+// kb into the fixed-point charge tiles (block rank from the node's block mask).
+template <int U>
+__device__ __forceinline__ void accum_recs(TcSmem *s, const int4 (&h)[U], const float (&w)[U], const int (&px)[U],
+                                           const uint32_t (&m)[8], const int (&pw)[8], int kb)
+{
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+        const float f = __int_as_float(h[j].z);
+#pragma unroll
+        for (int tap = 0; tap < 2; ++tap) {
+            const float val = tap ? f * w[j] : (1.f - f) * w[j];
+            const int rel = h[j].x + tap;
+            const int rb = rel >> 4;
+            if (val == 0.f || rb < 0 || rb >= 256) continue;
+            const int wd = rb >> 5, bit = rb & 31;
+            const int rank = pw[wd] + __popc(m[wd] & ((1u << bit) - 1u));
+            if ((rank >> 4) != kb) continue;
+            atomicAdd(&s->u.acc[((rank & (kSlots - 1)) * kBlk + (rel & (kBlk - 1))) * kGroup + px[j]],
+                      __float2int_rn(val * kFix));
+        }
+    }
+}
+
 // Builder threads (warps 4-7, bt = 0..127).  For each node the 128 record
 // lists (corner c = bt / 32 of pixel bt % 32: the pixel's records in bin
 // node - c) are concatenated and the builders share the records evenly; the
@@ -479,25 +526,38 @@ __device__ void build_batches(const TcArgs &a, TcSmem *s, const Rec *sorted, con
     constexpr int U = 8;                                // records in flight per thread
     const int bt = threadIdx.x - 128, lane = bt & 31, cw = bt >> 5;
     const int nb = a.nb;
+    // the charge tiles share shared memory with the generation's histogram: zero them once
+    // here; afterwards the conversion clears every cell it reads
+    for (int i = bt; i < kSlots * kBlk * kGroup / 4; i += 128)
+        reinterpret_cast<int4 *>(s->u.acc)[i] = make_int4(0, 0, 0, 0);
+    // a node's list bounds and block masks are loaded one node ahead (unconditionally: the
+    // indexes stay inside this CTA's offset and mask buffers; unused values are discarded)
+    auto fetch = [&](int n, int &b, int &beg, int &end, uint4 &mk0, uint4 &mk1) {
+        const int nx = n / nb, ny = n - nx * nb;
+        const int bx = nx - (cw & 1), by = ny - (cw >> 1);
+        b = (bx >= 0 && by >= 0) ? bx * nb + by : 0;
+        const int *orow = offt + (size_t)lane * (kMaxBins + 1);
+        beg = orow[b];
+        end = (bx >= 0 && by >= 0) ? orow[b + 1] : beg;
+        const uint4 *mk = reinterpret_cast<const uint4 *>(bmask + ((size_t)lane * kMaxBins + b) * 8);
+        mk0 = mk[0];
+        mk1 = mk[1];
+    };
+    int fb = 0, fbeg = 0, fend = 0;
+    uint4 fm0 = make_uint4(0u, 0u, 0u, 0u), fm1 = fm0;
+    if (nn > 0) fetch(nodes[0], fb, fbeg, fend, fm0, fm1);
+    const bool pin = s->pin[lane] != 0;
     for (int u = 0; u < nn; ++u) {
         if (builders_any_abort(s)) return;
         const int n = nodes[u];
-        const int nx = n / nb, ny = n - nx * nb;
-        const int bx = nx - (cw & 1), by = ny - (cw >> 1);
-        int beg = 0, len = 0, b = 0;
-        if (s->pin[lane] && bx >= 0 && by >= 0) {
-            const int *orow = offt + (size_t)lane * (kMaxBins + 1);
-            b = bx * nb + by;
-            beg = orow[b];
-            len = orow[b + 1] - beg;
-        }
+        const int beg = pin ? fbeg : 0, len = pin ? fend - fbeg : 0;
         // arrival blocks present: OR of the 128 lists' masks (written when the records were sorted)
         uint4 mk0 = make_uint4(0u, 0u, 0u, 0u), mk1 = mk0;
         if (len > 0) {
-            const uint4 *mk = reinterpret_cast<const uint4 *>(bmask + ((size_t)lane * kMaxBins + b) * 8);
-            mk0 = mk[0];
-            mk1 = mk[1];
+            mk0 = fm0;
+            mk1 = fm1;
         }
+        if (u + 1 < nn) fetch(nodes[u + 1], fb, fbeg, fend, fm0, fm1);
         int x = len;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -527,6 +587,13 @@ __device__ void build_batches(const TcArgs &a, TcSmem *s, const Rec *sorted, con
         // each builder takes a contiguous slice of the concatenated lists
         const int k_lo = (R * bt) >> 7, k_hi = (R * (bt + 1)) >> 7;
         const int L_lo = k_lo < k_hi ? find_list(s->lst_off, k_lo) : 0;
+        // the first U records of the slice stay in registers for all of the node's batches
+        // (most slices are that short); longer slices reload the rest in each batch
+        int4 hc[U];
+        float wc[U];
+        int pc[U];
+        int L2c = L_lo;
+        load_recs<U>(s, sorted, k_lo, k_hi, L2c, hc, wc, pc);
         builders_sync();
         uint32_t m[8];
         int pw[8], nblk = 0;
@@ -538,46 +605,15 @@ __device__ void build_batches(const TcArgs &a, TcSmem *s, const Rec *sorted, con
         }
         const int nbatch = nblk > 0 ? (nblk + kSlots - 1) / kSlots : 1;
         for (int kb = 0; kb < nbatch; ++kb) {
-            for (int i = bt; i < kSlots * kBlk * kGroup / 4; i += 128)
-                reinterpret_cast<int4 *>(s->u.acc)[i] = make_int4(0, 0, 0, 0);
-            builders_sync();
             // pass 2: fixed-point charge of the blocks of this batch
-            int L2 = L_lo;
-            for (int k0 = k_lo; k0 < k_hi; k0 += U) {
+            accum_recs<U>(s, hc, wc, pc, m, pw, kb);
+            int L2 = L2c;
+            for (int k0 = k_lo + U; k0 < k_hi; k0 += U) {
                 int4 h[U];
                 float w[U];
                 int px[U];
-#pragma unroll
-                for (int j = 0; j < U; ++j) {
-                    const int k = k0 + j;
-                    h[j] = make_int4(0, 0, 0, 0);
-                    w[j] = 0.f;
-                    px[j] = 0;
-                    if (k < k_hi) {
-                        while (L2 < 127 && s->lst_off[L2 + 1] <= k) ++L2;
-                        const int L = L2;
-                        const Rec *r = sorted + s->lst_beg[L] + (k - s->lst_off[L]);
-                        h[j] = *reinterpret_cast<const int4 *>(r);
-                        w[j] = reinterpret_cast<const float *>(&r->w)[L >> 5];
-                        px[j] = L & 31;
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < U; ++j) {
-                    const float f = __int_as_float(h[j].z);
-#pragma unroll
-                    for (int tap = 0; tap < 2; ++tap) {
-                        const float val = tap ? f * w[j] : (1.f - f) * w[j];
-                        const int rel = h[j].x + tap;
-                        const int rb = rel >> 4;
-                        if (val == 0.f || rb < 0 || rb >= 256) continue;
-                        const int wd = rb >> 5, bit = rb & 31;
-                        const int rank = pw[wd] + __popc(m[wd] & ((1u << bit) - 1u));
-                        if ((rank >> 4) != kb) continue;
-                        atomicAdd(&s->u.acc[((rank & (kSlots - 1)) * kBlk + (rel & (kBlk - 1))) * kGroup + px[j]],
-                                  __float2int_rn(val * kFix));
-                    }
-                }
+                load_recs<U>(s, sorted, k0, k_hi, L2, h, w, px);
+                accum_recs<U>(s, h, w, px, m, pw, kb);
             }
             builders_sync();
             const int st = q & 1;
@@ -587,14 +623,19 @@ __device__ void build_batches(const TcArgs &a, TcSmem *s, const Rec *sorted, con
             // one 16-byte core-matrix row (8 ticks of one pixel) per step
             for (int j = bt; j < count * kGroup * 2; j += 128) {
                 const int sl = j >> 6, p = j & (kGroup - 1), h = (j >> 5) & 1;
-                const int *ac = s->u.acc + (sl * kBlk + 8 * h) * kGroup + p;
+                int *ac = s->u.acc + (sl * kBlk + 8 * h) * kGroup + p;
+                int c8[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) n_cells += ac[e * kGroup] != 0;   // nonzero charge cells
+                for (int e = 0; e < 8; ++e) {
+                    c8[e] = ac[e * kGroup];
+                    ac[e * kGroup] = 0;                       // read and clear
+                    n_cells += c8[e] != 0;                    // nonzero charge cells
+                }
                 uint4 v;
-                v.x = pack2<FMT>((float)ac[0 * kGroup] * a.qscale, (float)ac[1 * kGroup] * a.qscale);
-                v.y = pack2<FMT>((float)ac[2 * kGroup] * a.qscale, (float)ac[3 * kGroup] * a.qscale);
-                v.z = pack2<FMT>((float)ac[4 * kGroup] * a.qscale, (float)ac[5 * kGroup] * a.qscale);
-                v.w = pack2<FMT>((float)ac[6 * kGroup] * a.qscale, (float)ac[7 * kGroup] * a.qscale);
+                v.x = pack2<FMT>((float)c8[0] * a.qscale, (float)c8[1] * a.qscale);
+                v.y = pack2<FMT>((float)c8[2] * a.qscale, (float)c8[3] * a.qscale);
+                v.z = pack2<FMT>((float)c8[4] * a.qscale, (float)c8[5] * a.qscale);
+                v.w = pack2<FMT>((float)c8[6] * a.qscale, (float)c8[7] * a.qscale);
                 *reinterpret_cast<uint4 *>(dst + sl * 1024 + core_off(p, 8 * h)) = v;
             }
             if (bt < count) {
