@@ -691,18 +691,20 @@ __device__ void issue_mmas(const TcArgs &a, TcSmem *s, int w, const unsigned sho
             const uint64_t ad0 = smem_desc(im0, 128, 256), bd0 = smem_desc(saddr(s->bst[st]), 128, 256);
             tc_fence_after();
             uint32_t issued = 0;
-            for (int t = w; t < kTiles; t += kIssuers) {
-                if (k0 + kTileM * t >= T) break;
-                const uint32_t d = tm + (uint32_t)(kGroup * t);
-                const int base = kTileM * t + a.rho0;          // A row of block 0; block b: base - 16 b
+            // slot-major: consecutive MMAs go to different accumulator tiles (a short N = 32 MMA
+            // into the tile the previous one wrote waits for it); each tile still takes its
+            // slots in order
 #pragma unroll
-                for (int i = 0; i < kSlots; ++i) {
-                    if (i < count) {
-                        const int arow = base - kBlk * (int)((b4[i >> 2] >> (8 * (i & 3))) & 0xffu);
-                        if (arow >= 0 && arow <= a.rho0) {        // otherwise the A tile is all zero
-                            mma_f16(d, ad0 + (uint64_t)(2 * arow), bd0 + (uint64_t)(64 * i), a.idesc);
-                            ++issued;
-                        }
+            for (int i = 0; i < kSlots; ++i) {
+                if (i >= count) break;
+                const int boff = a.rho0 - kBlk * (int)((b4[i >> 2] >> (8 * (i & 3))) & 0xffu);
+#pragma unroll
+                for (int t = w; t < kTiles; t += kIssuers) {
+                    const int arow = kTileM * t + boff;            // A row of this block in tile t
+                    if (k0 + kTileM * t < T && arow >= 0 && arow <= a.rho0) {   // else the A tile is all zero
+                        mma_f16(tm + (uint32_t)(kGroup * t), ad0 + (uint64_t)(2 * arow), bd0 + (uint64_t)(64 * i),
+                                a.idesc);
+                        ++issued;
                     }
                 }
             }
