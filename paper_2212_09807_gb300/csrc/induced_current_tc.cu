@@ -299,6 +299,78 @@ __device__ __forceinline__ uint32_t pack2(float a, float b)
 }
 
 // ------------------------------------------------- record generation ----
+// Point ranges of a segment, seen from the pixel whose centre is (cx, cy),
+// that can give a record inside a unit's table rows bx in [bx_lo, bx_hi):
+// a record's corners span rows bx and bx + 1 of the folded x offset
+// xi = |dx| bpp - 1/2 (nearest reads: bx = round(xi)), so its undiffused x
+// offset lies in |dx| in [D_lo, D_hi] = [(bx_lo - 1) / bpp, (bx_hi + 1/2) / bpp]
+// (D_lo = 0 below row 2), and its y offset within the table,
+// |dy| < (nb + 1/2) / bpp, each widened by the diffusion clip * sTp and by
+// 1e-3 pitch against rounding.  The x band is two slabs (dx > 0, dx < 0) or one
+// (D_lo = 0); each slab, intersected with the y slab, gives a range of u and
+// so of points mu (u = (mu + 1/2) / N), widened by one point each side.  Point
+// indices idx = mu M + nu in [r0, r1) and [r2, r3) (r1 <= r2, or the second
+// empty); every point outside them is rejected by point_record or by the
+// unit's row test, so generating only these changes no record.
+__device__ __forceinline__ void band_ranges(const Anchor &A, int M, float cx, float cy, float fbpp, int nb, float clip,
+                                            int bx_lo, int bx_hi, int &r0, int &r1, int &r2, int &r3)
+{
+    const float w = clip * A.sTp + 1e-3f;
+    const float Ry = ((float)nb + 0.5f) / fbpp + w;
+    const float Dhi = ((float)bx_hi + 0.5f) / fbpp + w;
+    const float Dlo = bx_lo >= 2 ? (float)(bx_lo - 1) / fbpp - w : 0.f;
+    // u-interval of o + u d in [lo, hi] within [0, 1]
+    auto slab = [](float o, float d, float lo, float hi, float &u0, float &u1) {
+        if (fabsf(d) < 1e-12f) {
+            if (o < lo || o > hi) u1 = -1.f;
+        } else {
+            const float ta = (lo - o) / d, tb = (hi - o) / d;
+            u0 = fmaxf(u0, fminf(ta, tb));
+            u1 = fminf(u1, fmaxf(ta, tb));
+        }
+    };
+    float y0 = 0.f, y1 = 1.f;
+    slab(A.fy0 - cy, A.dY, -Ry, Ry, y0, y1);
+    const float ox = A.fx0 - cx;
+    float a0 = y0, a1 = y1, b0 = y0, b1 = -1.f;
+    if (Dlo > 0.f) {
+        slab(ox, A.dX, Dlo, Dhi, a0, a1);
+        b1 = y1;
+        slab(ox, A.dX, -Dhi, -Dlo, b0, b1);
+    } else {
+        slab(ox, A.dX, -Dhi, Dhi, a0, a1);
+    }
+    const float N = (float)A.N;
+    auto to_idx = [&](float u0, float u1, int &i0, int &i1) {
+        i0 = i1 = 0;
+        if (!(u0 <= u1)) return;
+        const int mu0 = max(0, (int)floorf(u0 * N - 0.5f) - 1);
+        const int mu1 = min(A.N - 1, (int)ceilf(u1 * N - 0.5f) + 1);
+        if (mu1 >= mu0) {
+            i0 = mu0 * M;
+            i1 = (mu1 + 1) * M;
+        }
+    };
+    int p0, p1, q0, q1;
+    to_idx(a0, a1, p0, p1);
+    to_idx(b0, b1, q0, q1);
+    if (p1 <= p0) {                     // only the second (or none)
+        p0 = q0;
+        p1 = q1;
+        q0 = q1 = 0;
+    } else if (q1 > q0) {
+        if (q0 < p0) {                  // order the two
+            int t0 = p0, t1 = p1;
+            p0 = q0, p1 = q1, q0 = t0, q1 = t1;
+        }
+        if (q0 <= p1) {                 // overlapping or adjacent: merge
+            p1 = max(p1, q1);
+            q0 = q1 = 0;
+        }
+    }
+    r0 = p0, r1 = p1, r2 = q0, r3 = q1;
+}
+
 // Generation cursor of a group: pixel slot, CSR position, point index.
 struct GenState {
     int gp, e, base;
@@ -317,6 +389,7 @@ __device__ int gen_chunk(const TcArgs &a, TcSmem *s, GenState &st, int64_t pi0, 
     const int nb = a.nb, nb2 = nb * nb, M = a.c.mc_per_sample;
     const float clip = a.c.diff_clip_sigma, fbpp = (float)a.bpp;
     const int npx = a.g.npx_x * a.g.npx_y;
+    const bool split = bx_lo > 0 || bx_hi < nb;
     int nrec = 0;
     while (st.gp < npg) {
         const int64_t pi = pi0 + st.gp;
@@ -334,31 +407,32 @@ __device__ int gen_chunk(const TcArgs &a, TcSmem *s, GenState &st, int64_t pi0, 
         const int e1 = a.off[pi + 1];
         const int start = nrec;
         bool full = false;
+        int cur = -1, sg = 0, r0 = 0, r1 = 0, r2 = 0, r3 = 0, n1 = 0, ncand = 0;
+        Anchor A;
         while (st.e < e1) {
-            const int sg = a.segs[st.e];
-            const Anchor A = a.anch[sg];
-            const int total = A.N * M;
-            bool skip = st.base >= total;
-            if (!skip && (bx_lo > 0 || bx_hi < nb)) {
-                // table rows bx this segment's points can reach from this pixel: its x-offsets
-                // span [d0, d1] (pitch units) widened by the diffusion clip; one bin of margin
-                const float cx = (float)(ix - A.ix_ref) + 0.5f;
-                const float d0 = A.fx0 - cx, d1 = A.fx0 + A.dX - cx, w = clip * A.sTp;
-                const float dmin = (d0 * d1 <= 0.f) ? 0.f : fminf(fabsf(d0), fabsf(d1));
-                const float dmax = fmaxf(fabsf(d0), fabsf(d1));
-                const int rmin = (int)floorf(fmaxf((dmin - w) * fbpp - 0.5f, 0.f)) - 1;
-                const int rmax = (int)floorf(fmaxf((dmax + w) * fbpp - 0.5f, 0.f)) + 1;
-                skip = rmax + 1 < bx_lo || rmin >= bx_hi;   // records' corners span rows bx, bx + 1
+            if (st.e != cur) {
+                // the pair's candidate points: all of them, or for a unit of a split group the
+                // ranges that can reach its table rows
+                cur = st.e;
+                sg = a.segs[st.e];
+                A = a.anch[sg];
+                r0 = 0, r1 = A.N * M, r2 = 0, r3 = 0;
+                if (split)
+                    band_ranges(A, M, (float)(ix - A.ix_ref) + 0.5f, (float)(iy - A.iy_ref) + 0.5f, fbpp, nb, clip,
+                                bx_lo, bx_hi, r0, r1, r2, r3);
+                n1 = r1 - r0;
+                ncand = n1 + (r3 - r2);
             }
-            if (skip) {
+            if (st.base >= ncand) {
                 ++st.e;
                 st.base = 0;
                 continue;
             }
-            const int idx = st.base + tid;
+            const int b = st.base + tid;
             bool ok = false;
             Rec r;
-            if (idx < total) {
+            if (b < ncand) {
+                const int idx = b < n1 ? r0 + b : r2 + (b - n1);
                 const PointPos pp = point_position(A, idx, M, key, (uint32_t)(sg - seg0), clip, a.dp);
                 ok = point_record(A, pp, (float)(ix - A.ix_ref) + 0.5f, (float)(iy - A.iy_ref) + 0.5f, fbpp, nb,
                                   a.c.nearest_lut, r);
