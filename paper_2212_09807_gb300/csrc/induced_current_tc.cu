@@ -66,6 +66,7 @@ constexpr int kMaxSplit = 16;               // table-node ranges a pixel group m
 constexpr int kFlushNodes = 64;             // nodes per accumulation window (see flush_acc)
 constexpr float kFix = 4096.f;              // fixed-point scale of the charge accumulators (2^-12 e-)
 constexpr int kIssuers = 4;
+constexpr int kPairs = 128;                 // (pixel, segment) pairs loaded together by the generation
 constexpr uint32_t kTmemCols = 512;
 constexpr int kMaxSpin = 1 << 22;           // bounded mbarrier waits (x ~ 0.5 us each)
 
@@ -83,6 +84,10 @@ struct __align__(1024) TcSmem {
             unsigned char nflag[kMaxBins];
             int scan_tmp[kThreads / 32 + 1];
             int warp_n[kThreads / 32];
+            Anchor anc[kPairs];             // a batch of a pixel's segments: anchors,
+            int psg[kPairs];                // segment indexes,
+            int pr0[kPairs], pn1[kPairs], pr2[kPairs];   // candidate ranges
+            int poff[kPairs];               // and candidate offsets
         } g;
         int acc[kSlots * kBlk * kGroup];
     } u;
@@ -95,6 +100,9 @@ struct __align__(1024) TcSmem {
     int pin[kGroup];
     int n_nodes, group, abort;
 };
+
+static_assert(sizeof(TcSmem) + 1024 <= 232448, "shared memory of the tensor-core kernel above 227 KB");
+static_assert(sizeof(((TcSmem *)nullptr)->u.g) <= sizeof(((TcSmem *)nullptr)->u.acc), "generation area above the tiles");
 
 // A unit of work: the pixel group [first, first + count) of the active list,
 // restricted to the table nodes with bx in [nb r / k, nb (r + 1) / k).  Units
@@ -407,62 +415,78 @@ __device__ int gen_chunk(const TcArgs &a, TcSmem *s, GenState &st, int64_t pi0, 
         const int e1 = a.off[pi + 1];
         const int start = nrec;
         bool full = false;
-        int cur = -1, sg = 0, r0 = 0, r1 = 0, r2 = 0, r3 = 0, n1 = 0, ncand = 0;
-        Anchor A;
         while (st.e < e1) {
-            if (st.e != cur) {
-                // the pair's candidate points: all of them, or for a unit of a split group the
-                // ranges that can reach its table rows
-                cur = st.e;
-                sg = a.segs[st.e];
-                A = a.anch[sg];
-                r0 = 0, r1 = A.N * M, r2 = 0, r3 = 0;
+            // a batch of the pixel's segments, one thread each: anchor and candidate points
+            // (all of them, or for a unit of a split group the ranges that can reach its rows)
+            const int np = min(kPairs, e1 - st.e);
+            int cnt = 0;
+            if (tid < np) {
+                const int sg = a.segs[st.e + tid];
+                const Anchor A = a.anch[sg];
+                int r0 = 0, r1 = A.N * M, r2 = 0, r3 = 0;
                 if (split)
                     band_ranges(A, M, (float)(ix - A.ix_ref) + 0.5f, (float)(iy - A.iy_ref) + 0.5f, fbpp, nb, clip,
                                 bx_lo, bx_hi, r0, r1, r2, r3);
-                n1 = r1 - r0;
-                ncand = n1 + (r3 - r2);
+                s->u.g.anc[tid] = A;
+                s->u.g.psg[tid] = sg;
+                s->u.g.pr0[tid] = r0;
+                s->u.g.pn1[tid] = r1 - r0;
+                s->u.g.pr2[tid] = r2;
+                cnt = (r1 - r0) + (r3 - r2);
             }
-            if (st.base >= ncand) {
-                ++st.e;
-                st.base = 0;
-                continue;
-            }
-            const int b = st.base + tid;
-            bool ok = false;
-            Rec r;
-            if (b < ncand) {
-                const int idx = b < n1 ? r0 + b : r2 + (b - n1);
-                const PointPos pp = point_position(A, idx, M, key, (uint32_t)(sg - seg0), clip, a.dp);
-                ok = point_record(A, pp, (float)(ix - A.ix_ref) + 0.5f, (float)(iy - A.iy_ref) + 0.5f, fbpp, nb,
-                                  a.c.nearest_lut, r);
-                if (ok) {                       // corner nodes (bx, bx + 1) must reach the unit's range
-                    const int bx = r.b0 / nb;
-                    ok = bx < bx_hi && bx + 1 >= bx_lo;
-                }
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, ok);
-            if (lane == 0) s->u.g.warp_n[warp] = __popc(m);
+            int ncand;
+            const int off = block_scan(cnt, s, &ncand);
+            if (tid < np) s->u.g.poff[tid] = off;
             __syncthreads();
-            int wb = 0, nq = 0;
+            // the batch's candidates, kThreads at a time
+            while (st.base < ncand) {
+                const int c = st.base + tid;
+                bool ok = false;
+                Rec r;
+                if (c < ncand) {
+                    int q = 0;                  // the pair holding candidate c: last q with poff[q] <= c
 #pragma unroll
-            for (int w2 = 0; w2 < kThreads / 32; ++w2) {
-                const int c2 = s->u.g.warp_n[w2];
-                wb += (w2 < warp) ? c2 : 0;
-                nq += c2;
+                    for (int step = kPairs / 2; step > 0; step >>= 1)
+                        if (q + step < np && s->u.g.poff[q + step] <= c) q += step;
+                    const int loc = c - s->u.g.poff[q], n1 = s->u.g.pn1[q];
+                    const int idx = loc < n1 ? s->u.g.pr0[q] + loc : s->u.g.pr2[q] + (loc - n1);
+                    const Anchor A = s->u.g.anc[q];
+                    const PointPos pp =
+                        point_position(A, idx, M, key, (uint32_t)(s->u.g.psg[q] - seg0), clip, a.dp);
+                    ok = point_record(A, pp, (float)(ix - A.ix_ref) + 0.5f, (float)(iy - A.iy_ref) + 0.5f, fbpp,
+                                      nb, a.c.nearest_lut, r);
+                    if (ok) {                   // corner nodes (bx, bx + 1) must reach the unit's range
+                        const int bx = r.b0 / nb;
+                        ok = bx < bx_hi && bx + 1 >= bx_lo;
+                    }
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, ok);
+                if (lane == 0) s->u.g.warp_n[warp] = __popc(m);
+                __syncthreads();
+                int wb = 0, nq = 0;
+#pragma unroll
+                for (int w2 = 0; w2 < kThreads / 32; ++w2) {
+                    const int c2 = s->u.g.warp_n[w2];
+                    wb += (w2 < warp) ? c2 : 0;
+                    nq += c2;
+                }
+                __syncthreads();
+                if (nrec + nq > a.rec_cap) {    // chunk full: this step is redone in the next chunk
+                    full = true;
+                    break;
+                }
+                if (ok) {
+                    const int d = nrec + wb + __popc(m & ((1u << lane) - 1u));
+                    recs[d] = r;
+                    atomicAdd(&s->u.g.hist[r.b0], 1);
+                }
+                nrec += nq;
+                st.base += kThreads;
             }
-            __syncthreads();
-            if (nrec + nq > a.rec_cap) {    // chunk full: this batch is redone in the next chunk
-                full = true;
-                break;
-            }
-            if (ok) {
-                const int d = nrec + wb + __popc(m & ((1u << lane) - 1u));
-                recs[d] = r;
-                atomicAdd(&s->u.g.hist[r.b0], 1);
-            }
-            nrec += nq;
-            st.base += kThreads;
+            if (full) break;
+            st.e += np;
+            st.base = 0;
+            __syncthreads();                    // the batch's arrays are read: the next may overwrite them
         }
         __syncthreads();
         if (nrec > start) {
