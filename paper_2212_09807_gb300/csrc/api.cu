@@ -35,7 +35,7 @@ bool cfg_ok(const sim_config *c)
     if (c->per_point_drift != 0 && c->per_point_drift != 1) return false;
     if (c->nearest_lut != 0 && c->nearest_lut != 1) return false;
     if (c->tc_units_per_sm < 0 || c->tc_units_per_sm > 16) return false;
-    if (c->tc_record_chunk != 0 && (c->tc_record_chunk < 4096 || c->tc_record_chunk > (1 << 18) ||
+    if (c->tc_record_chunk != 0 && (c->tc_record_chunk < 4096 || c->tc_record_chunk > (1 << 20) ||
                                     (c->tc_record_chunk & (c->tc_record_chunk - 1)) != 0))
         return false;
     if (c->direct_ctas_per_sm < 0 || c->direct_ctas_per_sm > 3) return false;
@@ -81,7 +81,7 @@ bool hits_ok(const sim_hits *h)
 size_t current_scratch(const sim_config &c, int64_t pixels)
 {
     return c.precision == 0 ? current_scratch_bytes(pixels)
-                            : current_tc_scratch_bytes(pixels, c.n_ticks, c.tc_units_per_sm);
+                            : current_tc_scratch_bytes(pixels, c.n_ticks, c.tc_units_per_sm, c.tc_record_chunk);
 }
 
 cudaError_t launch_current(const sim_config &c, const sim_segments &s, const sim_drifted &d, const sim_response &r,

@@ -60,7 +60,7 @@ constexpr int kSlots = 16;                  // blocks per operand batch
 constexpr int kMaxBins = 2048;              // nb * nb <= kMaxBins
 constexpr int kMaxRows = 2304;              // im2col rows: rho0 + 128 for nt <= 2048
 constexpr int kRowBytes = 32;               // 16 FP16 per im2col row
-constexpr int kRecCap = 1 << 18;            // records per chunk per CTA (buffer size; a chunk may be shorter)
+constexpr int kRecDefault = 1 << 18;       // records per chunk per CTA unless configured (at most 2^20)
 constexpr int kSubsPerSm = 2;               // work-balanced units per SM (target), unless tuned
 constexpr int kMaxSplit = 16;               // table-node ranges a pixel group may be cut into
 constexpr int kFlushNodes = 64;             // nodes per accumulation window (see flush_acc)
@@ -135,8 +135,8 @@ struct TcArgs {
     const int32_t *order;                   // units by decreasing work
     const int64_t *n_units;
     float *slices;                          // partial currents [slice][kGroup][n_ticks]
-    Rec *recs, *sorted;                     // [grid][kRecCap]
-    int rec_cap;                            // records per chunk (<= kRecCap)
+    Rec *recs, *sorted;                     // [grid][rec_cap]
+    int rec_cap;                            // records per chunk per CTA
     int *offt;                              // [grid][kGroup][kMaxBins + 1]
     uint32_t *bmask;                        // [grid][kGroup][kMaxBins][8]: arrival blocks of each (pixel, bin)
 };
@@ -994,8 +994,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_induced_current_tc(TcArgs a)
     const bool go = a.counts[3] == 0 && a.counts[1] <= a.pix_cap;
     const int64_t nsub = go ? *a.n_units : 0;
     const int T = a.c.n_ticks, nb2 = a.nb * a.nb;
-    Rec *recs = a.recs + (size_t)blockIdx.x * kRecCap;
-    Rec *sorted = a.sorted + (size_t)blockIdx.x * kRecCap;
+    Rec *recs = a.recs + (size_t)blockIdx.x * a.rec_cap;
+    Rec *sorted = a.sorted + (size_t)blockIdx.x * a.rec_cap;
     int *offt = a.offt + (size_t)blockIdx.x * kGroup * (kMaxBins + 1);
 
     if (tid == 0) {
@@ -1166,7 +1166,7 @@ struct TcLayout {
     size_t queue, table, recs, sorted, offt, bmask, pwork, nsub, pos, nslice, spos, units, order, slices, scan, total;
 };
 
-TcLayout tc_layout(int grid, int64_t pix_cap, int T, int units_per_sm)
+TcLayout tc_layout(int grid, int64_t pix_cap, int T, int units_per_sm, int rec_chunk)
 {
     TcLayout t;
     size_t o = 0;
@@ -1189,8 +1189,8 @@ TcLayout tc_layout(int grid, int64_t pix_cap, int T, int units_per_sm)
     t.slices = take(sizeof(float) * (size_t)max_slices * kGroup * (size_t)T);
     t.scan = take(scan_scratch_bytes(ng));
     t.table = take((size_t)kMaxBins * kMaxRows * kRowBytes);
-    t.recs = take((size_t)grid * kRecCap * sizeof(Rec));
-    t.sorted = take((size_t)grid * kRecCap * sizeof(Rec));
+    t.recs = take((size_t)grid * rec_chunk * sizeof(Rec));
+    t.sorted = take((size_t)grid * rec_chunk * sizeof(Rec));
     t.offt = take((size_t)grid * kGroup * (kMaxBins + 1) * sizeof(int));
     t.bmask = take((size_t)grid * kGroup * kMaxBins * 8 * sizeof(uint32_t));
     t.total = o;
@@ -1199,9 +1199,11 @@ TcLayout tc_layout(int grid, int64_t pix_cap, int T, int units_per_sm)
 
 }  // namespace
 
-size_t current_tc_scratch_bytes(int64_t pix_cap, int T, int units_per_sm)
+size_t current_tc_scratch_bytes(int64_t pix_cap, int T, int units_per_sm, int rec_chunk)
 {
-    return tc_layout(tc_grid(), pix_cap > 0 ? pix_cap : 1, T, units_per_sm > 0 ? units_per_sm : kSubsPerSm).total;
+    return tc_layout(tc_grid(), pix_cap > 0 ? pix_cap : 1, T, units_per_sm > 0 ? units_per_sm : kSubsPerSm,
+                     rec_chunk > 0 ? rec_chunk : kRecDefault)
+        .total;
 }
 
 // Operand scales.  FP16: charge tiles in units of 4 e- (the fixed-point
@@ -1220,7 +1222,8 @@ cudaError_t launch_induced_current_tc(const sim_config &c, const sim_segments &s
     const int fmt = c.precision == 1 ? 1 : 0;      // 1: BF16, 2: FP16
     const int grid = tc_grid();
     const int units_per_sm = c.tc_units_per_sm > 0 ? c.tc_units_per_sm : kSubsPerSm;
-    const TcLayout lay = tc_layout(grid, pix_cap, c.n_ticks, units_per_sm);
+    const int rec_chunk = c.tc_record_chunk > 0 ? c.tc_record_chunk : kRecDefault;
+    const TcLayout lay = tc_layout(grid, pix_cap, c.n_ticks, units_per_sm, rec_chunk);
     char *p = reinterpret_cast<char *>(scratch);
     TcArgs a;
     a.c = c;
@@ -1259,7 +1262,7 @@ cudaError_t launch_induced_current_tc(const sim_config &c, const sim_segments &s
     a.sorted = reinterpret_cast<Rec *>(p + lay.sorted);
     a.offt = reinterpret_cast<int *>(p + lay.offt);
     a.bmask = reinterpret_cast<uint32_t *>(p + lay.bmask);
-    a.rec_cap = c.tc_record_chunk > 0 ? c.tc_record_chunk : kRecCap;
+    a.rec_cap = rec_chunk;
 
     cudaError_t e = cudaMemsetAsync(a.queue, 0, 32, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.status + 1, 0, 2 * sizeof(unsigned long long), st);

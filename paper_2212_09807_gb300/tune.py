@@ -21,7 +21,7 @@ import itertools
 from . import sim
 
 TC_UNITS = (1, 2, 4, 8)
-TC_CHUNKS = (1 << 16, 1 << 17, 1 << 18)
+TC_CHUNKS = (1 << 16, 1 << 17, 1 << 18, 1 << 19, 1 << 20)
 DIRECT_CTAS = (1, 2, 3)
 
 
@@ -38,8 +38,10 @@ def autotune(cfg: dict, lut, nt: int, bins_per_pitch: int, seg: sim.Segments, ca
     pixels, hits) capacities that fit the sample."""
     import torch
     cands = cands if cands is not None else candidates(int(cfg.get("precision", 0)))
-    # workspace for the largest scratch: the most units per SM
-    big = dict(cfg, **max(cands, key=lambda c: c.get("tc_units_per_sm", 0)))
+    # workspace for the largest scratch: the most units per SM and the longest record chunk
+    big = dict(cfg)
+    for k in ("tc_units_per_sm", "tc_record_chunk"):
+        big[k] = max(int(c.get(k, 0)) for c in cands)
     run = sim.EventRunner(big, lut, nt, bins_per_pitch, seg.n, *caps, device=device,
                           max_events=max(seg.n_events, 0))
     table = []

@@ -106,7 +106,7 @@ def test_tuning_fields_are_checked(L):
     from paper_2212_09807_gb300 import sim
     from synth import params
     b = C.c_size_t()
-    for bad in (dict(tc_units_per_sm=17), dict(tc_record_chunk=5000), dict(tc_record_chunk=1 << 19),
+    for bad in (dict(tc_units_per_sm=17), dict(tc_record_chunk=5000), dict(tc_record_chunk=1 << 21),
                 dict(direct_ctas_per_sm=4)):
         cfg = sim.make_config(params.module_config(**bad))
         assert L.sim_workspace_size(C.byref(cfg), 0, 100, 1000, 100, C.byref(b)) == -1, bad
