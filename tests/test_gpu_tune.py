@@ -43,7 +43,7 @@ def test_tensor_core_form_across_shapes():
     n = len(seg["x0"])
     ref, _ = _currents(cfg, lut_dev, seg, n)
     scale = np.abs(ref).max()
-    for u, r in ((1, 1 << 12), (8, 1 << 16), (16, 1 << 18)):
+    for u, r in ((1, 1 << 12), (8, 1 << 16), (16, 1 << 18), (2, 1 << 20)):
         cur, _ = _currents(dict(cfg, tc_units_per_sm=u, tc_record_chunk=r), lut_dev, seg, n)
         assert np.abs(cur - ref).max() <= 1e-6 * scale, (u, r)
 
