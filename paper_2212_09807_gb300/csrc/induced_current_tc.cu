@@ -96,6 +96,7 @@ struct __align__(1024) TcSmem {
     uint64_t full_im[2], empty_im[2], full_b[2], empty_b[2], done;
     uint32_t taddr;
     uint32_t blkmask[8];
+    unsigned char rank_of[256], blk_of[256];    // a node's present arrival blocks: block -> rank -> block
     int lst_beg[128], lst_off[128], lst_wsum[4];
     int pin[kGroup];
     int n_nodes, group, abort;
@@ -587,10 +588,10 @@ __device__ __forceinline__ void load_recs(const TcSmem *s, const Rec *sorted, in
 }
 
 // Adds the two ticks of each record whose arrival block falls in operand batch
-// kb into the fixed-point charge tiles (block rank from the node's block mask).
+// kb into the fixed-point charge tiles (block rank from the node's rank table).
 template <int U>
 __device__ __forceinline__ void accum_recs(TcSmem *s, const int4 (&h)[U], const float (&w)[U], const int (&px)[U],
-                                           const uint32_t (&m)[8], const int (&pw)[8], int kb)
+                                           int kb)
 {
 #pragma unroll
     for (int j = 0; j < U; ++j) {
@@ -601,8 +602,7 @@ __device__ __forceinline__ void accum_recs(TcSmem *s, const int4 (&h)[U], const 
             const int rel = h[j].x + tap;
             const int rb = rel >> 4;
             if (val == 0.f || rb < 0 || rb >= 256) continue;
-            const int wd = rb >> 5, bit = rb & 31;
-            const int rank = pw[wd] + __popc(m[wd] & ((1u << bit) - 1u));
+            const int rank = s->rank_of[rb];    // the tap's block is present: its records set it
             if ((rank >> 4) != kb) continue;
             atomicAdd(&s->u.acc[((rank & (kSlots - 1)) * kBlk + (rel & (kBlk - 1))) * kGroup + px[j]],
                       __float2int_rn(val * kFix));
@@ -692,26 +692,34 @@ __device__ void build_batches(const TcArgs &a, TcSmem *s, const Rec *sorted, con
         int pc[U];
         int L2c = L_lo;
         load_recs<U>(s, sorted, k_lo, k_hi, L2c, hc, wc, pc);
-        builders_sync();
-        uint32_t m[8];
-        int pw[8], nblk = 0;
+        // rank of each present arrival block (its order, hence its batch and slot) and the
+        // inverse, in shared memory: two blocks per builder
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            m[j] = s->blkmask[j];
-            pw[j] = nblk;
-            nblk += __popc(m[j]);
+        for (int i = 0; i < 2; ++i) {
+            const int b = bt + 128 * i, wd = b >> 5;
+            const uint32_t wm = s->blkmask[wd];
+            if ((wm >> (b & 31)) & 1u) {
+                int r = __popc(wm & ((1u << (b & 31)) - 1u));
+                for (int j = 0; j < wd; ++j) r += __popc(s->blkmask[j]);
+                s->rank_of[b] = (unsigned char)r;
+                s->blk_of[r] = (unsigned char)b;
+            }
         }
+        builders_sync();
+        int nblk = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) nblk += __popc(s->blkmask[j]);
         const int nbatch = nblk > 0 ? (nblk + kSlots - 1) / kSlots : 1;
         for (int kb = 0; kb < nbatch; ++kb) {
             // pass 2: fixed-point charge of the blocks of this batch
-            accum_recs<U>(s, hc, wc, pc, m, pw, kb);
+            accum_recs<U>(s, hc, wc, pc, kb);
             int L2 = L2c;
             for (int k0 = k_lo + U; k0 < k_hi; k0 += U) {
                 int4 h[U];
                 float w[U];
                 int px[U];
                 load_recs<U>(s, sorted, k0, k_hi, L2, h, w, px);
-                accum_recs<U>(s, h, w, px, m, pw, kb);
+                accum_recs<U>(s, h, w, px, kb);
             }
             builders_sync();
             const int st = q & 1;
@@ -736,15 +744,7 @@ __device__ void build_batches(const TcArgs &a, TcSmem *s, const Rec *sorted, con
                 v.w = pack2<FMT>((float)c8[6] * a.qscale, (float)c8[7] * a.qscale);
                 *reinterpret_cast<uint4 *>(dst + sl * 1024 + core_off(p, 8 * h)) = v;
             }
-            if (bt < count) {
-                // block of slot kb * kSlots + bt: its set bit
-                const int want = kb * kSlots + bt;
-                int j = 0;
-                while (j < 7 && pw[j + 1] <= want) ++j;
-                uint32_t xm = m[j];
-                for (int z = want - pw[j]; z > 0; --z) xm &= xm - 1u;
-                s->meta[st].blk[bt] = (unsigned char)(j * 32 + __ffs(xm) - 1);
-            }
+            if (bt < count) s->meta[st].blk[bt] = s->blk_of[kb * kSlots + bt];   // block of slot bt
             if (bt == 0) {
                 s->meta[st].node = n;
                 s->meta[st].count = count > 0 ? count : 0;
