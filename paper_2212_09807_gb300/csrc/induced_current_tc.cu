@@ -380,7 +380,9 @@ __device__ __forceinline__ void band_ranges(const Anchor &A, int M, float cx, fl
     r0 = p0, r1 = p1, r2 = q0, r3 = q1;
 }
 
-// Generation cursor of a group: pixel slot, CSR position, point index.
+// Generation cursor of a group: pixel slot gp, CSR position e of the first
+// segment of the current batch of the pixel's segments (-1: pixel not begun),
+// and the offset base of the next step in the batch's concatenated candidates.
 struct GenState {
     int gp, e, base;
 };
