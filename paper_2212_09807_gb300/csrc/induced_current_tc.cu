@@ -18,25 +18,29 @@
 // the im2col (Toeplitz) unfolding of the row: M = 128 ticks, N = 32 pixels,
 // K = 16 arrival ticks.
 //
-// Design: one CTA of 256 threads per SM (persistent, dynamic group queue).
-//  - A CTA owns a group of 32 active pixels and a pass of 2048 ticks; the
-//    accumulators D (16 tiles of 128 ticks x 32 pixels, FP32) stay in tensor
-//    memory (all 512 columns) for the whole pass.
+// Design: one CTA of 256 threads per SM (persistent, dynamic unit queue).
+//  - A unit is a group of 32 active pixels, or for a heavy group a range of
+//    its table-node rows (the units of a group write partial currents that a
+//    second kernel adds in unit order); a CTA takes a unit and a pass of 2048
+//    ticks; the accumulators D (16 tiles of 128 ticks x 32 pixels, FP32) live
+//    in tensor memory (all 512 columns) and are added into the FP32 currents
+//    every 64 nodes.
 //  - The im2col unfolding of every table row is built once per call in
 //    global memory (FP16/BF16, canonical no-swizzle K-major layout); for each
 //    node the CTA copies that row's unfolding (rho0 + 128 rows x 32 bytes)
 //    into shared memory with one bulk asynchronous copy, double-buffered.
-//  - Records of the group's pixels are generated into a per-CTA buffer and
-//    sorted per pixel by table bin (counting sort).  A node receives the
+//  - Records of the unit's pixels are generated into a per-CTA buffer (a
+//    pixel's segments 128 at a time, their candidate points walked together)
+//    and sorted per pixel by table bin (counting sort).  A node receives the
 //    records of four bins (its corners) of each pixel.
-//  - Builder warps 4-7 (warp = corner, lane = pixel) turn a node's records
-//    into charge tiles Q[16 blocks][16 ticks][32 pixels], accumulated with
-//    integer atomics in fixed point (order-independent, so the result is
-//    bitwise reproducible), then converted to FP16/BF16 operand tiles.
+//  - Builder warps 4-7 share a node's records evenly and turn them into
+//    charge tiles Q[16 blocks][16 ticks][32 pixels], accumulated with integer
+//    atomics in fixed point (order-independent, so the result is bitwise
+//    reproducible), then converted to FP16/BF16 operand tiles.
 //  - Issuer warps 0-3 (one thread each) own tick tiles t = w, w + 4, ... and
-//    issue the MMAs of each batch; tcgen05.commit on mbarriers returns the
-//    operand buffers.  At the end of a pass warps 0-3 read D back (tcgen05.ld,
-//    lane = tick) and store the currents.
+//    issue the MMAs of each batch slot by slot; tcgen05.commit on mbarriers
+//    returns the operand buffers.  Warps 0-3 read D back (tcgen05.ld,
+//    lane = tick) at each flush.
 // Every mbarrier wait is bounded; a wait that gives up sets
 // SIM_STATUS_TIMEOUT in the status word and the CTA drains and returns.
 #include <algorithm>
