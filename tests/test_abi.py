@@ -112,3 +112,23 @@ def test_tuning_fields_are_checked(L):
         assert L.sim_workspace_size(C.byref(cfg), 0, 100, 1000, 100, C.byref(b)) == -1, bad
     cfg = sim.make_config(params.module_config(precision=2, tc_units_per_sm=8, tc_record_chunk=1 << 16))
     assert L.sim_workspace_size(C.byref(cfg), 0, 100, 1000, 100, C.byref(b)) == 0
+
+
+def test_autotuner_candidates_are_valid_configurations(L):
+    """Every shape the autotuner may pick passes the ABI's checks, and the
+    tensor-core workspace grows with the record chunk (two buffers of 32-byte
+    records per CTA)."""
+    from paper_2212_09807_gb300 import sim, tune
+    from synth import params
+    b = C.c_size_t()
+    sizes = {}
+    for prec in (0, 1, 2):
+        for cand in tune.candidates(prec):
+            cfg = sim.make_config(params.module_config(precision=prec, **cand))
+            assert L.sim_workspace_size(C.byref(cfg), 0, 1000, 40000, 4000, C.byref(b)) == 0, (prec, cand)
+            if prec == 2 and cand["tc_units_per_sm"] == 1:
+                sizes[cand["tc_record_chunk"]] = b.value
+    chunks = sorted(sizes)
+    assert chunks[-1] == 1 << 20
+    for lo, hi in zip(chunks, chunks[1:]):
+        assert sizes[hi] - sizes[lo] >= 2 * 32 * (hi - lo)        # at least one CTA's two record buffers
