@@ -84,6 +84,29 @@ def test_quench_drift(model):
     assert (d["anode"] < 0).sum() >= 2   # degenerate segments present and inactive
 
 
+def test_recombination_closed_form_values_gpu():
+    """Q_R / Q_0 of the GPU's quench step at 2.1, 5, 10 and 20 MeV/cm against the
+    hand-evaluated closed forms of Eq. (birks) / Eq. (box) (tests/golden), to
+    1e-5.  R is recovered from the outputs as Q_a e^(t_drift/tau) W_ion / dE."""
+    import os
+    rows = []
+    for ln in open(os.path.join(os.path.dirname(__file__), "golden", "recombination_closed_form.txt")):
+        f = ln.split("#")[0].split()
+        if f:
+            rows.append((f[0], float(f[1]), float(f[2])))
+    for model, name in ((0, "birks"), (1, "box")):
+        cfg = params.small_config(recomb_model=model)
+        ref = [(d, r) for m, d, r in rows if m == name]
+        a = np.asarray([(5.0, 5.0, 3.0, 0.0, 5.5, 5.0, 3.0, 0.0, 0.5 * d) for d, _ in ref], dtype=np.float32)
+        seg = {k: np.ascontiguousarray(a[:, i]) for i, k in enumerate(events.COLS)}
+        lut_dev, _ = lut_pair(cfg)
+        g = Steps(cfg, seg, lut_dev).quench_drift().drifted_np()
+        assert np.all(g["anode"] >= 0)
+        R = (g["Qa"].astype(np.float64) * np.exp(g["t_drift"].astype(np.float64) / np.float64(np.float32(cfg["lifetime_us"])))
+             * np.float64(np.float32(cfg["w_ion_MeV"])) / seg["dE"].astype(np.float64))
+        np.testing.assert_allclose(R, [r for _, r in ref], rtol=1e-5, atol=0, err_msg=name)
+
+
 def test_pixel_map(small):
     st, o, seg, d = small["st"], small["o"], small["seg"], small["d"]
     m = st.maps_np()

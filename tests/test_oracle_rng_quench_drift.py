@@ -75,6 +75,35 @@ def test_mip_recombination_around_0p7(model):
     assert abs(o.recomb(2.1) - val) < tol
 
 
+def _recomb_gold():
+    rows = []
+    for ln in open(os.path.join(GOLD, "recombination_closed_form.txt")):
+        ln = ln.split("#")[0].split()
+        if ln:
+            rows.append((ln[0], float(ln[1]), float(ln[2])))
+    return rows
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_recombination_closed_form_values(model):
+    """R at 2.1, 5, 10 and 20 MeV/cm against the hand-evaluated closed forms of
+    Eq. (birks) / Eq. (box) with the paper's parameters (Sec. 3.1), to 1e-5:
+    a 1 % error in rho, k_b, beta or the field moves R by more than 1e-3."""
+    cfg = params.tile_config(recomb_model=model)
+    assert (cfg["efield_kV_cm"], cfg["lar_density_g_cm3"]) == (0.5, 1.38)    # the values the table assumes
+    o = oracle.Oracle(cfg, params.LUT)
+    name = ("birks", "box")[model]
+    rows = [(d, r) for m, d, r in _recomb_gold() if m == name]
+    assert len(rows) == 4
+    for dedx, R in rows:
+        assert abs(o.recomb(dedx) / R - 1.0) < 1e-5, (name, dedx, o.recomb(dedx), R)
+    # through the whole quench step: 0.5 cm segments at the anode carry Q_R = R dE / W_ion
+    seg = _seg([(5.0, 5.0, 0.1, 0.0, 5.5, 5.0, 0.1, 0.0, 0.5 * d) for d, _ in rows])
+    d = o.quench_drift(seg)
+    R_step = d["QR"] * o.c.w_ion / seg["dE"].astype(np.float64)
+    assert np.allclose(R_step, [R for _, R in rows], rtol=1e-5, atol=0)
+
+
 def test_birks_inverted_relation():
     # Eq. (birks) solved for k_b: (A_b / R - 1) / (dE/dx) = k_b / epsilon at every dE/dx
     cfg = params.tile_config(recomb_model=0)
