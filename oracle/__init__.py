@@ -23,12 +23,18 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle library with gcc (IEEE order kept: no FMA contraction)."""
+    """Compile the oracle library with gcc (IEEE order kept: no FMA contraction).
+
+    With OpenMP when the compiler has it (the many-pixel functions then share
+    their independent pixels among the host cores); without, they run on one
+    thread and give the same results."""
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
         tmp = LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
-                               "-ffp-contract=off", "-fno-fast-math", "-Wall",
-                               SRC, "-o", tmp, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-Wall"]
+        try:
+            subprocess.check_call(base + ["-fopenmp", SRC, "-o", tmp, "-lm"], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base + [SRC, "-o", tmp, "-lm"])
         os.replace(tmp, LIB)
     return LIB
 
@@ -91,6 +97,14 @@ def lib():
         L.ora_hit_point.argtypes = [P(_Cfg), C.c_int32, C.c_int32, C.c_double, f64p]
         L.ora_track_dqdx.argtypes = [C.c_int64, f64p, f64p, f64p, f64p, f64p, f64p, C.c_double, C.c_int32,
                                      C.c_double, f64p, i64p, f64p]
+        L.ora_threads.argtypes = [C.c_int]
+        L.ora_threads.restype = C.c_int
+        L.ora_map_event.argtypes = [P(_Cfg), C.c_int64] + [f32p] * 4 + [f64p, i32p, C.c_int64, i64p, i32p, f64p]
+        L.ora_map_event.restype = C.c_int64
+        L.ora_pixel_currents_many.argtypes = ([P(_Cfg), f64p] + [f32p] * 8 + [f64p] * 4
+                                              + [i32p, i32p, C.c_uint64, C.c_int64, i32p, i64p, i64p, f64p, C.c_int])
+        L.ora_electronics_many.argtypes = [P(_Cfg), C.c_uint64, C.c_int64, i32p, f64p, f64p, C.c_int64, i32p, i32p,
+                                           i32p, f64p, i64p, i32p, C.c_int]
         assert L.ora_cfg_size() == C.sizeof(_Cfg), "oracle config struct mismatch"
         _lib = L
     return _lib
@@ -233,6 +247,80 @@ class Oracle:
                 out.append(s)
                 mg.append(m)
         return np.array(out, dtype=np.int64), np.array(mg)
+
+    def map_event(self, seg: dict, dr: dict) -> dict:
+        """The map of every segment (ora_map_event) as both CSR directions:
+        ``pixels`` (mapped pixel ids, increasing), ``off``/``segs`` (each
+        pixel's segments, increasing) and ``margin`` (R_map - d of each entry)."""
+        cols = dr["_seg"]
+        n = len(cols[0])
+        sT = np.ascontiguousarray(dr["sigma_T"], dtype=np.float64)
+        an = np.ascontiguousarray(dr["anode"], dtype=np.int32)
+        cap = max(1024, 64 * n)
+        while True:
+            ps = np.zeros(cap, np.int64)
+            pp = np.zeros(cap, np.int32)
+            pm = np.zeros(cap)
+            m = self.L.ora_map_event(C.byref(self.c), n, _p(cols[0], C.c_float), _p(cols[1], C.c_float),
+                                     _p(cols[4], C.c_float), _p(cols[5], C.c_float), _p(sT, C.c_double),
+                                     _p(an, C.c_int32), cap, _p(ps, C.c_int64), _p(pp, C.c_int32),
+                                     _p(pm, C.c_double))
+            if m <= cap:
+                break
+            cap = int(m)
+        ps, pp, pm = ps[:m], pp[:m], pm[:m]
+        order = np.argsort(pp, kind="stable")            # segments stay increasing within a pixel
+        pix_sorted = pp[order]
+        pixels, start = np.unique(pix_sorted, return_index=True)
+        off = np.append(start, m).astype(np.int64)
+        return dict(pixels=pixels.astype(np.int32), off=off, segs=ps[order], margin=pm[order])
+
+    @staticmethod
+    def threads(n_threads: int = 0) -> int:
+        """Host threads the many-pixel functions use (0 = all cores)."""
+        return int(lib().ora_threads(int(n_threads)))
+
+    def pixel_currents(self, seg: dict, dr: dict, pixels, off, segs, event_id: int = 0, n_threads: int = 0):
+        """Currents [n, n_ticks] of many pixels: pixel pixels[i] with segment
+        list segs[off[i]:off[i+1]], each exactly as pixel_current computes it."""
+        assert self.lut is not None
+        cols = dr["_seg"]
+        pixels = np.ascontiguousarray(pixels, dtype=np.int32)
+        off = np.ascontiguousarray(off, dtype=np.int64)
+        segs = np.ascontiguousarray(segs, dtype=np.int64)
+        assert len(off) == len(pixels) + 1
+        I = np.zeros((len(pixels), int(self.c.n_ticks)))
+        self.L.ora_pixel_currents_many(C.byref(self.c), _p(self.lut, C.c_double),
+                                       *[_p(a, C.c_float) for a in cols[:8]],
+                                       _p(dr["Qa"], C.c_double), _p(dr["t_drift"], C.c_double),
+                                       _p(dr["sigma_T"], C.c_double), _p(dr["sigma_L"], C.c_double),
+                                       _p(dr["anode"], C.c_int32), _p(dr["n_samples"], C.c_int32), event_id,
+                                       len(pixels), _p(pixels, C.c_int32), _p(off, C.c_int64), _p(segs, C.c_int64),
+                                       _p(I, C.c_double), int(n_threads))
+        return I
+
+    def electronics_many(self, pixels, I, event_id: int = 0, band=None, n_threads: int = 0):
+        """Front end of many pixels (row i of I is pixel pixels[i]'s current),
+        each exactly as electronics computes it; band: one tie band per pixel
+        (or a scalar).  Returns a list of per-pixel dicts like electronics."""
+        pixels = np.ascontiguousarray(pixels, dtype=np.int32)
+        n = len(pixels)
+        I = np.ascontiguousarray(I, dtype=np.float64)
+        assert I.shape == (n, int(self.c.n_ticks))
+        bnd = np.ascontiguousarray(np.broadcast_to(np.asarray(0.0 if band is None else band, np.float64), (n,)))
+        cap = int(self.c.n_ticks)
+        tc = np.zeros((n, cap), np.int32)
+        ta = np.zeros((n, cap), np.int32)
+        ad = np.zeros((n, cap), np.int32)
+        qv = np.zeros((n, cap))
+        nh = np.zeros(n, np.int64)
+        tie = np.zeros(n, np.int32)
+        self.L.ora_electronics_many(C.byref(self.c), event_id, n, _p(pixels, C.c_int32), _p(I, C.c_double),
+                                    _p(bnd, C.c_double), cap, _p(tc, C.c_int32), _p(ta, C.c_int32),
+                                    _p(ad, C.c_int32), _p(qv, C.c_double), _p(nh, C.c_int64), _p(tie, C.c_int32),
+                                    int(n_threads))
+        return [dict(t_cross=tc[i, :nh[i]].copy(), t_adc=ta[i, :nh[i]].copy(), adc=ad[i, :nh[i]].copy(),
+                     q=qv[i, :nh[i]].copy(), tie_tick=int(tie[i])) for i in range(n)]
 
     # -- step 4 ------------------------------------------------------------
     def pixel_current(self, seg: dict, dr: dict, pixel: int, segs, event_id: int = 0,

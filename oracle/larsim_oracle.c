@@ -20,6 +20,13 @@
  *                       Sec. 3.3.1 interpolated trilinearly
  *   ora_electronics     Sec. 3.4 (CSA integration, discriminator with noise,
  *                       hold, ADC, reset)
+ *   ora_map_event, ora_pixel_currents_many, ora_electronics_many
+ *                       the same three steps for a whole event: every
+ *                       segment's map, and the current and front end of many
+ *                       pixels, each pixel exactly as the single-pixel
+ *                       functions compute it (the pixels are independent and
+ *                       are shared among the host cores with OpenMP when the
+ *                       library is built with it)
  *   ora_hit_intervals   Sec. 3.4: the ticks whose current a hit digitises
  *                       (per-hit charge truth: the per-segment sums over these
  *                       intervals are formed from ora_pixel_current of each
@@ -48,6 +55,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORA_PI 3.14159265358979323846
 
@@ -600,6 +610,94 @@ int64_t ora_electronics(const ora_cfg *c, uint64_t event_id, int32_t pixel, cons
     }
     if (tie_tick) *tie_tick = tie;
     return nh;
+}
+
+/* ------------------------------------------------------- whole events -- */
+
+/* Host threads the many-pixel functions use for a request of n_threads
+ * (0 = all available); 1 when the library was built without OpenMP. */
+int ora_threads(int n_threads)
+{
+#ifdef _OPENMP
+    return n_threads > 0 ? n_threads : omp_get_max_threads();
+#else
+    (void)n_threads;
+    return 1;
+#endif
+}
+
+/* Map of every segment of an event (Sec. 3.3.2): the pairs of
+ * ora_map_segment_box, segment by segment in increasing segment order, pixel
+ * ids increasing within a segment.  Writes up to cap pairs (segment index,
+ * pixel id, margin R_map - d) and returns the number of pairs (which may
+ * exceed cap). */
+int64_t ora_map_event(const ora_cfg *c, int64_t n, const float *x0, const float *y0, const float *x1,
+                      const float *y1, const double *sigma_T, const int32_t *anode, int64_t cap,
+                      int64_t *pair_seg, int32_t *pair_pix, double *pair_margin)
+{
+    int64_t bcap = 4096;
+    int32_t *ids = (int32_t *)malloc(sizeof(int32_t) * (size_t)bcap);
+    double *mg = (double *)malloc(sizeof(double) * (size_t)bcap);
+    int64_t total = 0;
+    for (int64_t s = 0; s < n; ++s) {
+        if (anode[s] < 0) continue;
+        int64_t m = ora_map_segment_box(c, x0[s], y0[s], x1[s], y1[s], sigma_T[s], anode[s], ids, mg, bcap);
+        if (m > bcap) {
+            bcap = m;
+            ids = (int32_t *)realloc(ids, sizeof(int32_t) * (size_t)bcap);
+            mg = (double *)realloc(mg, sizeof(double) * (size_t)bcap);
+            m = ora_map_segment_box(c, x0[s], y0[s], x1[s], y1[s], sigma_T[s], anode[s], ids, mg, bcap);
+        }
+        for (int64_t j = 0; j < m; ++j, ++total) {
+            if (total < cap) {
+                pair_seg[total] = s;
+                pair_pix[total] = ids[j];
+                pair_margin[total] = mg[j];
+            }
+        }
+    }
+    free(ids);
+    free(mg);
+    return total;
+}
+
+/* ora_pixel_current of n_pix pixels: pixel pixels[i] with the segment list
+ * segs[off[i] .. off[i+1]) writes row i of I [n_pix][n_ticks]. */
+void ora_pixel_currents_many(const ora_cfg *c, const double *lut,
+                             const float *x0, const float *y0, const float *z0, const float *t0,
+                             const float *x1, const float *y1, const float *z1, const float *t1,
+                             const double *Qa, const double *t_drift, const double *sigma_T,
+                             const double *sigma_L, const int32_t *anode, const int32_t *n_samples,
+                             uint64_t event_id, int64_t n_pix, const int32_t *pixels, const int64_t *off,
+                             const int64_t *segs, double *I, int n_threads)
+{
+    (void)n_threads;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(ora_threads(n_threads))
+#endif
+    for (int64_t i = 0; i < n_pix; ++i)
+        ora_pixel_current(c, lut, x0, y0, z0, t0, x1, y1, z1, t1, Qa, t_drift, sigma_T, sigma_L, anode,
+                          n_samples, event_id, pixels[i], segs + off[i], off[i + 1] - off[i],
+                          I + (size_t)i * (size_t)c->n_ticks, 0.0, NULL);
+}
+
+/* ora_electronics of n_pix pixels: pixel pixels[i] with the current row i of
+ * I and tie band band[i] (NULL: 0) writes up to cap hits to entries
+ * [i cap, (i+1) cap) of the hit arrays, its hit count to n_hits[i] and its
+ * first tied tick to tie_tick[i]. */
+void ora_electronics_many(const ora_cfg *c, uint64_t event_id, int64_t n_pix, const int32_t *pixels,
+                          const double *I, const double *band, int64_t cap, int32_t *t_cross, int32_t *t_adc,
+                          int32_t *adc, double *qv, int64_t *n_hits, int32_t *tie_tick, int n_threads)
+{
+    (void)n_threads;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4) num_threads(ora_threads(n_threads))
+#endif
+    for (int64_t i = 0; i < n_pix; ++i) {
+        const size_t o = (size_t)i * (size_t)cap;
+        n_hits[i] = ora_electronics(c, event_id, pixels[i], I + (size_t)i * (size_t)c->n_ticks, cap, t_cross + o,
+                                    t_adc + o, adc + o, qv + o, band ? band[i] : 0.0, tie_tick + i);
+    }
 }
 
 /* ------------------------------------------------- per-hit charge truth -- */

@@ -428,3 +428,38 @@ def test_nearest_lookup_conserves_charge():
     pix, _, _, _ = o.pixel_map(seg, d)
     total = sum(o.pixel_current(seg, d, p, s).sum() for p, s in pix.items())
     assert abs(total / d["Qa"].sum() - 1.0) < 1e-12
+
+
+# ------------------------------------------------------------- whole events --
+
+def test_whole_event_functions_equal_the_single_pixel_ones():
+    """ora_map_event is ora_map_segment_box of every segment; the many-pixel
+    current and front end are pixel_current and electronics of each pixel
+    alone, bit for bit, whatever the number of threads."""
+    from synth import events
+    cfg = params.small_config()
+    lut64 = response.lut_for(cfg, params.LUT)
+    o = oracle.Oracle(cfg, params.LUT, lut64)
+    seg = events.scatter_event(cfg, 21, 40, max_len=0.6)
+    d = o.quench_drift(seg)
+    m = o.map_event(seg, d)
+    pix, _, _, _ = o.pixel_map(seg, d)
+    assert m["pixels"].tolist() == sorted(pix)
+    for i, p in enumerate(m["pixels"].tolist()):
+        assert m["segs"][m["off"][i]:m["off"][i + 1]].tolist() == pix[p]
+    assert np.all(m["margin"] >= 0)
+    pick = np.arange(0, len(m["pixels"]), 7)
+    sub_off = np.concatenate([[0], np.cumsum(m["off"][pick + 1] - m["off"][pick])])
+    sub_segs = np.concatenate([m["segs"][m["off"][i]:m["off"][i + 1]] for i in pick])
+    for threads in (1, 0):
+        I = o.pixel_currents(seg, d, m["pixels"][pick], sub_off, sub_segs, event_id=3, n_threads=threads)
+        hits = o.electronics_many(m["pixels"][pick], I, event_id=3, band=0.5, n_threads=threads)
+        for j, i in enumerate(pick):
+            p = int(m["pixels"][i])
+            ref = o.pixel_current(seg, d, p, pix[p], event_id=3)
+            assert np.array_equal(I[j], ref)
+            e = o.electronics(p, ref, event_id=3, band=0.5)
+            for k in ("t_cross", "t_adc", "adc", "q"):
+                assert np.array_equal(hits[j][k], e[k]), k
+            assert hits[j]["tie_tick"] == e["tie_tick"]
+    assert sum(len(h["t_cross"]) for h in hits) > 0
