@@ -106,7 +106,14 @@ typedef struct sim_config {
      * default 262144; the workspace holds two record buffers of 32 bytes per
      * record and CTA); FP32 direct form: resident CTAs per SM (1..3, default 3).
      * paper_2212_09807_gb300/tune.py picks them by timing a sample. */
-    int32_t tc_units_per_sm, tc_record_chunk, direct_ctas_per_sm, tune_pad;
+    int32_t tc_units_per_sm, tc_record_chunk, direct_ctas_per_sm;
+    /* polls of a bounded device-side wait of the tensor-core forms before it
+     * gives up (0 = default 2^22, about two seconds; 1 .. 2^30).  A wait that
+     * gives up sets SIM_STATUS_TIMEOUT and the kernel winds down: its results
+     * are then invalid, and it still waits (with the default bound) for the
+     * MMAs and copies it has issued before it returns.  Lowering it makes the
+     * waits of a normal call give up: this is how the timeout path is tested. */
+    int32_t wait_spin_limit;
 } sim_config;
 
 /* Energy-deposit segments S_i = (r_s, r_e, E) (Sec. 2), as structure-of-arrays
@@ -295,7 +302,10 @@ int sim_event(const sim_config *cfg, const sim_segments *seg, const sim_response
  *    call, cudaGetSymbolAddress); make that first call before any stream
  *    capture.
  *  - All calls share the array: calls whose work overlaps on the GPU race and
- *    must be ordered by the caller (one stream, or events between streams). */
+ *    must be ordered by the caller (one stream, or events between streams).
+ *  - The looked-up address is cached per device for the life of the process;
+ *    it is invalid after cudaDeviceReset on that device, so a process that
+ *    resets a device must not call this entry point on it afterwards. */
 #define SIM_NOALLOC_SCRATCH_BYTES (16u << 20)
 int sim_pixel_map_noalloc(const sim_config *cfg, const sim_segments *seg, const sim_drifted *dr,
                           const sim_response *resp, int32_t *seg_pix_off, int32_t *seg_pix_ids,

@@ -39,6 +39,7 @@ bool cfg_ok(const sim_config *c)
                                     (c->tc_record_chunk & (c->tc_record_chunk - 1)) != 0))
         return false;
     if (c->direct_ctas_per_sm < 0 || c->direct_ctas_per_sm > 3) return false;
+    if (c->wait_spin_limit < 0 || c->wait_spin_limit > (1 << 30)) return false;
     return true;
 }
 
@@ -160,6 +161,7 @@ bool abi_config_ok(const sim_config *c) { return cfg_ok(c); }
 bool abi_segments_ok(const sim_segments *s) { return seg_ok(s); }
 bool abi_events_ok(const sim_config *c, const sim_segments *s) { return events_ok(c, s); }
 bool abi_drifted_ok(const sim_drifted *d) { return drifted_ok(d); }
+bool abi_response_ok(const sim_response *r, bool need_table) { return resp_ok(r, need_table); }
 int abi_cuda_fail(cudaError_t e) { return cuda_fail(e); }
 }  // namespace larsim
 

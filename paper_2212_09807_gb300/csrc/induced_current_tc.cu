@@ -72,7 +72,7 @@ constexpr float kFix = 4096.f;              // fixed-point scale of the charge a
 constexpr int kIssuers = 4;
 constexpr int kPairs = 128;                 // (pixel, segment) pairs loaded together by the generation
 constexpr uint32_t kTmemCols = 512;
-constexpr int kMaxSpin = 1 << 22;           // bounded mbarrier waits (x ~ 0.5 us each)
+constexpr int kMaxSpin = 1 << 22;           // bounded mbarrier waits (x ~ 0.5 us each), unless configured
 
 struct __align__(16) BatchMeta {
     int node, count, last, pad;
@@ -103,7 +103,7 @@ struct __align__(1024) TcSmem {
     unsigned char rank_of[256], blk_of[256];    // a node's present arrival blocks: block -> rank -> block
     int lst_beg[128], lst_off[128], lst_wsum[4];
     int pin[kGroup];
-    int n_nodes, group, abort;
+    int n_nodes, group, abort, spin;
 };
 
 static_assert(sizeof(TcSmem) + 1024 <= 232448, "shared memory of the tensor-core kernel above 227 KB");
@@ -195,12 +195,18 @@ __device__ __forceinline__ void bar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
 }
 
-// Bounded wait for the completion of the phase with the given parity.  After
-// an abort it returns false at once, unless honor_abort is false (teardown
-// waits for the CTA's own MMAs and copies, which always complete).
-__device__ __forceinline__ bool bar_wait(TcSmem *s, uint64_t *bar, uint32_t parity, bool honor_abort = true)
+// Bounded wait for the completion of the phase with the given parity: at
+// most s->spin polls (the configured limit).  After an abort it returns false
+// at once.  Waits for the CTA's own MMAs and copies (which always complete:
+// the accumulator flushes and the teardown) pass own = true: they ignore the
+// abort and take the default bound, so that nothing this CTA issued is still
+// in flight when it reads tensor memory, frees it or exits, and the phases of
+// those barriers never fall behind their waiters.
+__device__ __forceinline__ bool bar_wait(TcSmem *s, uint64_t *bar, uint32_t parity, bool own = false)
 {
-    for (int it = 0; it < kMaxSpin; ++it) {
+    const bool honor_abort = !own;
+    const int lim = own ? kMaxSpin : s->spin;
+    for (int it = 0; it < lim; ++it) {
         uint32_t ok;
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      " selp.u32 %0, 1, 0, p;\n}\n"
@@ -959,7 +965,7 @@ __device__ void flush_acc(const TcArgs &a, TcSmem *s, uint32_t tm, uint32_t &flu
     const int T = a.c.n_ticks;
     if (lane == 0) mma_commit(&s->done);
     __syncwarp();
-    const bool ok = bar_wait(s, &s->done, flushes & 1);
+    const bool ok = bar_wait(s, &s->done, flushes & 1, true) && !*(volatile int *)&s->abort;
     tc_fence_after();
     for (int t = 0; t < kTiles; ++t) {
         const int tick0 = k0 + kTileM * t;
@@ -1013,6 +1019,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_induced_current_tc(TcArgs a)
         }
         bar_init(&s->done, kIssuers);
         s->abort = 0;
+        s->spin = a.c.wait_spin_limit > 0 ? a.c.wait_spin_limit : kMaxSpin;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -1114,10 +1121,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_induced_current_tc(TcArgs a)
     if (warp < 4) {
         if (lane == 0) mma_commit(&s->done);
         __syncwarp();
-        bar_wait(s, &s->done, flushes & 1, false);
+        bar_wait(s, &s->done, flushes & 1, true);
         if (lane == 0 && warp == 0)
             for (int b = 0; b < 2; ++b)
-                if (im_last[b] >= 0) bar_wait(s, &s->full_im[b], (uint32_t)(im_last[b] >> 1) & 1, false);
+                if (im_last[b] >= 0) bar_wait(s, &s->full_im[b], (uint32_t)(im_last[b] >> 1) & 1, true);
     }
     tc_fence_before();
     __syncthreads();

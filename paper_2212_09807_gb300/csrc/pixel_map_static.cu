@@ -25,6 +25,7 @@ bool abi_config_ok(const sim_config *c);
 bool abi_segments_ok(const sim_segments *s);
 bool abi_events_ok(const sim_config *c, const sim_segments *s);
 bool abi_drifted_ok(const sim_drifted *d);
+bool abi_response_ok(const sim_response *r, bool need_table);
 int abi_cuda_fail(cudaError_t e);
 }  // namespace larsim
 
@@ -40,7 +41,9 @@ void *g_scratch_addr[kMaxDevices];   // device address of g_map_scratch, per dev
 
 // In host code `g_map_scratch` names a host-side stand-in, not device memory,
 // so the device address is looked up once per device (with that device
-// current) and cached.
+// current) and cached.  The cached address belongs to the device's context:
+// after cudaDeviceReset it is stale (the process must not call this entry
+// point on that device again).
 int scratch_for_current_device(void **out)
 {
     int dev = -1;
@@ -65,8 +68,7 @@ extern "C" int sim_pixel_map_noalloc(const sim_config *cfg, const sim_segments *
                                      int64_t pair_cap, int32_t *active_pixels, int32_t *pix_seg_off,
                                      int32_t *pix_seg_ids, int64_t pix_cap, int64_t *counts, void *stream)
 {
-    if (!abi_config_ok(cfg) || !abi_segments_ok(seg) || !abi_events_ok(cfg, seg) || !resp || resp->nb < 1 ||
-        resp->bins_per_pitch < 1 ||
+    if (!abi_config_ok(cfg) || !abi_segments_ok(seg) || !abi_events_ok(cfg, seg) || !abi_response_ok(resp, false) ||
         pair_cap < 0 || pix_cap < 0 || !counts)
         return SIM_ERR_INVALID_ARG;
     if (seg->n > 0 && !abi_drifted_ok(dr)) return SIM_ERR_INVALID_ARG;

@@ -20,6 +20,8 @@ SIM_OK = 0
 SIM_STATUS_PAIR_OVERFLOW = 1
 SIM_STATUS_PIXEL_OVERFLOW = 2
 SIM_STATUS_HIT_OVERFLOW = 4
+SIM_STATUS_TICK_RANGE = 8
+SIM_STATUS_TIMEOUT = 16
 ANCHOR_BYTES = 64
 
 _lib = None
@@ -55,7 +57,7 @@ class SimConfig(C.Structure):
         ("precision", C.c_int32), ("fp64_charge", C.c_int32), ("disabled_pixels", C.c_void_p),
         ("per_point_drift", C.c_int32), ("nearest_lut", C.c_int32),
         ("tc_units_per_sm", C.c_int32), ("tc_record_chunk", C.c_int32), ("direct_ctas_per_sm", C.c_int32),
-        ("tune_pad", C.c_int32),
+        ("wait_spin_limit", C.c_int32),
     ]
 
 
@@ -185,7 +187,7 @@ def make_config(cfg: dict) -> SimConfig:
             c.disabled_pixels = None if m is None else int(m.data_ptr())
             continue
         v = cfg.get(name, 0) if name in ("precision", "fp64_charge", "per_point_drift", "nearest_lut", "tc_units_per_sm",
-                                         "tc_record_chunk", "direct_ctas_per_sm", "tune_pad") else cfg[name]
+                                         "tc_record_chunk", "direct_ctas_per_sm", "wait_spin_limit") else cfg[name]
         setattr(c, name, int(v) & 0xFFFFFFFFFFFFFFFF if name == "seed" else (float(v) if ct is C.c_float else int(v)))
     return c
 

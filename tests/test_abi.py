@@ -112,6 +112,30 @@ def test_tuning_fields_are_checked(L):
         assert L.sim_workspace_size(C.byref(cfg), 0, 100, 1000, 100, C.byref(b)) == -1, bad
     cfg = sim.make_config(params.module_config(precision=2, tc_units_per_sm=8, tc_record_chunk=1 << 16))
     assert L.sim_workspace_size(C.byref(cfg), 0, 100, 1000, 100, C.byref(b)) == 0
+    for bad in (-1, (1 << 30) + 1):                     # the bounded waits' poll limit
+        cfg = sim.make_config(params.module_config(wait_spin_limit=bad))
+        assert L.sim_workspace_size(C.byref(cfg), 0, 100, 1000, 100, C.byref(b)) == -1, bad
+    cfg = sim.make_config(params.module_config(wait_spin_limit=16))
+    assert L.sim_workspace_size(C.byref(cfg), 0, 100, 1000, 100, C.byref(b)) == 0
+
+
+def test_noalloc_map_checks_the_response_like_the_map(L):
+    """sim_pixel_map_noalloc rejects on the host every response sim_pixel_map
+    rejects (table limits, row stride), before it looks up its scratch."""
+    from paper_2212_09807_gb300 import sim
+    from synth import params
+    cfg = sim.make_config(params.module_config())
+    seg, d = sim.SimSegments(), sim.SimDrifted()      # an empty event: no device pointer is needed
+    fake = C.c_void_p(16)                             # never dereferenced: the checks fail first
+    counts = C.c_void_p(64)
+    for nb, nt, ld, bpp in ((45, 1950, 1950, 30), (45, 4000, 4000, 30), (46, 1950, 1952, 30), (45, 1950, 1952, 0)):
+        r = sim.SimResponse()
+        r.nb, r.nt, r.ld, r.bins_per_pitch = nb, nt, ld, bpp
+        for fn in ("sim_pixel_map_noalloc", "sim_pixel_map"):
+            args = [C.byref(cfg), C.byref(seg), C.byref(d), C.byref(r), fake, fake, 10, fake, fake, fake, 10]
+            rc = (L.sim_pixel_map_noalloc(*args, counts, None) if fn == "sim_pixel_map_noalloc"
+                  else L.sim_pixel_map(*args, fake, 1 << 20, None))
+            assert rc == -1, (fn, nb, nt, ld, bpp)
 
 
 def test_autotuner_candidates_are_valid_configurations(L):
