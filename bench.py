@@ -2,9 +2,11 @@
 """Benchmark of the GB300 charge-readout path (arXiv:2212.09807, Sec. 3).
 
 One step = the whole hot path (quench+drift, pixel map, induced current,
-electronics) over one synthetic event resident in HBM.  Default workload: one
-detector module (2 TPCs, 2 anodes of 4x5 tiles of 70x70 pixels) with one
-neutrino-like interaction of ~20k segments.  Prints one JSON line.
+electronics) over one synthetic event resident in HBM.  Default workload: the
+largest single-GPU configuration, a beam spill on a 7x5 array of detector
+modules (35 modules, 6.86 M pixels): 50 neutrino-like interactions plus 100
+rock muons, ~1.2e6 segments, t0 spread over 10 us.  The one-module
+interaction (~2e4 segments) is timed beside it.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -32,9 +34,9 @@ sys.path.insert(0, ROOT)
 from synth import events, params, response  # noqa: E402
 
 # kernels per step: 1 quench/drift + 14 pixel map + 6 electronics, plus the induced current:
-# 1 (FP32 direct) or 13 (tensor cores: work plan 4 + two 3-kernel scans, table unfolding 1,
-# contraction 1, reduction of split groups 1)
-KERNELS_PER_STEP = {0: 22, 1: 34, 2: 34}
+# 1 (FP32 direct) or 14 (tensor cores: work plan 4 + two 3-kernel scans, table rounding 1,
+# table unfolding 1, contraction 1, reduction of split groups 1)
+KERNELS_PER_STEP = {0: 22, 1: 35, 2: 35}
 FP32_LANES_PER_SM = 128
 
 
@@ -44,7 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["module", "tile", "spill"], default="module")
+    ap.add_argument("--workload", choices=["module", "tile", "spill"], default="spill")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--precision", type=int, choices=[0, 1, 2], default=2,
@@ -55,9 +57,16 @@ def parse():
     ap.add_argument("--no-light", action="store_true", help="skip timing the light path")
     ap.add_argument("--no-tune", action="store_true",
                     help="time the headline event with the default scheduling shapes instead of autotuned ones")
-    ap.add_argument("--serving-requests", type=int, default=15, help="requests per load point")
-    ap.add_argument("--batched-events", type=int, default=32)
-    ap.add_argument("--batched-hi", type=float, default=1.0e4, help="largest event of the batched comparison")
+    ap.add_argument("--serving-requests", type=int, default=60, help="requests per load point")
+    ap.add_argument("--serving-loads", default="0.7",
+                    help="comma-separated arrival rates as fractions of the plain form's capacity")
+    ap.add_argument("--batched-events", type=int, default=256)
+    ap.add_argument("--batched-hi", type=float, default=2.0e5, help="largest event of the batched comparison")
+    ap.add_argument("--batched-subbatches", type=int, default=4,
+                    help="graph-captured sub-batches the batched events are cut into")
+    ap.add_argument("--form-steps", type=int, default=2, help="timed steps of each non-headline current form")
+    ap.add_argument("--cpu-pixels", type=int, default=1024,
+                    help="active pixels of the CPU baseline's timed sample")
     return ap.parse_args()
 
 
@@ -186,30 +195,34 @@ def stored_traffic(kernel_file: str):
 
 # ------------------------------------------------------------------ oracle ---
 
-def oracle_sample(cfg, seg, lut64, rng, n_pix=6):
+def oracle_sample(cfg, seg, lut64, rng, n_pix=1024):
     """Times the FP64 oracle on a bounded sample of one event and scales it to
-    the whole event: quench+drift and the (box-restricted brute-force) pixel map
-    of every segment are run in full; current + electronics of ``n_pix`` random
-    active pixels are timed and scaled by the event's active-pixel count.
-    Returns (estimated whole-event seconds, sample description)."""
+    the whole event: quench+drift and the pixel map of every segment run in
+    full (one thread); current + front end of ``n_pix`` random active pixels
+    run on all host cores (the oracle's OpenMP many-pixel functions) and are
+    scaled by the event's active-pixel count.  Returns (estimated whole-event
+    seconds, host threads used, sample description)."""
     import oracle
     o = oracle.Oracle(cfg, params.LUT, lut64)
     t0 = time.perf_counter()
     d = o.quench_drift(seg)
-    pix, _, _, _ = o.pixel_map(seg, d)
+    m = o.map_event(seg, d)
     t_map = time.perf_counter() - t0
-    keys = np.array(sorted(pix))
-    pick = rng.choice(keys, min(n_pix, len(keys)), replace=False)
+    P = len(m["pixels"])
+    idx = np.sort(rng.choice(P, min(n_pix, P), replace=False))
+    pix = m["pixels"][idx]
+    off = np.concatenate([[0], np.cumsum(m["off"][idx + 1] - m["off"][idx])])
+    segs = np.concatenate([m["segs"][m["off"][i]:m["off"][i + 1]] for i in idx])
     t0 = time.perf_counter()
-    for p in pick:
-        I = o.pixel_current(seg, d, int(p), pix[int(p)])
-        o.electronics(int(p), I)
-    t_pix = (time.perf_counter() - t0) / len(pick)
-    est = t_map + t_pix * len(keys)
-    desc = (f"oracle, 1 thread: quench+drift and pixel map of all {len(seg['x0'])} segments in full, "
-            f"current+electronics timed on {len(pick)} random active pixels and scaled to all "
-            f"{len(keys)} active pixels")
-    return est, desc
+    I = o.pixel_currents(seg, d, pix, off, segs)
+    o.electronics_many(pix, I)
+    t_pix = (time.perf_counter() - t0) / len(idx)
+    threads = o.threads()
+    est = t_map + t_pix * P
+    desc = (f"FP64 oracle: quench+drift and pixel map of all {len(seg['x0'])} segments in full (1 thread); "
+            f"current + front end of {len(idx)} random active pixels on {threads} host threads (OpenMP), "
+            f"scaled to all {P} active pixels")
+    return est, threads, desc
 
 
 def run_reference(args):
@@ -223,7 +236,7 @@ def run_reference(args):
     ests = []
     t_start = time.perf_counter()
     for i in range(args.warmup + args.steps):
-        est, sdesc = oracle_sample(cfg, seg, lut64, rng, n_pix=3)
+        est, threads, sdesc = oracle_sample(cfg, seg, lut64, rng, n_pix=128)
         if i >= args.warmup:
             ests.append(est)
     wall = time.perf_counter() - t_start
@@ -232,7 +245,7 @@ def run_reference(args):
         "impl": "reference", "metric": "segments/s", "value": v, "unit": "segments/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
         "dtype": "f64", "data": "synthetic", "config": {"workload": desc, "segments": S},
-        "cpu_baseline": {"value": v, "unit": "segments/s", "cores": 1, "kind": "oracle", "sample": sdesc},
+        "cpu_baseline": {"value": v, "unit": "segments/s", "cores": threads, "kind": "oracle", "sample": sdesc},
         "e2e": {"value": v, "unit": "segments/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": wall, "vs_baseline": None,
     }))
@@ -240,24 +253,34 @@ def run_reference(args):
 
 # --------------------------------------------------------------------- ours ---
 
-def batched_vs_plain(cfg, lut, dev, n_events=32, lo=1.0e3, hi=1.0e4, reps=2):
-    """The same events run one sim_event call each (plain) and as one batch;
-    segments/s of both and the per-event latencies of the plain form (each
-    event's own device time) against the batch's completion time."""
+def batched_vs_plain(cfg, lut, dev, n_events=256, lo=1.0e3, hi=2.0e5, n_sub=4):
+    """Batched events (256 interactions with segment counts log-uniform in
+    [1e3, 2e5], all waiting at t = 0) run two ways on the same GPU:
+      * plain: one sim_event call per event, in order;
+      * batched: the events cut into ``n_sub`` sub-batches of consecutive
+        events, each a replay of one CUDA graph of the batched sim_event
+        (sim.BatchGraphRunner: capacities of the largest sub-batch, event
+        offsets and ids in device memory), scheduling shapes autotuned on a
+        batch of the first 16 events.
+    Reports segments/s of both, every event's completion time from the common
+    start (its own call's end, or its sub-batch's replay end: p50 / p99), and
+    the plain form's per-event device times.  Inputs are resident on the
+    device before the timed region."""
     import torch
-    from paper_2212_09807_gb300 import sim
+    from paper_2212_09807_gb300 import serve, sim, tune
     evs = events.batch_events(cfg, params.BASE["seed"] + 4, n_events, lo, hi)
     sizes = [len(e["x0"]) for e in evs]
     total, big = sum(sizes), max(sizes)
     ids = list(range(1000, 1000 + n_events))
-    from paper_2212_09807_gb300 import serve
     singles = [sim.Segments.from_numpy(e, i, dev) for e, i in zip(evs, ids)]
-    batch = sim.Segments.batch_from_numpy(evs, ids, dev)
+    per = -(-n_events // n_sub)
+    subs = [(evs[k:k + per], ids[k:k + per]) for k in range(0, n_events, per)]
+    sub_segs = [sim.Segments.batch_from_numpy(e, i, dev) for e, i in subs]
 
-    def fitted(n, caps, runs, max_events=0):
-        """Runner whose capacities fit every event of `runs` (untimed sizing pass)."""
+    def fitted(cfg_, n, caps, runs, max_events=0):
+        """Runner whose capacities fit every event (or batch) of `runs` (untimed sizing pass)."""
         while True:
-            r = sim.EventRunner(cfg, lut, params.LUT["nt"], params.LUT["bins_per_pitch"], n, *caps, device=dev,
+            r = sim.EventRunner(cfg_, lut, params.LUT["nt"], params.LUT["bins_per_pitch"], n, *caps, device=dev,
                                 max_events=max_events)
             worst = [0, 0, 0]
             for sg in runs:
@@ -272,66 +295,65 @@ def batched_vs_plain(cfg, lut, dev, n_events=32, lo=1.0e3, hi=1.0e4, reps=2):
             del r
             torch.cuda.empty_cache()
 
-    plain = fitted(big, serve._caps(big), singles)
-    # autotuned scheduling shapes for the batched call, timed on a batch of the first 16 events (untimed here)
-    from paper_2212_09807_gb300 import tune
+    # plain: the sizing pass is also the warm-up
+    plain = fitted(cfg, big, serve._caps(big), singles)
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(n_events + 1)]
+    marks[0].record()
+    for k, sg in enumerate(singles):
+        plain.enqueue(sg)
+        marks[k + 1].record()
+    torch.cuda.synchronize()
+    assert plain.counts()[3] == 0
+    t_plain = marks[0].elapsed_time(marks[-1])
+    plain_done = [marks[0].elapsed_time(marks[k + 1]) for k in range(n_events)]
+    plain_service = [marks[k].elapsed_time(marks[k + 1]) for k in range(n_events)]
+    del plain
+    torch.cuda.empty_cache()
+
+    # batched: shapes tuned on a sample batch, runner sized on every sub-batch, one graph replayed per sub-batch
     ns = min(16, n_events)
     sample = sim.Segments.batch_from_numpy(evs[:ns], ids[:ns], dev)
     s_tot = sum(sizes[:ns])
-    probe = fitted(s_tot, serve._caps(s_tot), [sample], max_events=ns)
+    probe = fitted(cfg, s_tot, serve._caps(s_tot), [sample], max_events=ns)
     s_caps = (probe.max_pairs, probe.max_pixels, probe.hits.capacity)
     del probe
     chosen, table = tune.autotune(cfg, lut, params.LUT["nt"], params.LUT["bins_per_pitch"], sample, s_caps,
                                   device=dev)
-    tuned_cfg = dict(cfg, **chosen)
-    cfg_keep = cfg
-    cfg = tuned_cfg
-    batch_run = fitted(total, serve._caps(total), [batch], max_events=n_events)
-    cfg = cfg_keep
-    best_plain, best_batch, lat = None, None, None
-    for _ in range(reps):
-        marks = [torch.cuda.Event(enable_timing=True) for _ in range(n_events + 1)]
-        marks[0].record()
-        for k, sg in enumerate(singles):
-            plain.enqueue(sg)
-            marks[k + 1].record()
-        torch.cuda.synchronize()
-        t_plain = marks[0].elapsed_time(marks[-1])
-        per = [marks[k].elapsed_time(marks[k + 1]) for k in range(n_events)]
-        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        b0.record()
-        batch_run.enqueue(batch)
-        b1.record()
-        torch.cuda.synchronize()
-        t_batch = b0.elapsed_time(b1)
-        if best_plain is None or t_plain < best_plain:
-            best_plain, lat = t_plain, per
-        best_batch = t_batch if best_batch is None else min(best_batch, t_batch)
-    assert batch_run.counts()[3] == 0
-    # the plain loop again, each event a replay of one CUDA graph of the whole step (sim.GraphRunner)
-    g = sim.GraphRunner(plain)
-    best_graph, glat = None, None
-    for _ in range(reps):
-        marks = [torch.cuda.Event(enable_timing=True) for _ in range(n_events + 1)]
-        marks[0].record()
-        for k, sg in enumerate(singles):
-            g.load(sg.cols, sg.n, sg.event_id)
-            g.replay()
-            marks[k + 1].record()
-        torch.cuda.synchronize()
-        t_graph = marks[0].elapsed_time(marks[-1])
-        if best_graph is None or t_graph < best_graph:
-            best_graph, glat = t_graph, [marks[k].elapsed_time(marks[k + 1]) for k in range(n_events)]
-    assert plain.counts()[3] == 0
+    bcfg = dict(cfg, **chosen)
+    nmax = max(sg.n for sg in sub_segs)
+    runner = fitted(bcfg, nmax, serve._caps(nmax), sub_segs, max_events=per)
+    g = sim.BatchGraphRunner(runner)
+    for sg in sub_segs[:1]:                       # one untimed replay
+        g.load(sg)
+        g.replay()
+    torch.cuda.synchronize()
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(len(sub_segs) + 1)]
+    marks[0].record()
+    for k, sg in enumerate(sub_segs):
+        g.load(sg)
+        g.replay()
+        marks[k + 1].record()
+    torch.cuda.synchronize()
+    assert runner.counts()[3] == 0
+    t_batch = marks[0].elapsed_time(marks[-1])
+    batch_done = []
+    for k, (e, _) in enumerate(subs):
+        batch_done += [marks[0].elapsed_time(marks[k + 1])] * len(e)
+    del g, runner
+    torch.cuda.empty_cache()
+    pct = lambda v, q: float(np.percentile(v, q))          # noqa: E731
     return {"events": n_events, "segments": total, "sizes": f"log-uniform [{lo:.0f}, {hi:.0f}] segments",
-            "plain_segments_per_s": total / (best_plain / 1e3), "batched_segments_per_s": total / (best_batch / 1e3),
-            "graph_segments_per_s": total / (best_graph / 1e3),
-            "plain_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-            "graph_latency_ms": {"p50": float(np.percentile(glat, 50)), "p99": float(np.percentile(glat, 99))},
-            "batched_completion_ms": best_batch,
+            "arrival": "all events waiting at t = 0; completion times from the common start",
+            "plain_segments_per_s": total / (t_plain / 1e3),
+            "graph_batched_segments_per_s": total / (t_batch / 1e3),
+            "plain_completion_ms": {"p50": pct(plain_done, 50), "p99": pct(plain_done, 99)},
+            "batched_completion_ms": {"p50": pct(batch_done, 50), "p99": pct(batch_done, 99)},
+            "plain_service_ms": {"p50": pct(plain_service, 50), "p99": pct(plain_service, 99)},
+            "subbatches": len(subs), "events_per_subbatch": per,
+            "subbatch_ms": [marks[k].elapsed_time(marks[k + 1]) for k in range(len(subs))],
+            "total_ms": {"plain": t_plain, "graph_batched": t_batch},
             "tuning": {"sample": f"batch of the first {ns} events", "chosen": chosen,
                        "candidates_ms": [[c, round(ms, 3)] for c, ms in table]}}
-
 
 
 FORMS = {0: ("fp32_direct", "f32"), 1: ("bf16_tensor", "bf16"), 2: ("fp16_tensor", "f16")}
@@ -347,7 +369,8 @@ def time_form(cfg, seg, lut, dev, precision, steps, warmup, rank):
     cfg = dict(cfg, precision=precision)
     S = len(seg["x0"])
     T = int(cfg["n_ticks"])
-    caps = [40 * S, 4 * S, 4 * S]
+    from paper_2212_09807_gb300 import serve
+    caps = list(serve._caps(S))
     while True:                         # capacities: grow until the event fits (untimed sizing pass)
         run = sim.EventRunner(cfg, lut, params.LUT["nt"], params.LUT["bins_per_pitch"], S, *caps, device=dev)
         segs = sim.Segments.from_numpy(seg, event_id=rank, device=dev)
@@ -573,11 +596,14 @@ def light_path(dev, names=("module", "spill"), reps=5):
     return out
 
 
-def form_roofline(run, cfg, precision, a4_s, props, sm_mhz, dev):
-    """Roofline of the induced-current kernel of one form: FP32 direct against
-    the FP32 FMA peak; tensor-core forms against the measured dense 16-bit
-    tensor peak (dense MMA work counted on the device), with the algorithmic
-    (useful) work also stated."""
+def form_roofline(run, cfg, precision, a4_s, fp32_peak, dev):
+    """Roofline of the induced-current kernel of one form.  FP32 direct:
+    against the measured FP32 FMA rate (sim_probe_fma), work 2 flop per (point,
+    pixel within the table's reach, table tick).  Tensor-core forms: against
+    the measured dense 16-bit tensor peak, achieved = the algorithmic work
+    2 flop x nnz(Q) x L (one multiply-add per nonzero binned-charge cell and
+    table tick, cells counted on the device) over the call's time; the dense
+    MMA work (zeros inside the issued tiles included) is given beside it."""
     import torch
     from paper_2212_09807_gb300 import sim
     S = run.max_segments
@@ -588,28 +614,27 @@ def form_roofline(run, cfg, precision, a4_s, props, sm_mhz, dev):
     samples = int(ns[an >= 0].sum()) * int(cfg["mc_per_sample"])
     L = params.LUT["nt"]
     w_alg = 2.0 * 9 * L * samples                       # flop per launch (9 pixels per point)
-    useful = w_alg / a4_s / 1e12
+    per_point = w_alg / a4_s / 1e12
     if precision == 0:
-        peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-        return {"bound": "alu", "achieved": useful, "peak": peak, "unit": "TFLOP/s", "frac": useful / peak,
-                "traffic": stored_traffic("induced_current.cu"), "kernel": "k_induced_current",
-                "peak_note": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz",
+        return {"bound": "alu", "achieved": per_point, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": per_point / fp32_peak, "traffic": stored_traffic("induced_current.cu"),
+                "kernel": "k_induced_current",
+                "peak_note": "FP32 FMA rate measured on this GPU by sim_probe_fma (independent FMA chains), "
+                             "of measured",
                 "work_note": "2 flop x 9 pixels x 1950 table ticks per (point, perturbation)"}, samples
     n_mma = int(run.ws[4].item())
     nnz = int(run.ws[5].item())
-    L = params.LUT["nt"]
     dense = 2.0 * 128 * 32 * 16 * n_mma / a4_s / 1e12
-    useful_q = 2.0 * nnz * L / a4_s / 1e12
+    useful = 2.0 * nnz * L / a4_s / 1e12
     tpk = measured_peaks().get("bf16_tflops_sustained") or 1700.0
-    return {"bound": "tensor", "achieved": dense, "peak": tpk, "unit": "TFLOP/s", "frac": dense / tpk,
+    return {"bound": "tensor", "achieved": useful, "peak": tpk, "unit": "TFLOP/s", "frac": useful / tpk,
             "traffic": stored_traffic("induced_current_tc.cu"), "kernel": "k_induced_current_tc",
-            "mma_per_launch": n_mma, "nnz_charge_cells": nnz,
-            "useful_achieved": useful_q, "useful_frac": useful_q / tpk,
-            "per_point_achieved": useful,
+            "nnz_charge_cells": nnz, "mma_per_launch": n_mma,
+            "dense_achieved": dense, "dense_frac": dense / tpk, "per_point_achieved": per_point,
             "peak_note": "measured dense bf16 sustained (kernel timed inside a step), of measured; fp16 has the "
                          "same nominal rate",
-            "work_note": "dense: 2 x 128 x 32 x 16 flop per MMA (counted on the device); useful: 2 flop x "
-                         "nnz(Q) x 1950 table ticks (nonzero binned-charge cells, counted on the device); "
+            "work_note": "achieved: 2 flop x nnz(Q) x 1950 table ticks (nonzero binned-charge cells Q[p, node, "
+                         "tick], counted on the device); dense: 2 x 128 x 32 x 16 flop per issued MMA; "
                          "per_point: 2 flop x 9 pixels x 1950 ticks per (point, perturbation)"}, samples
 
 
@@ -662,6 +687,20 @@ def serving_vs_plain(precision, dev, n_requests=12, loads=(0.5, 0.7, 0.9), seed_
             "hbm_budget_gb": 120, "slice_pixels": SLICE, "loads": out}
 
 
+def timed_event(cfg, seg, lut, dev, precision, steps, warmup, event_id, fp32_peak):
+    """time_form plus the derived per-step numbers and the kernel roofline."""
+    run, per, (n_pairs, n_pix, n_hits, _) = time_form(cfg, seg, lut, dev, precision, steps, warmup, event_id)
+    S, T = len(seg["x0"]), int(cfg["n_ticks"])
+    step_ms = per.sum(axis=1)
+    rl, samples = form_roofline(run, dict(cfg, precision=precision), precision, float(per[:, 2].mean()) / 1e3,
+                                fp32_peak, dev)
+    out = {"dtype": FORMS[precision][1], "ms_per_step": float(step_ms.mean()),
+           "segments_per_s": S / (float(step_ms.mean()) / 1e3), "induced_current_ms": float(per[:, 2].mean()),
+           "roofline": rl}
+    info = dict(S=S, T=T, n_pairs=n_pairs, n_pix=n_pix, n_hits=n_hits, samples=samples, step_ms=step_ms)
+    return run, per, out, info
+
+
 def run_ours(args):
     import torch
     from paper_2212_09807_gb300 import sim
@@ -683,6 +722,7 @@ def run_ours(args):
     lut_pad = response.pad_rows(lut64)
     lut = torch.as_tensor(lut_pad, device=dev)
     props = torch.cuda.get_device_properties(dev)
+    fp32_peak = sim.fma_peak_tflops(dev)           # measured FP32 FMA rate, TFLOP/s
 
     # the other forms of the induced-current step, timed on the same event first (untimed for the headline)
     forms = {}
@@ -690,23 +730,24 @@ def run_ours(args):
         for prec in (0, 1, 2):
             if prec == args.precision:
                 continue
-            r2, per2, c2 = time_form(cfg, seg, lut, dev, prec, max(3, args.steps // 2), args.warmup, rank)
-            sm_max = measured_peaks().get("sm_max_mhz", 2070.0)
-            rl, _ = form_roofline(r2, cfg, prec, float(per2[:, 2].mean()) / 1e3, props, sm_max, dev)
-            forms[FORMS[prec][0]] = {"dtype": FORMS[prec][1], "ms_per_step": float(per2.sum(axis=1).mean()),
-                                     "segments_per_s": S / (float(per2.sum(axis=1).mean()) / 1e3),
-                                     "induced_current_ms": float(per2[:, 2].mean()), "roofline": rl}
+            r2, _, out2, _ = timed_event(cfg, seg, lut, dev, prec, args.form_steps, 1, rank, fp32_peak)
+            forms[FORMS[prec][0]] = dict(out2, steps=args.form_steps, warmup=1)
             del r2
             torch.cuda.empty_cache()
 
     # scheduling shapes of the induced-current step for this event, picked by the autotuner (untimed);
-    # results do not depend on them beyond the tensor-core forms' accumulation rounding
+    # results do not depend on them beyond the tensor-core forms' accumulation rounding.  A large event
+    # is tuned over a few candidates with one repetition each.
     tuned = None
     if not args.no_tune:
-        from paper_2212_09807_gb300 import tune
+        from paper_2212_09807_gb300 import serve, tune
         segs_dev = sim.Segments.from_numpy(seg, event_id=replica_event_id(rank), device=dev)
-        tuned, _ = tune.autotune(cfg, lut, L, params.LUT["bins_per_pitch"], segs_dev, (40 * S, 4 * S, 4 * S),
-                                 reps=2, device=dev)
+        big = S > 200000
+        cands = None
+        if big and args.precision != 0:
+            cands = [dict(tc_units_per_sm=u, tc_record_chunk=c) for u, c in ((1, 1 << 20), (2, 1 << 20), (2, 1 << 18))]
+        tuned, _ = tune.autotune(cfg, lut, L, params.LUT["bins_per_pitch"], segs_dev, serve._caps(S, 1.2),
+                                 reps=1 if big else 2, device=dev, cands=cands)
         cfg = dict(cfg, **tuned)
         del segs_dev
         torch.cuda.empty_cache()
@@ -720,53 +761,70 @@ def run_ours(args):
     clk = ClockSampler(gpu_id)
     clk.start()
     time.sleep(0.15)
-    run, per, (n_pairs, n_pix, n_hits, status) = time_form(cfg, seg, lut, dev, args.precision, args.steps,
-                                                           args.warmup, replica_event_id(rank))
+    run, per, head, info = timed_event(cfg, seg, lut, dev, args.precision, args.steps, args.warmup,
+                                       replica_event_id(rank), fp32_peak)
     clocks = clk.stop()
-    step_ms = per.sum(axis=1)
-    total_ms = float(step_ms.sum())
-    total_ms = max_over_ranks(total_ms, pg, dev)
+    n_pairs, n_pix, n_hits, samples, step_ms = (info[k] for k in ("n_pairs", "n_pix", "n_hits", "samples",
+                                                                   "step_ms"))
+    total_ms = max_over_ranks(float(step_ms.sum()), pg, dev)
     value = job_rate(world, S * args.steps, total_ms / 1e3)
     a45_ms = max_over_ranks(float(per[:, 2:].sum()), pg, dev)
     pix_ticks = job_rate(world, n_pix * T * args.steps, a45_ms / 1e3)
-    sm_mhz = clocks.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
-    roofline, samples = form_roofline(run, cfg, args.precision, float(per[:, 2].mean()) / 1e3, props, sm_mhz, dev)
-    forms[FORMS[args.precision][0]] = {"dtype": FORMS[args.precision][1], "ms_per_step": total_ms / args.steps,
-                                       "segments_per_s": value / world,
-                                       "induced_current_ms": float(per[:, 2].mean()), "roofline": roofline}
+    roofline = head["roofline"]
+    forms[FORMS[args.precision][0]] = dict(head, steps=args.steps, warmup=args.warmup)
 
     # end to end through the public API: pinned host segments in, hits out
     io = sim.EventIO(run)
     host = {k: torch.as_tensor(np.ascontiguousarray(seg[k], dtype=np.float32)).pin_memory() for k in seg}
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, min(args.warmup, 2))):
         io.simulate(host, S, replica_event_id(rank))
     torch.cuda.synchronize()
     if pg:
         pg.barrier()
     t0 = time.perf_counter()
     h2d = d2h = 0
-    for _ in range(args.steps):
+    e2e_steps = max(2, args.steps // 2)
+    for _ in range(e2e_steps):
         _, _, hb, db = io.simulate(host, S, replica_event_id(rank))
         h2d, d2h = hb, db
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, pg, dev)
-    e2e = {"value": job_rate(world, S * args.steps, e2e_s), "unit": "segments/s", "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h}
-    post = post_hit_steps(run, cfg, dev) if not args.no_post else None
+    e2e = {"value": job_rate(world, S * e2e_steps, e2e_s), "unit": "segments/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "steps": e2e_steps}
     del run, io
     torch.cuda.empty_cache()
+
+    # the one-module interaction beside the headline, with the steps after the front end on its hits
+    module = None
+    post = None
+    if args.workload != "module":
+        mcfg, mseg, mdesc = workload("module")
+        mcfg["precision"] = args.precision
+        mlut = torch.as_tensor(response.pad_rows(response.lut_for(mcfg, params.LUT)), device=dev)
+        mrun, mper, mout, minfo = timed_event(mcfg, mseg, mlut, dev, args.precision, 10, 3, replica_event_id(rank),
+                                              fp32_peak)
+        module = dict(mout, workload=mdesc, segments=minfo["S"], active_pixels=minfo["n_pix"],
+                      hits=minfo["n_hits"], steps=10, warmup=3, scheduling="defaults",
+                      step_breakdown_ms={k: float(mper[:, i].mean()) for i, k in
+                                         enumerate(("quench_drift", "pixel_map", "induced_current", "electronics"))})
+        post = post_hit_steps(mrun, mcfg, dev) if not args.no_post else None
+        del mrun
+        torch.cuda.empty_cache()
     light_res = light_path(dev) if not args.no_light else None
     torch.cuda.empty_cache()
 
-    batched = (batched_vs_plain(cfg, lut, dev, args.batched_events, 1.0e3, args.batched_hi,
-                                reps=1 if args.batched_events > 64 else 2) if not args.no_batched else None)
-    serving = serving_vs_plain(args.precision, dev, args.serving_requests) if not args.no_serving else None
+    bcfg = params.module_config(precision=args.precision)
+    blut = torch.as_tensor(response.pad_rows(response.lut_for(bcfg, params.LUT)), device=dev)
+    batched = (batched_vs_plain(bcfg, blut, dev, args.batched_events, 1.0e3, args.batched_hi,
+                                args.batched_subbatches) if not args.no_batched else None)
+    loads = tuple(float(x) for x in args.serving_loads.split(",") if x)
+    serving = serving_vs_plain(args.precision, dev, args.serving_requests, loads) if not args.no_serving else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         lut_or = lut_pad[..., :L].astype(np.float64)
-        est, sdesc = oracle_sample(cfg, seg, lut_or, np.random.default_rng(0), n_pix=8)
-        cpu = {"value": S / est, "unit": "segments/s", "cores": 1, "kind": "oracle", "sample": sdesc}
+        est, threads, sdesc = oracle_sample(cfg, seg, lut_or, np.random.default_rng(0), n_pix=args.cpu_pixels)
+        cpu = {"value": S / est, "unit": "segments/s", "cores": threads, "kind": "oracle", "sample": sdesc}
 
     if rank == 0:
         print(json.dumps({
@@ -785,7 +843,8 @@ def run_ours(args):
                                   "induced_current": float(per[:, 2].mean()),
                                   "electronics": float(per[:, 3].mean())},
             "roofline": roofline, "step_rooflines": step_rooflines(per, S, n_pairs, n_pix, T),
-            "forms": forms, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,
+            "fp32_fma_peak_tflops": fp32_peak,
+            "forms": forms, "module_event": module, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,
             "serving": serving, "after_front_end": post, "light": light_res,
             "gpu_launches": KERNELS_PER_STEP[args.precision] * args.steps, "clocks": clocks,
         }))

@@ -327,6 +327,15 @@ int sim_event_view_of(const sim_config *cfg, int64_t max_events, int64_t n_segme
                       int64_t max_pairs, int64_t max_pixels, void *ws, size_t ws_bytes,
                       sim_event_view *view);
 
+/* Measurement support (no counterpart in the paper): enqueues a kernel of
+ * `blocks` CTAs of 256 threads that issues only independent FP32 fused
+ * multiply-adds, iters x 128 per thread, and writes the flops it performs to
+ * *flops (host).  Timed with events on `stream`, it gives the device's FP32
+ * FMA rate, the bound of the FP32 direct form of sim_induced_current.  sink:
+ * device FP32 [blocks * 256] (never written in practice; it keeps the
+ * arithmetic live).  1 <= blocks <= 2^20, iters >= 1. */
+int sim_probe_fma(int64_t blocks, int32_t iters, float *sink, double *flops, void *stream);
+
 /* ---------------------------------------------- after the front end ---- */
 
 /* Running sums of the response table rows, for sim_hit_truth, stored as quads

@@ -91,7 +91,7 @@ def lib():
                                         + [i32p, i32p, C.c_uint64, C.c_int32, i64p, C.c_int64, f64p, C.c_double,
                                            C.POINTER(C.c_int64)])
         L.ora_electronics.argtypes = [P(_Cfg), C.c_uint64, C.c_int32, f64p, C.c_int64,
-                                      i32p, i32p, i32p, f64p, C.c_double, i32p]
+                                      i32p, i32p, i32p, f64p, C.c_double, i32p, f64p]
         L.ora_electronics.restype = C.c_int64
         L.ora_hit_intervals.argtypes = [P(_Cfg), C.c_int64, i32p, i32p, i32p, i32p]
         L.ora_hit_point.argtypes = [P(_Cfg), C.c_int32, C.c_int32, C.c_double, f64p]
@@ -104,7 +104,7 @@ def lib():
         L.ora_pixel_currents_many.argtypes = ([P(_Cfg), f64p] + [f32p] * 8 + [f64p] * 4
                                               + [i32p, i32p, C.c_uint64, C.c_int64, i32p, i64p, i64p, f64p, C.c_int])
         L.ora_electronics_many.argtypes = [P(_Cfg), C.c_uint64, C.c_int64, i32p, f64p, f64p, C.c_int64, i32p, i32p,
-                                           i32p, f64p, i64p, i32p, C.c_int]
+                                           i32p, f64p, i64p, i32p, f64p, C.c_int]
         assert L.ora_cfg_size() == C.sizeof(_Cfg), "oracle config struct mismatch"
         _lib = L
     return _lib
@@ -315,12 +315,13 @@ class Oracle:
         qv = np.zeros((n, cap))
         nh = np.zeros(n, np.int64)
         tie = np.zeros(n, np.int32)
+        pt = np.zeros(n)
         self.L.ora_electronics_many(C.byref(self.c), event_id, n, _p(pixels, C.c_int32), _p(I, C.c_double),
                                     _p(bnd, C.c_double), cap, _p(tc, C.c_int32), _p(ta, C.c_int32),
                                     _p(ad, C.c_int32), _p(qv, C.c_double), _p(nh, C.c_int64), _p(tie, C.c_int32),
-                                    int(n_threads))
+                                    _p(pt, C.c_double), int(n_threads))
         return [dict(t_cross=tc[i, :nh[i]].copy(), t_adc=ta[i, :nh[i]].copy(), adc=ad[i, :nh[i]].copy(),
-                     q=qv[i, :nh[i]].copy(), tie_tick=int(tie[i])) for i in range(n)]
+                     q=qv[i, :nh[i]].copy(), tie_tick=int(tie[i]), p_tie=float(pt[i])) for i in range(n)]
 
     # -- step 4 ------------------------------------------------------------
     def pixel_current(self, seg: dict, dr: dict, pixel: int, segs, event_id: int = 0,
@@ -353,11 +354,12 @@ class Oracle:
         ad = np.zeros(cap, np.int32)
         qv = np.zeros(cap)
         tie = np.zeros(1, np.int32)
+        pt = np.zeros(1)
         n = self.L.ora_electronics(C.byref(self.c), event_id, int(pixel), _p(I, C.c_double), cap,
                                    _p(tc, C.c_int32), _p(ta, C.c_int32), _p(ad, C.c_int32),
-                                   _p(qv, C.c_double), float(band), _p(tie, C.c_int32))
+                                   _p(qv, C.c_double), float(band), _p(tie, C.c_int32), _p(pt, C.c_double))
         return dict(t_cross=tc[:n].copy(), t_adc=ta[:n].copy(), adc=ad[:n].copy(),
-                    q=qv[:n].copy(), tie_tick=int(tie[0]))
+                    q=qv[:n].copy(), tie_tick=int(tie[0]), p_tie=float(pt[0]))
 
     # -- after step 5: per-hit charge truth, 3-D points, dQ/dx --------------
     def hit_intervals(self, t_cross, t_adc):

@@ -553,12 +553,20 @@ void ora_pixel_current(const ora_cfg *c, const double *lut,
  * A digitisation still pending at the end of the window is dropped.
  * Threshold and ADC decisions compare FP32 roundings of the FP64 operands.
  * ``tie_tick`` receives the first tick whose decision lies within ``band``
- * electrons of its threshold (or -1).  Returns the number of hits (may
- * exceed cap; only cap are written). */
+ * electrons of its threshold (or -1).  ``p_tie`` (if non-null) receives the
+ * probability, under the noise model, that some decision of this trace lies
+ * within the band: each idle tick's margin v - thr is normal with mean q - thr
+ * (q: the CSA charge of the trace) and variance s_unc^2 + s_disc^2, so it falls
+ * within the band with probability ~ 2 band phi((q - thr)/s) / s, and an ADC
+ * decision's fractional code with probability 2 band / lsb_e; p_tie = 1 - prod
+ * (1 - p).  Tests use it to bound how many pixels a band may exclude.
+ * Returns the number of hits (may exceed cap; only cap are written). */
 int64_t ora_electronics(const ora_cfg *c, uint64_t event_id, int32_t pixel, const double *I,
                         int64_t cap, int32_t *t_cross, int32_t *t_adc, int32_t *adc,
-                        double *qv, double band, int32_t *tie_tick)
+                        double *qv, double band, int32_t *tie_tick, double *p_tie)
 {
+    const double sd = sqrt(c->s_unc * c->s_unc + c->s_disc * c->s_disc);
+    double log_none = 0.0;                     /* log P(no decision within the band) */
     int T = c->n_ticks;
     double lsb_e = c->gain * c->lsb_mV;
     int adc_max = (1 << c->adc_bits) - 1;
@@ -580,6 +588,11 @@ int64_t ora_electronics(const ora_cfg *c, uint64_t event_id, int32_t pixel, cons
             double v = q + c->s_unc * n[0];
             double thr = c->thr + c->s_disc * n[1];
             if (tie < 0 && fabs(v - thr) < band) tie = k;
+            if (p_tie && sd > 0.0) {
+                double z = (q - c->thr) / sd;
+                double p = 2.0 * band * exp(-0.5 * z * z) / (sd * sqrt(2.0 * ORA_PI));
+                log_none += log1p(-(p < 1.0 ? p : 1.0 - 1e-16));
+            }
             if ((float)v >= (float)thr) {
                 tc = k;
                 ta = k + c->hold;
@@ -592,6 +605,10 @@ int64_t ora_electronics(const ora_cfg *c, uint64_t event_id, int32_t pixel, cons
             double r = (double)((float)v / (float)lsb_e);
             double code = floor(r);
             if (tie < 0 && fabs(v / lsb_e - floor(v / lsb_e + 0.5)) * lsb_e < band) tie = k;
+            if (p_tie) {
+                double p = 2.0 * band / lsb_e;
+                log_none += log1p(-(p < 1.0 ? p : 1.0 - 1e-16));
+            }
             if (code < 0) code = 0;
             if (code > adc_max) code = adc_max;
             if (nh < cap) {
@@ -609,6 +626,7 @@ int64_t ora_electronics(const ora_cfg *c, uint64_t event_id, int32_t pixel, cons
         }
     }
     if (tie_tick) *tie_tick = tie;
+    if (p_tie) *p_tie = -expm1(log_none);
     return nh;
 }
 
@@ -683,11 +701,13 @@ void ora_pixel_currents_many(const ora_cfg *c, const double *lut,
 
 /* ora_electronics of n_pix pixels: pixel pixels[i] with the current row i of
  * I and tie band band[i] (NULL: 0) writes up to cap hits to entries
- * [i cap, (i+1) cap) of the hit arrays, its hit count to n_hits[i] and its
- * first tied tick to tie_tick[i]. */
+ * [i cap, (i+1) cap) of the hit arrays, its hit count to n_hits[i], its
+ * first tied tick to tie_tick[i] and its tie probability to p_tie[i] (if
+ * non-null). */
 void ora_electronics_many(const ora_cfg *c, uint64_t event_id, int64_t n_pix, const int32_t *pixels,
                           const double *I, const double *band, int64_t cap, int32_t *t_cross, int32_t *t_adc,
-                          int32_t *adc, double *qv, int64_t *n_hits, int32_t *tie_tick, int n_threads)
+                          int32_t *adc, double *qv, int64_t *n_hits, int32_t *tie_tick, double *p_tie,
+                          int n_threads)
 {
     (void)n_threads;
 #ifdef _OPENMP
@@ -696,7 +716,8 @@ void ora_electronics_many(const ora_cfg *c, uint64_t event_id, int64_t n_pix, co
     for (int64_t i = 0; i < n_pix; ++i) {
         const size_t o = (size_t)i * (size_t)cap;
         n_hits[i] = ora_electronics(c, event_id, pixels[i], I + (size_t)i * (size_t)c->n_ticks, cap, t_cross + o,
-                                    t_adc + o, adc + o, qv + o, band ? band[i] : 0.0, tie_tick + i);
+                                    t_adc + o, adc + o, qv + o, band ? band[i] : 0.0, tie_tick + i,
+                                    p_tie ? p_tie + i : NULL);
     }
 }
 

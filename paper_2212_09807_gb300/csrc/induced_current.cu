@@ -32,7 +32,11 @@
 // A pixel's records fall on ~1000 of the 2025 bins, ~7 records per bin, so the
 // table is read from L2 once per (pixel, bin) instead of once per record.
 // Summation order is fixed (chunks in point order, bins increasing, records
-// in point order within a bin): results are bitwise reproducible.
+// in point order within a bin): results are bitwise reproducible.  A chunk's
+// records (at most kRecCap) are summed in FP32 registers and each chunk's sum
+// is added into a compensated (Kahan) running total per tick, kept in a small
+// per-CTA scratch row: a dense pixel sums ~1e6 records, whose plain FP32 sum
+// drifts by a few 1e-5 of its value; within a chunk the drift is ~5e-6.
 #include "current_records.cuh"
 
 namespace larsim {
@@ -66,6 +70,7 @@ struct CurArgs {
     DriftPar dp;
     Rec *recs;                                  // [grid][kRecCap], point order
     Rec *sorted;                                // [grid][kRecCap], bin order
+    float *tot;                                 // [grid][2][kPass]: compensated sums of a pass (total, compensation)
 };
 
 struct Smem {
@@ -175,6 +180,32 @@ __device__ __forceinline__ void apply_block(const Smem *s, int p1, int L, int la
     }
 }
 
+// tot += x with compensation c (Kahan): tot - c is the running sum to a few
+// FP32 roundings of the final value, however many partial sums are added.
+__device__ __forceinline__ void kahan_add(float &tot, float &c, float x)
+{
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(tot, y);
+    c = __fsub_rn(__fsub_rn(t, tot), y);
+    tot = t;
+}
+
+// Adds a lane's chunk sums (ticks t0 + 32 i of the pass) into the compensated
+// totals tot[t] / tot[kPass + t] (starting them on the first chunk) and clears
+// the sums.
+__device__ __forceinline__ void add_chunk(float *tot, int t0, float (&acc)[kTPL], bool first)
+{
+#pragma unroll
+    for (int i = 0; i < kTPL; ++i) {
+        const int t = t0 + 32 * i;
+        float sum = first ? 0.f : tot[t], c = first ? 0.f : tot[kPass + t];
+        kahan_add(sum, c, acc[i]);
+        tot[t] = sum;
+        tot[kPass + t] = c;
+        acc[i] = 0.f;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a)
 {
     if (a.counts[3] != 0) return;
@@ -190,6 +221,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a)
     const int npx = a.g.npx_x * a.g.npx_y;
     Rec *recs = a.recs + (size_t)blockIdx.x * kRecCap;
     Rec *sorted = a.sorted + (size_t)blockIdx.x * kRecCap;
+    float *tot = a.tot + (size_t)blockIdx.x * 2 * kPass;
     for (int i = tid; i < kQuads; i += kThreads) s->quad[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     const int blo_tick = kHalf * warp;                            // first tick of my low block
     const int bhi_tick = kPass - kHalf * (warp + 1);              // first tick of my high block
@@ -205,9 +237,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a)
         const int64_t seg0 = slot_first(a.ev, slot);
         const int e0 = a.off[pi], e1 = a.off[pi + 1];
         for (int k0 = 0; k0 < T; k0 += kPass) {
-            float acc_lo[kTPL], acc_hi[kTPL];
+            float acc_lo[kTPL], acc_hi[kTPL];               // the current chunk's records
 #pragma unroll
             for (int i = 0; i < kTPL; ++i) acc_lo[i] = acc_hi[i] = 0.f;
+            bool first_chunk = true;
             int e = e0, base = 0;                                     // generation cursor
             while (e < e1) {
                 // ---- 1. records of this chunk -------------------------------------
@@ -329,16 +362,22 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a)
                         apply_block(s, P + bhi_tick, L, lane, rc.w, rc.f, acc_hi);
                     }
                 }
+                // the chunk's sums into the compensated totals (each lane its own ticks)
+                add_chunk(tot, blo_tick + lane, acc_lo, first_chunk);
+                add_chunk(tot, bhi_tick + lane, acc_hi, first_chunk);
+                first_chunk = false;
                 __syncthreads();
             }
             float *out = a.current + (size_t)pi * T;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int kb = k0 + (h ? bhi_tick : blo_tick) + lane;
-                const float *ac = h ? acc_hi : acc_lo;
+                const int t0 = (h ? bhi_tick : blo_tick) + lane;
 #pragma unroll
-                for (int i = 0; i < kTPL; ++i)
-                    if (kb + 32 * i < T) out[kb + 32 * i] = ac[i];
+                for (int i = 0; i < kTPL; ++i) {
+                    const int k = k0 + t0 + 32 * i;
+                    const float v = first_chunk ? 0.f : __fsub_rn(tot[t0 + 32 * i], tot[kPass + t0 + 32 * i]);
+                    if (k < T) out[k] = v;
+                }
             }
         }
     }
@@ -358,7 +397,7 @@ int grid_for(int64_t pix_cap, int ctas_per_sm = 3)
 size_t current_scratch_bytes(int64_t pix_cap)
 {
     const int g = grid_for(pix_cap > 0 ? pix_cap : 1);
-    return 2 * align256((size_t)g * kRecCap * sizeof(Rec));
+    return 2 * align256((size_t)g * kRecCap * sizeof(Rec)) + align256((size_t)g * 2 * kPass * sizeof(float));
 }
 
 bool current_table_ok(int nb, int nt) { return nb * nb <= kMaxBins && ((nt + 3) / 4) * 4 <= kMaxRow; }
@@ -396,6 +435,7 @@ cudaError_t launch_induced_current(const sim_config &c, const sim_segments &s, c
     char *p = reinterpret_cast<char *>(scratch);
     a.recs = reinterpret_cast<Rec *>(p);
     a.sorted = reinterpret_cast<Rec *>(p + align256((size_t)grid * kRecCap * sizeof(Rec)));
+    a.tot = reinterpret_cast<float *>(p + 2 * align256((size_t)grid * kRecCap * sizeof(Rec)));
     const size_t smem = sizeof(Smem);
     const cudaError_t e = cudaFuncSetAttribute(k_induced_current, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem);

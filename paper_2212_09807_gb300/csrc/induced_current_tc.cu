@@ -25,8 +25,10 @@
 //    ticks; the accumulators D (16 tiles of 128 ticks x 32 pixels, FP32) live
 //    in tensor memory (all 512 columns) and are added into the FP32 currents
 //    every 64 nodes.
-//  - The im2col unfolding of every table row is built once per call in
-//    global memory (FP16/BF16, canonical no-swizzle K-major layout); for each
+//  - Each table row is rounded to FP16/BF16 once per call by error diffusion
+//    (k_round_rows: its suffix sums, hence the charge a point induces, keep
+//    their FP32 values), and the im2col unfolding of every rounded row is
+//    built in global memory (canonical no-swizzle K-major layout); for each
 //    node the CTA copies that row's unfolding (rho0 + 128 rows x 32 bytes)
 //    into shared memory with one bulk asynchronous copy, double-buffered.
 //  - Records of the unit's pixels are generated into a per-CTA buffer (a
@@ -1141,27 +1143,61 @@ __global__ void __launch_bounds__(kThreads, 1) k_induced_current_tc(TcArgs a)
     }
 }
 
-// im2col unfolding of the table rows, one 16-byte chunk (8 K values) per thread.
+// The table rows rounded to the operand type (x scale) by error diffusion, one
+// thread per row, from the last tick (the arrival, where the row peaks)
+// towards its start: each value is rounded together with the rounding error
+// carried from the ticks after it.  Every suffix sum of the rounded row then
+// equals the scaled FP32 one within half an operand ulp of a single value, so
+// the charge a point induces from any tick on to its arrival, and in
+// particular in all (the row's total), survives the rounding; independent
+// rounding of each value would let those sums drift by ~1e-5..1e-4 of their
+// value.  out: [nb2][L] operand bit patterns.
 template <int FMT>
-__global__ void k_im2col(const float *lut, int ld, int L, int nb2, int rho0, int rows, float scale,
-                         unsigned char *table)
+__global__ void k_round_rows(const float *lut, int ld, int L, int nb2, float scale, unsigned short *out)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nb2) return;
+    const float *row = lut + (size_t)n * ld;
+    unsigned short *o = out + (size_t)n * L;
+    float carry = 0.f;
+    for (int j = L - 1; j >= 0; --j) {
+        const float v = __fadd_rn(__fmul_rn(row[j], scale), carry);
+        float r;
+        unsigned short bits;
+        if (FMT == 0) {
+            const __half h = __float2half_rn(fminf(fmaxf(v, -65504.f), 65504.f));
+            r = __half2float(h);
+            bits = __half_as_ushort(h);
+        } else {
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            r = __bfloat162float(h);
+            bits = __bfloat16_as_ushort(h);
+        }
+        carry = __fsub_rn(v, r);
+        o[j] = bits;
+    }
+}
+
+// im2col unfolding of the rounded table rows, one 16-byte chunk (8 K values)
+// per thread.
+__global__ void k_im2col(const unsigned short *rtab, int L, int nb2, int rho0, int rows, unsigned char *table)
 {
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= (int64_t)nb2 * rows * 2) return;
     const int n = (int)(id / (rows * 2));
     const int rem = (int)(id - (int64_t)n * rows * 2);
     const int rho = rem >> 1, h = rem & 1;
-    float v[8];
+    uint32_t v[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
         const int j = rho - rho0 - (8 * h + e) + L - 1;
-        v[e] = (j >= 0 && j < L) ? lut[(size_t)n * ld + j] * scale : 0.f;
+        v[e] = (j >= 0 && j < L) ? (uint32_t)rtab[(size_t)n * L + j] : 0u;     // +0 in both formats
     }
     uint4 o;
-    o.x = pack2<FMT>(v[0], v[1]);
-    o.y = pack2<FMT>(v[2], v[3]);
-    o.z = pack2<FMT>(v[4], v[5]);
-    o.w = pack2<FMT>(v[6], v[7]);
+    o.x = v[0] | (v[1] << 16);
+    o.y = v[2] | (v[3] << 16);
+    o.z = v[4] | (v[5] << 16);
+    o.w = v[6] | (v[7] << 16);
     *reinterpret_cast<uint4 *>(table + (size_t)n * rows * kRowBytes + core_off(rho, 8 * h)) = o;
 }
 
@@ -1176,7 +1212,8 @@ int tc_grid()
 int rho0_of(int L) { return 16 * ((L + 126) / 16); }
 
 struct TcLayout {
-    size_t queue, table, recs, sorted, offt, bmask, pwork, nsub, pos, nslice, spos, units, order, slices, scan, total;
+    size_t queue, table, rtab, recs, sorted, offt, bmask, pwork, nsub, pos, nslice, spos, units, order, slices, scan,
+        total;
 };
 
 TcLayout tc_layout(int grid, int64_t pix_cap, int T, int units_per_sm, int rec_chunk)
@@ -1202,6 +1239,7 @@ TcLayout tc_layout(int grid, int64_t pix_cap, int T, int units_per_sm, int rec_c
     t.slices = take(sizeof(float) * (size_t)max_slices * kGroup * (size_t)T);
     t.scan = take(scan_scratch_bytes(ng));
     t.table = take((size_t)kMaxBins * kMaxRows * kRowBytes);
+    t.rtab = take((size_t)kMaxBins * 2048 * sizeof(unsigned short));     // rounded rows, nt <= 2048
     t.recs = take((size_t)grid * rec_chunk * sizeof(Rec));
     t.sorted = take((size_t)grid * rec_chunk * sizeof(Rec));
     t.offt = take((size_t)grid * kGroup * (kMaxBins + 1) * sizeof(int));
@@ -1306,8 +1344,10 @@ cudaError_t launch_induced_current_tc(const sim_config &c, const sim_segments &s
     const int64_t chunks = (int64_t)nb2 * rows * 2;
     const unsigned blocks = (unsigned)((chunks + 255) / 256);
     unsigned char *table = reinterpret_cast<unsigned char *>(p + lay.table);
-    if (fmt == 1) k_im2col<1><<<blocks, 256, 0, st>>>(r.lut, r.ld, r.nt, nb2, a.rho0, rows, rscale, table);
-    else k_im2col<0><<<blocks, 256, 0, st>>>(r.lut, r.ld, r.nt, nb2, a.rho0, rows, rscale, table);
+    unsigned short *rtab = reinterpret_cast<unsigned short *>(p + lay.rtab);
+    if (fmt == 1) k_round_rows<1><<<(nb2 + 63) / 64, 64, 0, st>>>(r.lut, r.ld, r.nt, nb2, rscale, rtab);
+    else k_round_rows<0><<<(nb2 + 63) / 64, 64, 0, st>>>(r.lut, r.ld, r.nt, nb2, rscale, rtab);
+    k_im2col<<<blocks, 256, 0, st>>>(rtab, r.nt, nb2, a.rho0, rows, table);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = sizeof(TcSmem) + 1024;

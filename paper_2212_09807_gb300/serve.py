@@ -326,11 +326,23 @@ def run_plain(cfg: dict, lut_padded, lut_nt: int, bins_per_pitch: int, requests:
     return results
 
 
+def percentile_spread(lat, q: float, n_boot: int = 2000, seed: int = 0):
+    """[5 %, 95 %] interval of the q-th percentile of ``lat`` over bootstrap
+    resamples of the requests (the spread of a percentile of a finite stream)."""
+    lat = np.asarray(lat, dtype=np.float64)
+    rng = np.random.default_rng(seed)
+    qs = np.percentile(lat[rng.integers(0, len(lat), (n_boot, len(lat)))], q, axis=1)
+    return [float(np.percentile(qs, 5)), float(np.percentile(qs, 95))]
+
+
 def summarize(results: list, t_first: float = 0.0) -> dict:
-    """p50/p99 latency (ms) overall and per kind; sustained segments/s."""
+    """p50/p99 latency (ms) overall (with the bootstrap spread of each) and per
+    kind; sustained segments/s."""
     lat = np.array([r.latency for r in results]) * 1e3
     out = {"requests": len(results), "latency_ms": {"p50": float(np.percentile(lat, 50)),
-                                                     "p99": float(np.percentile(lat, 99))}}
+                                                     "p99": float(np.percentile(lat, 99)),
+                                                     "p50_spread": percentile_spread(lat, 50),
+                                                     "p99_spread": percentile_spread(lat, 99)}}
     for kind in sorted({r.kind for r in results}):
         lk = np.array([r.latency for r in results if r.kind == kind]) * 1e3
         out[f"latency_ms_{kind}"] = {"p50": float(np.percentile(lk, 50)), "p99": float(np.percentile(lk, 99)),

@@ -133,6 +133,7 @@ def lib():
                                 cp(SimHits), _P, C.c_size_t, _P]
         L.sim_event_view_of.argtypes = [cp(SimConfig), C.c_int64, C.c_int64, C.c_int64, C.c_int64, _P,
                                         C.c_size_t, cp(SimEventView)]
+        L.sim_probe_fma.argtypes = [C.c_int64, C.c_int32, _P, cp(C.c_double), _P]
         L.sim_pixel_map_noalloc.argtypes = [cp(SimConfig), cp(SimSegments), cp(SimDrifted), cp(SimResponse),
                                             _P, _P, C.c_int64, _P, _P, _P, C.c_int64, _P, _P]
         L.sim_response_cumulative.argtypes = [cp(SimResponse), _P, _P]
@@ -160,7 +161,7 @@ def lib():
             getattr(L, f).restype = C.c_int
         for f in ("sim_workspace_size", "sim_quench_drift", "sim_pixel_map", "sim_induced_current",
                   "sim_induced_current_range", "sim_electronics", "sim_event", "sim_event_view_of",
-                  "sim_pixel_map_noalloc", "sim_response_cumulative", "sim_hit_truth_workspace_size", "sim_hit_truth", "sim_hit_points",
+                  "sim_pixel_map_noalloc", "sim_probe_fma", "sim_response_cumulative", "sim_hit_truth_workspace_size", "sim_hit_truth", "sim_hit_points",
                   "sim_track_dqdx"):
             getattr(L, f).restype = C.c_int
         sizes = (C.c_int64 * 5)()
@@ -389,6 +390,28 @@ def sim_event(cfg: SimConfig, seg: Segments, resp: Response, max_pairs: int, max
     s, r, h = seg.struct(), resp.struct(), hits.struct()
     _check(lib().sim_event(C.byref(cfg), C.byref(s), C.byref(r), int(max_pairs), int(max_pixels), C.byref(h),
                            _ptr(ws), int(ws.numel() * ws.element_size()), _stream(stream)), "sim_event")
+
+
+def fma_peak_tflops(device=None, iters: int = 4096, reps: int = 5) -> float:
+    """Measured FP32 FMA rate of the device (TFLOP/s): the best of `reps` timed
+    launches of sim_probe_fma with 8 CTAs of 256 threads per SM."""
+    import torch
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = 8 * sms
+    sink = torch.empty(blocks * 256, dtype=torch.float32, device=dev)
+    flops = C.c_double()
+    best = None
+    for r in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _check(lib().sim_probe_fma(blocks, iters, _ptr(sink), C.byref(flops), _stream(None)), "sim_probe_fma")
+        e1.record()
+        torch.cuda.synchronize()
+        if r > 0:                                  # the first launch warms up
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+    return flops.value / (best / 1e3) / 1e12
 
 
 def sim_response_cumulative(resp: Response, stream=None):
@@ -746,6 +769,77 @@ class GraphRunner:
     def replay(self):
         """Runs the captured step after the work already on the current stream (the
         inputs' copies); the current stream then waits for it."""
+        import torch
+        self.stream.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(self.stream):
+            self.graph.replay()
+        torch.cuda.current_stream().wait_stream(self.stream)
+
+
+class BatchGraphRunner:
+    """A batch of events (sim_segments with ``max_events`` slots) through
+    sim_event, captured once in a CUDA graph at fixed capacities and replayed
+    for any batch of up to ``max_events`` events and ``runner.max_segments``
+    segments.
+
+    The event offsets and ids live in device memory, so a replay reads the
+    batch that ``load`` copied into the graph's inputs: the events' columns
+    (device tensors), then inactive padding segments (zero length: no
+    charge, no pixels) up to the capacity, owned by the last slot; unused
+    slots are empty.  Every event's results are those of the same batch
+    called directly (its random numbers are keyed by its own id and
+    event-local segment index).  ``runner`` must have been built with
+    ``max_events`` slots and capacities that fit every batch it will run."""
+
+    FILL = GraphRunner.FILL
+
+    def __init__(self, runner: EventRunner, stream=None):
+        import torch
+        if runner.max_events < 1:
+            raise ValueError("the runner needs max_events >= 1 for a batch graph")
+        self.r = runner
+        dev = runner.device
+        n, E = runner.max_segments, runner.max_events
+        self.E = E
+        self.cols = {k: torch.full((n,), self.FILL[k], dtype=torch.float32, device=dev) for k in Segments.KEYS}
+        self.fill = {k: v.clone() for k, v in self.cols.items()}
+        self.offsets = torch.zeros(E + 1, dtype=torch.int64, device=dev)
+        self.offsets[-1] = n
+        self.ids = torch.zeros(E, dtype=torch.int64, device=dev)
+        self.seg = Segments(self.cols, 0, self.offsets, self.ids)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
+        self.stream.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(self.stream):
+            runner.enqueue(self.seg, self.stream)
+        self.stream.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=self.stream, capture_error_mode="thread_local"):
+            runner.enqueue(self.seg, self.stream)
+        self.stream.synchronize()
+
+    def load(self, batch: Segments):
+        """Enqueues device copies of a batch (a Segments with n_events >= 1)
+        into the graph's inputs on the current stream (copies only)."""
+        N = self.r.max_segments
+        n, e = batch.n, batch.n_events
+        if n > N or e > self.E or e < 1:
+            raise ValueError("batch outside the graph's capacities")
+        for k in Segments.KEYS:
+            if n > 0:
+                self.cols[k][:n].copy_(batch.cols[k][:n], non_blocking=True)
+            if n < N:
+                self.cols[k][n:].copy_(self.fill[k][n:], non_blocking=True)
+        self.offsets[: e + 1].copy_(batch.offsets[: e + 1], non_blocking=True)
+        if e < self.E:
+            self.offsets[e + 1:].fill_(n)
+        self.offsets[self.E:].fill_(N)                 # the padding belongs to the last slot
+        self.ids[:e].copy_(batch.ids[:e], non_blocking=True)
+        if e < self.E:
+            self.ids[e:].fill_(0)
+
+    def replay(self):
+        """Runs the captured batch after the work already on the current stream
+        (the inputs' copies); the current stream then waits for it."""
         import torch
         self.stream.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(self.stream):

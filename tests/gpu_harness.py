@@ -100,6 +100,33 @@ class Steps:
         return self.hits.to_numpy(min(n_hits, self.hit_cap))
 
 
+# Tie band (electrons) of the end-to-end hit comparison, per current form: the
+# charge error each form leaves at the front end's decisions (FP32 direct: a
+# few 1e-2 e- on the densest pixels; FP16 tensor cores: ~0.5 e-, from their
+# truncating FP32 accumulation).  Mismatches were measured at 0.05 e- (FP32)
+# and 0.5 e- (FP16) on the full-size module event and spill, none above.
+BAND = {0: 0.2, 2: 1.0}
+
+
+def tie_cap(p_ties):
+    """Largest number of tied pixels a band may cut, from the oracle's own tie
+    probabilities (p_tie of each hit pixel's trace): their expected number
+    plus four binomial standard deviations plus two."""
+    p = np.asarray(p_ties, dtype=np.float64)
+    return float(p.sum() + 4.0 * np.sqrt((p * (1.0 - p)).sum()) + 2.0)
+
+
+def prefix_charge_ok(I_gpu, I_ref, rel, floor_frac=2e-6):
+    """Every prefix sum of each pixel's current (the charge integrated by each
+    tick) within rel of the pixel's largest one plus floor_frac of the peak
+    pixel charge; returns (ok, worst relative error)."""
+    q_ref = np.cumsum(I_ref, axis=-1)
+    scale = np.abs(q_ref).max(axis=-1)
+    cum = np.abs(np.cumsum(np.asarray(I_gpu, np.float64) - I_ref, axis=-1)).max(axis=-1)
+    ok = bool(np.all(cum <= rel * scale + floor_frac * scale.max()))
+    return ok, float(np.max(cum / np.maximum(scale, 1e-300)))
+
+
 def current_errors(I_gpu, I_ref):
     """Per-pixel relative infinity-norm error and relative error of the integrated charge."""
     num = np.abs(I_gpu - I_ref).max(axis=-1)

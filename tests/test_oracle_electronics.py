@@ -7,6 +7,7 @@ hit period follow from integer arithmetic alone.
 import math
 
 import numpy as np
+import pytest
 
 import oracle
 from synth import params
@@ -110,3 +111,20 @@ def test_reset_noise_pedestal():
     # pedestal s n0 shortens the next integration by ~ s n0 / 100 ticks
     assert abs(g.mean() - 50.0) < 1.5
     assert 7.0 < g.std() < 11.0
+
+
+@pytest.mark.parametrize("current, band", [(300.0, 2.0), (60.0, 1.0)])
+def test_tie_probability_matches_tie_frequency(current, band):
+    """p_tie (the chance, under the noise model, that a trace has a decision
+    within the band) predicts how many pixels a band excludes: over 3000
+    constant-current pixels (different Philox streams) the tied fraction
+    agrees with the mean p_tie within 4 binomial standard errors."""
+    cfg = params.small_config(n_ticks=600)
+    o = oracle.Oracle(cfg, params.LUT)
+    n = 3000
+    pix = np.arange(n, dtype=np.int32) * 3
+    h = o.electronics_many(pix, np.full((n, 600), current), event_id=9, band=band)
+    tied = np.mean([x["tie_tick"] >= 0 for x in h])
+    pt = np.mean([x["p_tie"] for x in h])
+    assert 0.02 < pt < 0.5
+    assert abs(tied - pt) < 4 * np.sqrt(pt * (1 - pt) / n), (tied, pt)
