@@ -34,9 +34,9 @@ sys.path.insert(0, ROOT)
 from synth import events, params, response  # noqa: E402
 
 # kernels per step: 1 quench/drift + 14 pixel map + 6 electronics, plus the induced current:
-# 1 (FP32 direct) or 14 (tensor cores: work plan 4 + two 3-kernel scans, table rounding 1,
+# 1 (FP32 direct) or 15 (tensor cores: work plan 5 + two 3-kernel scans, table rounding 1,
 # table unfolding 1, contraction 1, reduction of split groups 1)
-KERNELS_PER_STEP = {0: 22, 1: 35, 2: 35}
+KERNELS_PER_STEP = {0: 22, 1: 36, 2: 36}
 FP32_LANES_PER_SM = 128
 
 
