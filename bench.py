@@ -317,8 +317,10 @@ def batched_vs_plain(cfg, lut, dev, n_events=256, lo=1.0e3, hi=2.0e5, n_sub=4):
     probe = fitted(cfg, s_tot, serve._caps(s_tot), [sample], max_events=ns)
     s_caps = (probe.max_pairs, probe.max_pixels, probe.hits.capacity)
     del probe
+    cands = None if int(cfg.get("precision", 0)) == 0 else [
+        dict(tc_units_per_sm=u, tc_record_chunk=c) for u in (2, 4) for c in (1 << 19, 1 << 20)]
     chosen, table = tune.autotune(cfg, lut, params.LUT["nt"], params.LUT["bins_per_pitch"], sample, s_caps,
-                                  device=dev)
+                                  reps=1, device=dev, cands=cands)
     bcfg = dict(cfg, **chosen)
     nmax = max(sg.n for sg in sub_segs)
     runner = fitted(bcfg, nmax, serve._caps(nmax), sub_segs, max_events=per)
@@ -723,6 +725,14 @@ def run_ours(args):
     lut = torch.as_tensor(lut_pad, device=dev)
     props = torch.cuda.get_device_properties(dev)
     fp32_peak = sim.fma_peak_tflops(dev)           # measured FP32 FMA rate, TFLOP/s
+    wall = {}                                      # wall seconds of each section (untimed parts included)
+    t_sec = time.perf_counter()
+
+    def lap(name):
+        nonlocal t_sec
+        now = time.perf_counter()
+        wall[name] = round(now - t_sec, 1)
+        t_sec = now
 
     # the other forms of the induced-current step, timed on the same event first (untimed for the headline)
     forms = {}
@@ -734,6 +744,7 @@ def run_ours(args):
             forms[FORMS[prec][0]] = dict(out2, steps=args.form_steps, warmup=1)
             del r2
             torch.cuda.empty_cache()
+    lap("forms")
 
     # scheduling shapes of the induced-current step for this event, picked by the autotuner (untimed);
     # results do not depend on them beyond the tensor-core forms' accumulation rounding.  A large event
@@ -751,6 +762,7 @@ def run_ours(args):
         cfg = dict(cfg, **tuned)
         del segs_dev
         torch.cuda.empty_cache()
+    lap("tune")
 
     if pg:
         pg.barrier()
@@ -764,6 +776,7 @@ def run_ours(args):
     run, per, head, info = timed_event(cfg, seg, lut, dev, args.precision, args.steps, args.warmup,
                                        replica_event_id(rank), fp32_peak)
     clocks = clk.stop()
+    lap("headline")
     n_pairs, n_pix, n_hits, samples, step_ms = (info[k] for k in ("n_pairs", "n_pix", "n_hits", "samples",
                                                                    "step_ms"))
     total_ms = max_over_ranks(float(step_ms.sum()), pg, dev)
@@ -783,7 +796,7 @@ def run_ours(args):
         pg.barrier()
     t0 = time.perf_counter()
     h2d = d2h = 0
-    e2e_steps = max(2, args.steps // 2)
+    e2e_steps = max(2, min(4, args.steps))
     for _ in range(e2e_steps):
         _, _, hb, db = io.simulate(host, S, replica_event_id(rank))
         h2d, d2h = hb, db
@@ -793,6 +806,7 @@ def run_ours(args):
            "d2h_bytes_per_step": d2h, "steps": e2e_steps}
     del run, io
     torch.cuda.empty_cache()
+    lap("e2e")
 
     # the one-module interaction beside the headline, with the steps after the front end on its hits
     module = None
@@ -810,21 +824,26 @@ def run_ours(args):
         post = post_hit_steps(mrun, mcfg, dev) if not args.no_post else None
         del mrun
         torch.cuda.empty_cache()
+    lap("module_event")
     light_res = light_path(dev) if not args.no_light else None
     torch.cuda.empty_cache()
+    lap("light")
 
     bcfg = params.module_config(precision=args.precision)
     blut = torch.as_tensor(response.pad_rows(response.lut_for(bcfg, params.LUT)), device=dev)
     batched = (batched_vs_plain(bcfg, blut, dev, args.batched_events, 1.0e3, args.batched_hi,
                                 args.batched_subbatches) if not args.no_batched else None)
+    lap("batched")
     loads = tuple(float(x) for x in args.serving_loads.split(",") if x)
     serving = serving_vs_plain(args.precision, dev, args.serving_requests, loads) if not args.no_serving else None
+    lap("serving")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         lut_or = lut_pad[..., :L].astype(np.float64)
         est, threads, sdesc = oracle_sample(cfg, seg, lut_or, np.random.default_rng(0), n_pix=args.cpu_pixels)
         cpu = {"value": S / est, "unit": "segments/s", "cores": threads, "kind": "oracle", "sample": sdesc}
+    lap("cpu_baseline")
 
     if rank == 0:
         print(json.dumps({
@@ -847,6 +866,7 @@ def run_ours(args):
             "forms": forms, "module_event": module, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,
             "serving": serving, "after_front_end": post, "light": light_res,
             "gpu_launches": KERNELS_PER_STEP[args.precision] * args.steps, "clocks": clocks,
+            "section_wall_s": wall,
         }))
     if pg:
         pg.destroy_process_group()
