@@ -47,9 +47,9 @@
  * floating-point values (which drift volume a segment belongs to, how many
  * points it is cut into) are taken in FP64 from the FP32 inputs with plain
  * IEEE operations in the order written here; the electronics' threshold and
- * ADC decisions round their FP64 operands to FP32 first (the precision the
- * GPU kernels decide in).  Where a decision lies within a stated band of its
- * threshold, the oracle reports it so that tests can exclude that tie.
+ * ADC decisions are taken in FP64.  Where a decision lies within a stated band
+ * of its threshold, the oracle reports it so that tests can exclude that tie
+ * (the band then also covers a device's FP32 decisions).
  */
 #include <math.h>
 #include <stdint.h>
@@ -551,7 +551,9 @@ void ora_pixel_current(const ora_cfg *c, const double *lut,
  *   optional periodic reset (period > 0, idle, k % period == 0, k > 0):
  *     q = s_reset n0 of counter (pixel, k, 4, 0) before the tick's current.
  * A digitisation still pending at the end of the window is dropped.
- * Threshold and ADC decisions compare FP32 roundings of the FP64 operands.
+ * Threshold and ADC decisions are taken in FP64 (a device that decides in
+ * FP32 can differ only where v lies within its FP32 rounding of the decision
+ * point, i.e. inside the tie band).
  * ``tie_tick`` receives the first tick whose decision lies within ``band``
  * electrons of its threshold (or -1).  ``p_tie`` (if non-null) receives the
  * probability, under the noise model, that some decision of this trace lies
@@ -593,7 +595,7 @@ int64_t ora_electronics(const ora_cfg *c, uint64_t event_id, int32_t pixel, cons
                 double p = 2.0 * band * exp(-0.5 * z * z) / (sd * sqrt(2.0 * ORA_PI));
                 log_none += log1p(-(p < 1.0 ? p : 1.0 - 1e-16));
             }
-            if ((float)v >= (float)thr) {
+            if (v >= thr) {
                 tc = k;
                 ta = k + c->hold;
                 if (last_adc + c->min_int > ta) ta = last_adc + c->min_int;
@@ -602,8 +604,7 @@ int64_t ora_electronics(const ora_cfg *c, uint64_t event_id, int32_t pixel, cons
         }
         if (!idle && k == ta) {
             double v = q + c->s_unc * n[0];
-            double r = (double)((float)v / (float)lsb_e);
-            double code = floor(r);
+            double code = floor(v / lsb_e);
             if (tie < 0 && fabs(v / lsb_e - floor(v / lsb_e + 0.5)) * lsb_e < band) tie = k;
             if (p_tie) {
                 double p = 2.0 * band / lsb_e;
