@@ -180,14 +180,15 @@ def measured_peaks():
         return {}
 
 
-def stored_traffic(kernel_file: str):
-    """DRAM bytes per launch from a committed ncu summary, if taken on this exact source."""
+def stored_traffic(kernel_file: str, workload_key: str):
+    """DRAM bytes per launch from a committed ncu summary of this kernel on this
+    workload (entry "<file>@<workload>"), if taken on this exact source."""
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
     except OSError:
         return None
     src = open(os.path.join(ROOT, "paper_2212_09807_gb300", "csrc", kernel_file), "rb").read()
-    ent = t.get(kernel_file)
+    ent = t.get(f"{kernel_file}@{workload_key}")
     if not ent or ent.get("src_sha256") != hashlib.sha256(src).hexdigest():
         return None
     return ent.get("dram_bytes_per_launch_full")
@@ -598,7 +599,7 @@ def light_path(dev, names=("module", "spill"), reps=5):
     return out
 
 
-def form_roofline(run, cfg, precision, a4_s, fp32_peak, dev):
+def form_roofline(run, cfg, precision, a4_s, fp32_peak, dev, wl_key=""):
     """Roofline of the induced-current kernel of one form.  FP32 direct:
     against the measured FP32 FMA rate (sim_probe_fma), work 2 flop per (point,
     pixel within the table's reach, table tick).  Tensor-core forms: against
@@ -619,7 +620,7 @@ def form_roofline(run, cfg, precision, a4_s, fp32_peak, dev):
     per_point = w_alg / a4_s / 1e12
     if precision == 0:
         return {"bound": "alu", "achieved": per_point, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": per_point / fp32_peak, "traffic": stored_traffic("induced_current.cu"),
+                "frac": per_point / fp32_peak, "traffic": stored_traffic("induced_current.cu", wl_key),
                 "kernel": "k_induced_current",
                 "peak_note": "FP32 FMA rate measured on this GPU by sim_probe_fma (independent FMA chains), "
                              "of measured",
@@ -630,7 +631,7 @@ def form_roofline(run, cfg, precision, a4_s, fp32_peak, dev):
     useful = 2.0 * nnz * L / a4_s / 1e12
     tpk = measured_peaks().get("bf16_tflops_sustained") or 1700.0
     return {"bound": "tensor", "achieved": useful, "peak": tpk, "unit": "TFLOP/s", "frac": useful / tpk,
-            "traffic": stored_traffic("induced_current_tc.cu"), "kernel": "k_induced_current_tc",
+            "traffic": stored_traffic("induced_current_tc.cu", wl_key), "kernel": "k_induced_current_tc",
             "nnz_charge_cells": nnz, "mma_per_launch": n_mma,
             "dense_achieved": dense, "dense_frac": dense / tpk, "per_point_achieved": per_point,
             "peak_note": "measured dense bf16 sustained (kernel timed inside a step), of measured; fp16 has the "
@@ -689,13 +690,13 @@ def serving_vs_plain(precision, dev, n_requests=12, loads=(0.5, 0.7, 0.9), seed_
             "hbm_budget_gb": 120, "slice_pixels": SLICE, "loads": out}
 
 
-def timed_event(cfg, seg, lut, dev, precision, steps, warmup, event_id, fp32_peak):
+def timed_event(cfg, seg, lut, dev, precision, steps, warmup, event_id, fp32_peak, wl_key=""):
     """time_form plus the derived per-step numbers and the kernel roofline."""
     run, per, (n_pairs, n_pix, n_hits, _) = time_form(cfg, seg, lut, dev, precision, steps, warmup, event_id)
     S, T = len(seg["x0"]), int(cfg["n_ticks"])
     step_ms = per.sum(axis=1)
     rl, samples = form_roofline(run, dict(cfg, precision=precision), precision, float(per[:, 2].mean()) / 1e3,
-                                fp32_peak, dev)
+                                fp32_peak, dev, wl_key)
     out = {"dtype": FORMS[precision][1], "ms_per_step": float(step_ms.mean()),
            "segments_per_s": S / (float(step_ms.mean()) / 1e3), "induced_current_ms": float(per[:, 2].mean()),
            "roofline": rl}
@@ -740,7 +741,8 @@ def run_ours(args):
         for prec in (0, 1, 2):
             if prec == args.precision:
                 continue
-            r2, _, out2, _ = timed_event(cfg, seg, lut, dev, prec, args.form_steps, 1, rank, fp32_peak)
+            r2, _, out2, _ = timed_event(cfg, seg, lut, dev, prec, args.form_steps, 1, rank, fp32_peak,
+                                         desc.split(":")[0])
             forms[FORMS[prec][0]] = dict(out2, steps=args.form_steps, warmup=1)
             del r2
             torch.cuda.empty_cache()
@@ -774,7 +776,7 @@ def run_ours(args):
     clk.start()
     time.sleep(0.15)
     run, per, head, info = timed_event(cfg, seg, lut, dev, args.precision, args.steps, args.warmup,
-                                       replica_event_id(rank), fp32_peak)
+                                       replica_event_id(rank), fp32_peak, desc.split(":")[0])
     clocks = clk.stop()
     lap("headline")
     n_pairs, n_pix, n_hits, samples, step_ms = (info[k] for k in ("n_pairs", "n_pix", "n_hits", "samples",
@@ -816,7 +818,7 @@ def run_ours(args):
         mcfg["precision"] = args.precision
         mlut = torch.as_tensor(response.pad_rows(response.lut_for(mcfg, params.LUT)), device=dev)
         mrun, mper, mout, minfo = timed_event(mcfg, mseg, mlut, dev, args.precision, 10, 3, replica_event_id(rank),
-                                              fp32_peak)
+                                              fp32_peak, mdesc.split(":")[0])
         module = dict(mout, workload=mdesc, segments=minfo["S"], active_pixels=minfo["n_pix"],
                       hits=minfo["n_hits"], steps=10, warmup=3, scheduling="defaults",
                       step_breakdown_ms={k: float(mper[:, i].mean()) for i, k in
