@@ -102,9 +102,10 @@ typedef struct sim_config {
     /* scheduling shapes of the induced-current step (results do not depend on
      * them beyond the tensor-core forms' accumulation rounding; 0 = default):
      * tensor-core forms: target work units per SM of the work plan (1..16,
-     * default 2) and records per CTA chunk (a power of two, 4096..1048576,
-     * default 262144; the workspace holds two record buffers of 32 bytes per
-     * record and CTA); FP32 direct form: resident CTAs per SM (1..3, default 3).
+     * default 2) and records per CTA chunk (a power of two, 4096..1048576;
+     * default 1048576 for calls sized for at least 131072 active pixels, else
+     * 262144; the workspace holds two record buffers of 32 bytes per record
+     * and CTA); FP32 direct form: resident CTAs per SM (1..3, default 3).
      * paper_2212_09807_gb300/tune.py picks them by timing a sample. */
     int32_t tc_units_per_sm, tc_record_chunk, direct_ctas_per_sm;
     /* polls of a bounded device-side wait of the tensor-core forms before it

@@ -66,7 +66,14 @@ constexpr int kSlots = 16;                  // blocks per operand batch
 constexpr int kMaxBins = 2048;              // nb * nb <= kMaxBins
 constexpr int kMaxRows = 2304;              // im2col rows: rho0 + 128 for nt <= 2048
 constexpr int kRowBytes = 32;               // 16 FP16 per im2col row
-constexpr int kRecDefault = 1 << 18;       // records per chunk per CTA unless configured (at most 2^20)
+// records per chunk per CTA unless configured (at most 2^20): 2^20 for calls
+// sized for at least 2^17 active pixels (a large event touches each node with
+// several chunks' worth of records: shorter chunks issue the same (node,
+// block) MMAs once per chunk, 1.7x the MMAs of the 35-module spill at 2^18),
+// else 2^18 (a smaller workspace: two buffers of 32-byte records per CTA)
+constexpr int kRecDefault = 1 << 18, kRecDefaultLarge = 1 << 20;
+constexpr int64_t kLargeCall = 1 << 17;
+inline int default_chunk(int64_t pix_cap) { return pix_cap >= kLargeCall ? kRecDefaultLarge : kRecDefault; }
 constexpr int kSubsPerSm = 2;               // work-balanced units per SM (target), unless tuned
 constexpr int kMaxSplit = 16;               // table-node ranges a pixel group may be cut into
 #ifndef LARSIM_TC_FLUSH_NODES
@@ -1323,7 +1330,7 @@ TcLayout tc_layout(int grid, int64_t pix_cap, int T, int units_per_sm, int rec_c
 size_t current_tc_scratch_bytes(int64_t pix_cap, int T, int units_per_sm, int rec_chunk)
 {
     return tc_layout(tc_grid(), pix_cap > 0 ? pix_cap : 1, T, units_per_sm > 0 ? units_per_sm : kSubsPerSm,
-                     rec_chunk > 0 ? rec_chunk : kRecDefault)
+                     rec_chunk > 0 ? rec_chunk : default_chunk(pix_cap > 0 ? pix_cap : 1))
         .total;
 }
 
@@ -1343,7 +1350,7 @@ cudaError_t launch_induced_current_tc(const sim_config &c, const sim_segments &s
     const int fmt = c.precision == 1 ? 1 : 0;      // 1: BF16, 2: FP16
     const int grid = tc_grid();
     const int units_per_sm = c.tc_units_per_sm > 0 ? c.tc_units_per_sm : kSubsPerSm;
-    const int rec_chunk = c.tc_record_chunk > 0 ? c.tc_record_chunk : kRecDefault;
+    const int rec_chunk = c.tc_record_chunk > 0 ? c.tc_record_chunk : default_chunk(pix_cap);
     const TcLayout lay = tc_layout(grid, pix_cap, c.n_ticks, units_per_sm, rec_chunk);
     char *p = reinterpret_cast<char *>(scratch);
     TcArgs a;
