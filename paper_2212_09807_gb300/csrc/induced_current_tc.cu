@@ -13,10 +13,12 @@
 // b0 + c.  Cut the arrival ticks into blocks of 16 (ab) and the output ticks
 // into tiles of 128 (t): for one node and one block the contribution to one
 // tile is a matrix product
-//   D_t[r, p] += sum_{a' < 16} Im[128 t - 16 ab + rho0 + r, a'] Q[p, 16 ab + a']
-// with Im[rho, a'] = R[node, rho - rho0 - a' + L - 1] (zero outside the row),
-// the im2col (Toeplitz) unfolding of the row: M = 128 ticks, N = 32 pixels,
-// K = 16 arrival ticks.
+//   D_t[m', p] += sum_{a' < 16} A[m', a'] Q[p, 16 ab + a'],
+//   A[m', a'] = R[node, 128 t + 127 - m' - 16 ab - a' + L - 1]
+// (zero outside the row; m' = 127 - (tick - 128 t): the accumulator rows run
+// backwards in a tile), a Toeplitz block of the row: M = 128 ticks, N = 32
+// pixels, K = 16 arrival ticks.  A depends on 16 ab - 128 t + m' + a' only,
+// so all the A tiles of a node are views of one buffer (k_phase_table).
 //
 // Design: one CTA of 256 threads per SM (persistent, dynamic unit queue).
 //  - A unit is a group of 32 active pixels, or for a heavy group a range of
@@ -27,10 +29,12 @@
 //    every 64 nodes.
 //  - Each table row is rounded to FP16/BF16 once per call by error diffusion
 //    (k_round_rows: its suffix sums, hence the charge a point induces, keep
-//    their FP32 values), and the im2col unfolding of every rounded row is
-//    built in global memory (canonical no-swizzle K-major layout); for each
-//    node the CTA copies that row's unfolding (rho0 + 128 rows x 32 bytes)
-//    into shared memory with one bulk asynchronous copy, double-buffered.
+//    their FP32 values) and laid out as its phase table (k_phase_table: 8
+//    shifted copies of the row interleaved in 16-byte rows, 35 KB per node,
+//    every A tile a no-swizzle K-major view with overlapping core matrices);
+//    the 72 MB of phase tables stay in L2.  For each node the CTA copies its
+//    phase table into shared memory with one bulk asynchronous copy,
+//    double-buffered.
 //  - Records of the unit's pixels are generated into a per-CTA buffer (a
 //    pixel's segments 128 at a time, their candidate points walked together)
 //    and sorted per pixel by table bin (counting sort).  A node receives the
@@ -42,7 +46,7 @@
 //  - Issuer warps 0-3 (one thread each) own tick tiles t = w, w + 4, ... and
 //    issue the MMAs of each batch slot by slot; tcgen05.commit on mbarriers
 //    returns the operand buffers.  Warps 0-3 read D back (tcgen05.ld,
-//    lane = tick) at each flush.
+//    lane = 127 - tick within the tile) at each flush.
 // Every mbarrier wait is bounded; a wait that gives up sets
 // SIM_STATUS_TIMEOUT in the status word and the CTA drains and returns.
 #include <algorithm>
@@ -64,8 +68,11 @@ constexpr int kPassTicks = kTileM * kTiles; // ticks per pass
 constexpr int kBlk = 16;                    // arrival ticks per block (MMA K)
 constexpr int kSlots = 16;                  // blocks per operand batch
 constexpr int kMaxBins = 2048;              // nb * nb <= kMaxBins
-constexpr int kMaxRows = 2304;              // im2col rows: rho0 + 128 for nt <= 2048
-constexpr int kRowBytes = 32;               // 16 FP16 per im2col row
+// Phase table of a node's row (see k_phase_table): 128-byte blocks of 8 rows
+// of 8 operand values; (nt + 126) / 8 + 18 blocks, at most 289 for nt <= 2048.
+constexpr int kMaxPhaseBlocks = 290;
+constexpr int kMaxIm = kMaxPhaseBlocks * 128;
+__host__ __device__ constexpr int phase_blocks(int L) { return (L + 126) / 8 + 18; }
 // records per chunk per CTA unless configured (at most 2^20): 2^20 for calls
 // sized for at least 2^17 active pixels (a large event touches each node with
 // several chunks' worth of records: shorter chunks issue the same (node,
@@ -98,7 +105,7 @@ struct __align__(16) BatchMeta {
 };
 
 struct __align__(1024) TcSmem {
-    unsigned char im[2][kMaxRows * kRowBytes];
+    unsigned char im[2][kMaxIm];
     unsigned char bst[2][kSlots * 1024];
     union {
         struct {
@@ -144,7 +151,7 @@ struct TcArgs {
     uint32_t idesc;
     float qscale;                           // fixed point -> operand units
     float out_scale;                        // accumulator -> current (1 / table scale)
-    const unsigned char *table;             // im2col unfolding, [nb*nb][im_bytes]
+    const unsigned char *table;             // phase tables of the rows, [nb*nb][im_bytes]
     const Anchor *anch;
     const int32_t *active, *off, *segs;
     const int32_t *perm;                    // active-pixel index of each position in patch order
@@ -821,8 +828,10 @@ __device__ void issue_mmas(const TcArgs &a, TcSmem *s, int w, const unsigned sho
             last = s->meta[st].last;
             const uint4 bw = *reinterpret_cast<const uint4 *>(s->meta[st].blk);
             const uint32_t b4[4] = {bw.x, bw.y, bw.z, bw.w};
-            // descriptors advance by address >> 4: one im2col row is 32 bytes, one slot 1024
-            const uint64_t ad0 = smem_desc(im0, 128, 256), bd0 = smem_desc(saddr(s->bst[st]), 128, 256);
+            // descriptors advance by address >> 4: A (the node's phase table) by 16 bytes per unit
+            // of `base`, B by 1024 bytes per slot.  A's core matrices: 128 bytes apart in both K
+            // and M (they overlap: the Toeplitz structure), rows 16 bytes apart.
+            const uint64_t ad0 = smem_desc(im0, 128, 128), bd0 = smem_desc(saddr(s->bst[st]), 128, 256);
             tc_fence_after();
             uint32_t issued = 0;
             // slot-major: consecutive MMAs go to different accumulator tiles (a short N = 32 MMA
@@ -831,12 +840,12 @@ __device__ void issue_mmas(const TcArgs &a, TcSmem *s, int w, const unsigned sho
 #pragma unroll
             for (int i = 0; i < kSlots; ++i) {
                 if (i >= count) break;
-                const int boff = a.rho0 - kBlk * (int)((b4[i >> 2] >> (8 * (i & 3))) & 0xffu);
+                const int boff = kBlk * (int)((b4[i >> 2] >> (8 * (i & 3))) & 0xffu);
 #pragma unroll
                 for (int t = w; t < kTiles; t += kIssuers) {
-                    const int arow = kTileM * t + boff;            // A row of this block in tile t
-                    if (k0 + kTileM * t < T && arow >= 0 && arow <= a.rho0) {   // else the A tile is all zero
-                        mma_f16(tm + (uint32_t)(kGroup * t), ad0 + (uint64_t)(2 * arow), bd0 + (uint64_t)(64 * i),
+                    const int base = boff - kTileM * t;            // A tile of this block in tile t
+                    if (k0 + kTileM * t < T && base >= 0 && base <= a.rho0) {   // else the A tile is all zero
+                        mma_f16(tm + (uint32_t)(kGroup * t), ad0 + (uint64_t)base, bd0 + (uint64_t)(64 * i),
                                 a.idesc);
                         ++issued;
                     }
@@ -1049,7 +1058,7 @@ __device__ void flush_acc(const TcArgs &a, TcSmem *s, uint32_t tm, uint32_t &flu
         const uint32_t ta = tm + ((uint32_t)(32 * warp) << 16) + kGroup * t;
         float v[32];
         tmem_ld32(ta, v);
-        const int tick = tick0 + 32 * warp + lane;
+        const int tick = tick0 + (kTileM - 1) - (32 * warp + lane);   // accumulator rows run backwards in a tile
         if (ok && tick < T) {
             float *base = rows + tick;
             if (!first) {
@@ -1254,19 +1263,27 @@ __global__ void k_round_rows(const float *lut, int ld, int L, int nb2, float sca
     }
 }
 
-// im2col unfolding of the rounded table rows, one 16-byte chunk (8 K values)
-// per thread.
-__global__ void k_im2col(const unsigned short *rtab, int L, int nb2, int rho0, int rows, unsigned char *table)
+// Phase table of each rounded row, the A operands of all its MMAs in one
+// buffer.  An MMA of block ab in tile t multiplies
+//   A[m', a'] = R[128 t + 127 - m' - 16 ab - a' + L - 1]
+// (m' = 127 - (tick - 128 t): accumulator rows run backwards in a tile) with
+// the charge Q[p][16 ab + a'].  Writing S[x] = R[L + 126 - x] (zero outside
+// the row), A[m', a'] = S[base + m' + a'], base = 16 ab - 128 t: constant
+// along anti-diagonals, so 8 rows of 8 values B[q][phi][e] = S[8 q + phi + e]
+// (phi, e < 8) per 128-byte block q hold every operand: the core matrix
+// (m' / 8, a' / 8) starts at block base / 8 + m' / 8 + a' / 8, its row phi
+// 16 bytes further.  One thread per 16-byte row; rtab: [nb2][L] operand bits.
+__global__ void k_phase_table(const unsigned short *rtab, int L, int nb2, int nq, unsigned char *table)
 {
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= (int64_t)nb2 * rows * 2) return;
-    const int n = (int)(id / (rows * 2));
-    const int rem = (int)(id - (int64_t)n * rows * 2);
-    const int rho = rem >> 1, h = rem & 1;
+    if (id >= (int64_t)nb2 * nq * 8) return;
+    const int n = (int)(id / (nq * 8));
+    const int rem = (int)(id - (int64_t)n * nq * 8);
+    const int q = rem >> 3, phi = rem & 7;
     uint32_t v[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-        const int j = rho - rho0 - (8 * h + e) + L - 1;
+        const int j = L + 126 - (8 * q + phi + e);
         v[e] = (j >= 0 && j < L) ? (uint32_t)rtab[(size_t)n * L + j] : 0u;     // +0 in both formats
     }
     uint4 o;
@@ -1274,7 +1291,7 @@ __global__ void k_im2col(const unsigned short *rtab, int L, int nb2, int rho0, i
     o.y = v[2] | (v[3] << 16);
     o.z = v[4] | (v[5] << 16);
     o.w = v[6] | (v[7] << 16);
-    *reinterpret_cast<uint4 *>(table + (size_t)n * rows * kRowBytes + core_off(rho, 8 * h)) = o;
+    *reinterpret_cast<uint4 *>(table + (size_t)n * nq * 128 + (size_t)rem * 16) = o;
 }
 
 int tc_grid()
@@ -1315,7 +1332,7 @@ TcLayout tc_layout(int grid, int64_t pix_cap, int T, int units_per_sm, int rec_c
     const int64_t max_slices = std::min<int64_t>(2 * (int64_t)units_per_sm * grid, ng * kMaxSplit);
     t.slices = take(sizeof(float) * (size_t)max_slices * kGroup * (size_t)T);
     t.scan = take(scan_scratch_bytes(ng));
-    t.table = take((size_t)kMaxBins * kMaxRows * kRowBytes);
+    t.table = take((size_t)kMaxBins * kMaxIm);
     t.rtab = take((size_t)kMaxBins * 2048 * sizeof(unsigned short));     // rounded rows, nt <= 2048
     t.recs = take((size_t)grid * rec_chunk * sizeof(Rec));
     t.sorted = take((size_t)grid * rec_chunk * sizeof(Rec));
@@ -1358,9 +1375,9 @@ cudaError_t launch_induced_current_tc(const sim_config &c, const sim_segments &s
     a.nb = r.nb;
     a.nt = r.nt;
     a.bpp = r.bins_per_pitch;
-    a.rho0 = rho0_of(r.nt);
-    const int rows = a.rho0 + kTileM;
-    a.im_bytes = rows * kRowBytes;
+    a.rho0 = rho0_of(r.nt);                         // the largest base of an MMA with a nonzero A tile
+    const int nq = phase_blocks(r.nt);
+    a.im_bytes = nq * 128;
     a.idesc = instr_desc(fmt, kTileM, kGroup);
     const float rscale = fmt == 0 ? 32768.f : 1.f, qunit = fmt == 0 ? 4.f : 1.f;
     a.qscale = 1.f / (kFix * qunit);
@@ -1422,13 +1439,13 @@ cudaError_t launch_induced_current_tc(const sim_config &c, const sim_segments &s
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int nb2 = r.nb * r.nb;
-    const int64_t chunks = (int64_t)nb2 * rows * 2;
+    const int64_t chunks = (int64_t)nb2 * nq * 8;
     const unsigned blocks = (unsigned)((chunks + 255) / 256);
     unsigned char *table = reinterpret_cast<unsigned char *>(p + lay.table);
     unsigned short *rtab = reinterpret_cast<unsigned short *>(p + lay.rtab);
     if (fmt == 1) k_round_rows<1><<<(nb2 + 63) / 64, 64, 0, st>>>(r.lut, r.ld, r.nt, nb2, rscale, rtab);
     else k_round_rows<0><<<(nb2 + 63) / 64, 64, 0, st>>>(r.lut, r.ld, r.nt, nb2, rscale, rtab);
-    k_im2col<<<blocks, 256, 0, st>>>(rtab, r.nt, nb2, a.rho0, rows, table);
+    k_phase_table<<<blocks, 256, 0, st>>>(rtab, r.nt, nb2, nq, table);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = sizeof(TcSmem) + 1024;
