@@ -40,7 +40,7 @@
 //    and sorted per pixel by table bin (counting sort).  A node receives the
 //    records of four bins (its corners) of each pixel.
 //  - Builder warps 4-7 share a node's records evenly and turn them into
-//    charge tiles Q[16 blocks][16 ticks][32 pixels], accumulated with integer
+//    charge tiles Q[32 blocks][16 ticks][32 pixels], accumulated with integer
 //    atomics in fixed point (order-independent, so the result is bitwise
 //    reproducible), then converted to FP16/BF16 operand tiles.
 //  - Issuer warps 0-3 (one thread each) own tick tiles t = w, w + 4, ... and
@@ -66,7 +66,12 @@ constexpr int kTileM = 128;                 // ticks per accumulator tile (MMA M
 constexpr int kTiles = 16;                  // tiles in tensor memory
 constexpr int kPassTicks = kTileM * kTiles; // ticks per pass
 constexpr int kBlk = 16;                    // arrival ticks per block (MMA K)
-constexpr int kSlots = 16;                  // blocks per operand batch
+#ifndef LARSIM_TC_SLOTS
+#define LARSIM_TC_SLOTS 32
+#endif
+constexpr int kSlots = LARSIM_TC_SLOTS;     // blocks per operand batch (a power of two, 16 or 32)
+constexpr int kSlotShift = kSlots == 32 ? 5 : 4;
+static_assert(kSlots == 16 || kSlots == 32, "operand batches of 16 or 32 blocks");
 constexpr int kMaxBins = 2048;              // nb * nb <= kMaxBins
 // Phase table of a node's row (see k_phase_table): 128-byte blocks of 8 rows
 // of 8 operand values; (nt + 126) / 8 + 18 blocks, at most 289 for nt <= 2048.
@@ -643,7 +648,7 @@ __device__ __forceinline__ void accum_recs(TcSmem *s, const int4 (&h)[U], const 
             const int rb = rel >> 4;
             if (val == 0.f || rb < 0 || rb >= 256) continue;
             const int rank = s->rank_of[rb];    // the tap's block is present: its records set it
-            if ((rank >> 4) != kb) continue;
+            if ((rank >> kSlotShift) != kb) continue;
             atomicAdd(&s->u.acc[((rank & (kSlots - 1)) * kBlk + (rel & (kBlk - 1))) * kGroup + px[j]],
                       __float2int_rn(val * kFix));
         }
@@ -826,8 +831,12 @@ __device__ void issue_mmas(const TcArgs &a, TcSmem *s, int w, const unsigned sho
             if (!bar_wait(s, &s->full_b[st], (q >> 1) & 1)) return;
             const int count = s->meta[st].count;
             last = s->meta[st].last;
-            const uint4 bw = *reinterpret_cast<const uint4 *>(s->meta[st].blk);
-            const uint32_t b4[4] = {bw.x, bw.y, bw.z, bw.w};
+            uint32_t b4[kSlots / 4];                          // the slots' blocks, four per word
+#pragma unroll
+            for (int i = 0; i < kSlots / 16; ++i) {
+                const uint4 bw = reinterpret_cast<const uint4 *>(s->meta[st].blk)[i];
+                b4[4 * i] = bw.x, b4[4 * i + 1] = bw.y, b4[4 * i + 2] = bw.z, b4[4 * i + 3] = bw.w;
+            }
             // descriptors advance by address >> 4: A (the node's phase table) by 16 bytes per unit
             // of `base`, B by 1024 bytes per slot.  A's core matrices: 128 bytes apart in both K
             // and M (they overlap: the Toeplitz structure), rows 16 bytes apart.
