@@ -94,7 +94,11 @@ constexpr int kMaxSplit = 16;               // table-node ranges a pixel group m
 constexpr int kFlushNodes = LARSIM_TC_FLUSH_NODES;   // nodes per accumulation window (see flush_acc)
 constexpr float kFix = 4096.f;              // fixed-point scale of the charge accumulators (2^-12 e-)
 constexpr int kIssuers = 4;
-constexpr int kPairs = 128;                 // (pixel, segment) pairs loaded together by the generation
+#ifndef LARSIM_TC_PAIRS
+#define LARSIM_TC_PAIRS 128
+#endif
+constexpr int kPairs = LARSIM_TC_PAIRS;     // (pixel, segment) pairs loaded together by the generation (<= 256)
+static_assert(kPairs <= 256 && (kPairs & (kPairs - 1)) == 0, "one pair per generation thread, a power of two");
 #ifndef LARSIM_TC_PATCH_ROWS
 #define LARSIM_TC_PATCH_ROWS 8
 #define LARSIM_TC_PATCH_COLS 4
@@ -667,7 +671,7 @@ __device__ void build_batches(const TcArgs &a, TcSmem *s, const Rec *sorted, con
                               const unsigned short *nodes, int nn, uint32_t &q, unsigned long long &n_cells)
 {
 #ifndef LARSIM_TC_RECS_IN_FLIGHT
-#define LARSIM_TC_RECS_IN_FLIGHT 8
+#define LARSIM_TC_RECS_IN_FLIGHT 4
 #endif
     constexpr int U = LARSIM_TC_RECS_IN_FLIGHT;         // records in flight per thread
     const int bt = threadIdx.x - 128, lane = bt & 31, cw = bt >> 5;
