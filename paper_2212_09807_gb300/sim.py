@@ -392,16 +392,17 @@ def sim_event(cfg: SimConfig, seg: Segments, resp: Response, max_pairs: int, max
                            _ptr(ws), int(ws.numel() * ws.element_size()), _stream(stream)), "sim_event")
 
 
-def fma_peak_tflops(device=None, iters: int = 4096, reps: int = 5) -> float:
-    """Measured FP32 FMA rate of the device (TFLOP/s): the best of `reps` timed
-    launches of sim_probe_fma with 8 CTAs of 256 threads per SM."""
+def fma_peak_tflops(device=None, iters: int = 16384, reps: int = 7) -> float:
+    """Measured FP32 FMA rate of the device (TFLOP/s): the median of `reps`
+    timed launches (~16 ms each) of sim_probe_fma with 8 CTAs of 256 threads
+    per SM, after one untimed launch."""
     import torch
     dev = torch.device("cuda") if device is None else torch.device(device)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     blocks = 8 * sms
     sink = torch.empty(blocks * 256, dtype=torch.float32, device=dev)
     flops = C.c_double()
-    best = None
+    times = []
     for r in range(reps + 1):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -409,9 +410,8 @@ def fma_peak_tflops(device=None, iters: int = 4096, reps: int = 5) -> float:
         e1.record()
         torch.cuda.synchronize()
         if r > 0:                                  # the first launch warms up
-            ms = e0.elapsed_time(e1)
-            best = ms if best is None else min(best, ms)
-    return flops.value / (best / 1e3) / 1e12
+            times.append(e0.elapsed_time(e1))
+    return flops.value / (float(np.median(times)) / 1e3) / 1e12
 
 
 def sim_response_cumulative(resp: Response, stream=None):
