@@ -60,7 +60,12 @@ namespace larsim {
 
 namespace {
 
-constexpr int kThreads = 256;
+#ifndef LARSIM_TC_BUILDERS
+#define LARSIM_TC_BUILDERS 128
+#endif
+constexpr int kBuilders = LARSIM_TC_BUILDERS;   // builder threads (warps 4 ..): 128 or 256
+static_assert(kBuilders == 128 || kBuilders == 256, "four or eight builder warps");
+constexpr int kThreads = 128 + kBuilders;   // warps 0-3 issue and flush, the rest build
 constexpr int kGroup = 32;                  // pixels per group (MMA N)
 constexpr int kTileM = 128;                 // ticks per accumulator tile (MMA M)
 constexpr int kTiles = 16;                  // tiles in tensor memory
@@ -135,7 +140,7 @@ struct __align__(1024) TcSmem {
     uint32_t taddr;
     uint32_t blkmask[8];
     unsigned char rank_of[256], blk_of[256];    // a node's present arrival blocks: block -> rank -> block
-    int lst_beg[128], lst_off[128], lst_wsum[4];
+    int lst_beg[128], lst_off[128], lst_wsum[8];
     int pin[kGroup];
     long long rowoff[kGroup];               // output row of each pixel slot (elements from the unit's base)
     int n_nodes, group, abort, spin;
@@ -269,7 +274,7 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void builders_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void builders_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kBuilders) : "memory"); }
 
 // Barrier of the builder threads that also returns whether any of them saw
 // the abort flag (a uniform decision: no builder is left waiting at a barrier).
@@ -277,10 +282,10 @@ __device__ __forceinline__ bool builders_any_abort(TcSmem *s)
 {
     const int mine = *(volatile int *)&s->abort;
     int any;
-    asm volatile("{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.or.pred q, 1, 128, p;\n"
+    asm volatile("{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n"
                  " selp.s32 %0, 1, 0, q;\n}\n"
                  : "=r"(any)
-                 : "r"(mine)
+                 : "r"(mine), "n"(kBuilders)
                  : "memory");
     return any != 0;
 }
@@ -541,7 +546,7 @@ __device__ int gen_chunk(const TcArgs &a, TcSmem *s, GenState &st, int64_t pi0, 
         __syncthreads();
         if (nrec > start) {
             // bin offsets of this pixel's part, node flags, scatter cursors
-            constexpr int kB = kMaxBins / kThreads;
+            constexpr int kB = (kMaxBins + kThreads - 1) / kThreads;
             int v[kB], sv = 0;
 #pragma unroll
             for (int i = 0; i < kB; ++i) {
@@ -659,9 +664,10 @@ __device__ __forceinline__ void accum_recs(TcSmem *s, const int4 (&h)[U], const 
     }
 }
 
-// Builder threads (warps 4-7, bt = 0..127).  For each node the 128 record
-// lists (corner c = bt / 32 of pixel bt % 32: the pixel's records in bin
-// node - c) are concatenated and the builders share the records evenly; the
+// Builder threads (warps 4 .., bt = 0 .. kBuilders - 1).  For each node the 128
+// record lists (corner c = bt / 32 of pixel bt % 32, held by builders bt <
+// 128: the pixel's records in bin node - c) are concatenated and all the
+// builders share the records evenly; the
 // charge of each (block, tick, pixel) cell is summed with integer atomics, so
 // the order does not matter.  Publishes each node's operand batches in order.
 // Control flow is uniform across the builders (their named barriers); after
@@ -675,16 +681,18 @@ __device__ void build_batches(const TcArgs &a, TcSmem *s, const Rec *sorted, con
 #endif
     constexpr int U = LARSIM_TC_RECS_IN_FLIGHT;         // records in flight per thread
     const int bt = threadIdx.x - 128, lane = bt & 31, cw = bt >> 5;
+    const bool owner = bt < 128;                        // holds one of the node's 128 lists
     const int nb = a.nb;
     // the charge tiles share shared memory with the generation's histogram: zero them once
     // here; afterwards the conversion clears every cell it reads
-    for (int i = bt; i < kSlots * kBlk * kGroup / 4; i += 128)
+    for (int i = bt; i < kSlots * kBlk * kGroup / 4; i += kBuilders)
         reinterpret_cast<int4 *>(s->u.acc)[i] = make_int4(0, 0, 0, 0);
     // a node's list bounds and block masks are loaded one node ahead (unconditionally: the
     // indexes stay inside this CTA's offset and mask buffers; unused values are discarded)
     auto fetch = [&](int n, int &b, int &beg, int &end, uint4 &mk0, uint4 &mk1) {
         const int nx = n / nb, ny = n - nx * nb;
-        const int bx = nx - (cw & 1), by = ny - (cw >> 1);
+        const int c = cw & 3;                           // non-owners fetch a copy of an owner's list
+        const int bx = nx - (c & 1), by = ny - (c >> 1);
         b = (bx >= 0 && by >= 0) ? bx * nb + by : 0;
         const int *orow = offt + (size_t)lane * (kMaxBins + 1);
         beg = orow[b];
@@ -696,7 +704,7 @@ __device__ void build_batches(const TcArgs &a, TcSmem *s, const Rec *sorted, con
     int fb = 0, fbeg = 0, fend = 0;
     uint4 fm0 = make_uint4(0u, 0u, 0u, 0u), fm1 = fm0;
     if (nn > 0) fetch(nodes[0], fb, fbeg, fend, fm0, fm1);
-    const bool pin = s->pin[lane] != 0;
+    const bool pin = owner && s->pin[lane] != 0;
     for (int u = 0; u < nn; ++u) {
         if (builders_any_abort(s)) return;
         const int n = nodes[u];
@@ -714,7 +722,7 @@ __device__ void build_batches(const TcArgs &a, TcSmem *s, const Rec *sorted, con
             const int y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
-        if (lane == 31) s->lst_wsum[cw] = x;
+        if (lane == 31 && owner) s->lst_wsum[cw] = x;
         if (bt < 8) s->blkmask[bt] = 0;
         builders_sync();
         {
@@ -731,11 +739,13 @@ __device__ void build_batches(const TcArgs &a, TcSmem *s, const Rec *sorted, con
             pre += (w2 < cw) ? s->lst_wsum[w2] : 0;
             R += s->lst_wsum[w2];
         }
-        s->lst_beg[bt] = beg;
-        s->lst_off[bt] = pre + x - len;
+        if (owner) {
+            s->lst_beg[bt] = beg;
+            s->lst_off[bt] = pre + x - len;
+        }
         builders_sync();
         // each builder takes a contiguous slice of the concatenated lists
-        const int k_lo = (R * bt) >> 7, k_hi = (R * (bt + 1)) >> 7;
+        const int k_lo = (int)(((long long)R * bt) / kBuilders), k_hi = (int)(((long long)R * (bt + 1)) / kBuilders);
         const int L_lo = k_lo < k_hi ? find_list(s->lst_off, k_lo) : 0;
         // the first U records of the slice stay in registers for all of the node's batches
         // (most slices are that short); longer slices reload the rest in each batch
@@ -745,10 +755,10 @@ __device__ void build_batches(const TcArgs &a, TcSmem *s, const Rec *sorted, con
         int L2c = L_lo;
         load_recs<U>(s, sorted, k_lo, k_hi, L2c, hc, wc, pc);
         // rank of each present arrival block (its order, hence its batch and slot) and the
-        // inverse, in shared memory: two blocks per builder
+        // inverse, in shared memory: 256 / kBuilders blocks per builder
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int b = bt + 128 * i, wd = b >> 5;
+        for (int i = 0; i < 256 / kBuilders; ++i) {
+            const int b = bt + kBuilders * i, wd = b >> 5;
             const uint32_t wm = s->blkmask[wd];
             if ((wm >> (b & 31)) & 1u) {
                 int r = __popc(wm & ((1u << (b & 31)) - 1u));
@@ -779,7 +789,7 @@ __device__ void build_batches(const TcArgs &a, TcSmem *s, const Rec *sorted, con
             const int count = min(kSlots, nblk - kb * kSlots);
             unsigned char *dst = s->bst[st];
             // one 16-byte core-matrix row (8 ticks of one pixel) per step
-            for (int j = bt; j < count * kGroup * 2; j += 128) {
+            for (int j = bt; j < count * kGroup * 2; j += kBuilders) {
                 const int sl = j >> 6, p = j & (kGroup - 1), h = (j >> 5) & 1;
                 int *ac = s->u.acc + (sl * kBlk + 8 * h) * kGroup + p;
                 int c8[8];
@@ -1170,7 +1180,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_induced_current_tc(TcArgs a)
                 uint32_t *bmask = a.bmask + (size_t)blockIdx.x * kGroup * kMaxBins * 8;
                 const int nrec = gen_chunk(a, s, st, pi0, npg, bx_lo, bx_hi, recs, sorted, offt, bmask, k0);
                 {
-                    constexpr int kB = kMaxBins / kThreads;
+                    constexpr int kB = (kMaxBins + kThreads - 1) / kThreads;
                     int fl[kB], sf = 0;
 #pragma unroll
                     for (int i = 0; i < kB; ++i) {
