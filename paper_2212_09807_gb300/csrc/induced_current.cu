@@ -1,64 +1,84 @@
 // induced_current.cu -- step 4 of the charge path (arXiv:2212.09807
-// Sec. 3.3.2): the current induced on each active pixel in each tick,
+// Sec. 3.3.2), FP32 form on the CUDA cores: the current induced on each
+// active pixel in each tick,
 //   I[p, k] = sum_s sum_mu sum_nu q_s Rt(x_mu + dx - x_p, y_mu + dy - y_p, k - a),
 // Eq. (current) with the charge density rho of N points x M perturbations
 // per segment, summed over the segments mapped to the pixel (the per-pixel
 // sum of Sec. 3.4).  Each term reads the table bilinearly at the folded
-// offset (four rows b0 = (bx, by), (bx+1, by), (bx, by+1), (bx+1, by+1)) and
-// linearly at the fractional arrival tick:
-//   v(j) = sum_c w_c R[b_c][j],   I[k] += (1 - f) v(k - A + L - 1) + f v(k - A + L - 2)
-// (w_c include the point charge q = Q_a / (N M)).
+// offset (four table nodes around the point's bin) and linearly at the
+// fractional arrival tick: a point record (arrival A + f, bin b0, q-scaled
+// corner weights w_c; current_records.cuh) deposits the charge (1 - f) w_c at
+// tick A and f w_c at tick A + 1 of node b0 + c.  With Q[p, n, a] the charge
+// so binned per (pixel, node, arrival tick),
+//   I[p, k] = sum_n sum_a Q[p, n, a] R[n, k - a + L - 1]
+// -- the same terms regrouped per node: a pixel's records fall on ~1200 of
+// the 2025 nodes, ~4.5 nonzero cells per 16-tick block of a node, so
+// collecting the charge first costs one FMA per nonzero cell and table tick
+// instead of eight per record and tick.
 //
-// Design: one CTA of 256 threads per active pixel (grid-stride, three CTAs per
-// SM), output stationary: 2048 ticks per pass.  Warp w owns a low block of
-// 128 ticks (128 w ..) and its mirror (2048 - 128 (w + 1) ..); in each block
-// lane l owns ticks l, 32 + l, 64 + l, 96 + l, in registers.  A record's ticks
-// form one interval, which for drifting charge usually starts at the window
-// start, so pairing each low block with a high one keeps the warps evenly
-// loaded while warps skip the blocks a record does not reach.
-//  1. records: the CTA regenerates every perturbed point of the pixel's
-//     segments (Philox keyed by segment and point), keeps those within the
-//     table's reach of this pixel as records {A, b0, f, w[4]} in its scratch
-//     slice (point order), with their bins and a bin histogram in shared memory;
-//  2. stable counting sort by bin (one warp computes destinations with
-//     match_any ranks from the bins in shared memory; the CTA moves the records);
-//  3. per distinct bin: the four table rows are staged once in shared memory
-//     (read one bin ahead into registers), interleaved so that each position
-//     holds the four corner values as one 16-byte quad, with zero quads beyond
-//     both ends of the row.  A record then costs a lane one 16-byte shared
-//     read and a 4-term dot product per tick for v(j); v(j - 1) is the
-//     neighbouring lane's v(j) (warp shuffle).  Consecutive lanes read
-//     consecutive quads: no bank conflicts.
-// A pixel's records fall on ~1000 of the 2025 bins, ~7 records per bin, so the
-// table is read from L2 once per (pixel, bin) instead of once per record.
-// Summation order is fixed (chunks in point order, bins increasing, records
-// in point order within a bin): results are bitwise reproducible.  A chunk's
-// records (at most kRecCap) are summed in FP32 registers and each chunk's sum
-// is added into a compensated (Kahan) running total per tick, kept in a small
-// per-CTA scratch row: a dense pixel sums ~1e6 records, whose plain FP32 sum
-// drifts by a few 1e-5 of its value; within a chunk the drift is ~5e-6.
+// Design: one CTA of 128 threads per active pixel (dynamic queue, pixels of
+// the most candidate points first; three CTAs per SM), output stationary:
+// thread t holds 16 consecutive ticks of a 2032-tick pass in registers.
+//  1. records: the pixel's segments are taken 128 at a time (one thread
+//     loads each anchor) and their candidate points walked 128 per step
+//     (Philox keyed by segment and point); those within the table's reach of
+//     the pixel become records in a per-CTA scratch buffer, with a bin
+//     histogram in shared memory; a chunk holds at most kRecCap records;
+//  2. the chunk is scattered into bin order and the table nodes its bins
+//     reach are listed;
+//  3. node loop, pipelined over two barriers per node: the charge of node
+//     n + 1 is deposited into fixed-point cells (integer shared-memory
+//     atomics: order-independent, so the result is bitwise reproducible; the
+//     scale, a power of two, follows the node's entries and the chunk's
+//     largest weight, so that taps round to ~1e-9 of the node's charge)
+//     and its table row staged, while node n is applied: for each present
+//     16-tick arrival block every thread loads the 31 table values its 16
+//     ticks need (eight 16-byte shared reads; 4 words of padding after every
+//     16 keep consecutive threads' windows conflict-free) and adds
+//     q_d R[.] for each nonzero cell d (a CTA-uniform branch).
+// Per tick the terms are summed in a fixed order (chunks in point order,
+// nodes increasing, blocks increasing, cells increasing) in FP32, and every
+// kKahanNodes nodes the partial sums are added into compensated (Kahan)
+// totals in registers: a dense pixel sums ~3e5 cells per tick, whose plain
+// FP32 sum would drift by ~1e-5 of its value.  A pixel's current depends on
+// its own segments only: the same bits alone, in a batch or in any range of
+// a call.
 #include "current_records.cuh"
 
 namespace larsim {
 
 namespace {
-constexpr int kThreads = 256;
+constexpr int kThreads = 128;
 constexpr int kWarps = kThreads / 32;
-constexpr int kTPL = 4;                         // consecutive ticks per lane and block
-constexpr int kHalf = 32 * kTPL;                // ticks per block
-constexpr int kPass = 2 * kThreads * kTPL;      // ticks per pass (two blocks per warp)
-constexpr int kRecCap = 8192;                   // records per chunk (per-CTA scratch)
+constexpr int kTPT = 16;                        // consecutive ticks per thread
+constexpr int kSpan = kThreads * kTPT;          // ticks the threads hold
+constexpr int kPass = kSpan - kTPT;             // ticks per pass (see tick_shift)
+constexpr int kBlk = 16;                        // arrival ticks per block
+constexpr int kBlocks = 256;                    // blocks of a pass: relative arrival ticks [0, 4096)
+constexpr int kRecCap = 65536;                  // records per chunk (per-CTA scratch; ~1 chunk per pixel)
 constexpr int kMaxBins = 2048;                  // nb * nb <= kMaxBins
-constexpr int kMaxRow = 2048;                   // staged row length (>= nt rounded to 4)
-constexpr int kEdge = kHalf + 8;                // zero quads before position 0 and after L - 1
-constexpr int kQuads = kMaxRow + 2 * kEdge;     // staged quads (position p at p + kEdge)
-constexpr int kPosPerThread = kMaxRow / kThreads;   // positions staged per thread
+constexpr int kMaxRow = 2048;                   // table length nt <= kMaxRow
+constexpr int kSegBatch = 128;                  // segments loaded together by the generation
+constexpr int kKahanNodes = 8;                  // nodes per plain FP32 partial sum
+// Staged table row: value j at position p = j + kEdge, word address
+// p + 4 (p / 16) (4 words of padding after every 16).  Thread t holds the
+// pass ticks 16 t - sigma + i (i < 16), sigma = L mod 16, so that its
+// 32-value window of block bl starts at j0 = 16 (t - bl) + L - 16 - sigma, a
+// multiple of 16; windows that touch the row have j0 in [-30, L - 1], so
+// positions [2, L + kEdge + 31) are read; those outside [kEdge, kEdge + L)
+// hold zero.  The threads hold ticks [-sigma, kSpan - sigma) of the pass:
+// a pass writes its first kPass ticks.
+constexpr int kEdge = 32;
+constexpr int kRowPos = kMaxRow + kEdge + 48;
+constexpr int kRowWords = kRowPos + kRowPos / 4 + 4;
+
+__device__ __forceinline__ int row_word(int p) { return p + 4 * (p >> 4); }
+__host__ __device__ constexpr int tick_shift(int L) { return L & 15; }
 
 struct CurArgs {
     sim_config c;
     const float *lut;
-    int nb, nt, ld, bpp, lp;                    // lp = nt rounded up to 4
-    float inv_nb;
+    int nb, nt, ld, bpp;
     const Anchor *anch;
     const int32_t *active, *off, *segs;
     const int64_t *counts;
@@ -68,21 +88,35 @@ struct CurArgs {
     EventInfo ev;
     Geo g;
     DriftPar dp;
+    int *queue;                                 // next entry of `order`
+    const int32_t *order;                       // pixel (relative to pix_begin) of each queue entry
     Rec *recs;                                  // [grid][kRecCap], point order
     Rec *sorted;                                // [grid][kRecCap], bin order
-    float *tot;                                 // [grid][2][kPass]: compensated sums of a pass (total, compensation)
 };
 
-struct Smem {
-    float4 quad[kQuads];                        // (R00, R10, R01, R11) at each table position
-    int hist[kMaxBins];                         // bin counts, then scatter cursors
-    unsigned short glist[kMaxBins];             // bins present, increasing
-    unsigned short gstart[kMaxBins + 1];        // start of each present bin in bin order
-    unsigned short rbin[kRecCap];               // bin of record i, then its destination
-    int warp_n[kWarps];
+struct __align__(16) Smem {
+    float row[2][kRowWords];                    // staged table rows of two nodes
+    union {
+        int cell[2][kBlocks * kBlk];            // charge cells of two nodes (fixed point, then FP32 in place)
+        struct {
+            Anchor anc[kSegBatch];              // a batch of the pixel's segments
+            int sg[kSegBatch];
+            int coff[kSegBatch + 1];            // candidate offsets of the batch
+        } g;
+    } u;
+    int hist[kMaxBins + 1];                     // bin counts; after the scatter, the end of each bin
+    unsigned char nflag[kMaxBins];
+    unsigned short nodes[kMaxBins];
+    uint32_t mask[3][kBlocks / 32];             // arrival blocks present, per node (three in flight)
     int scan_tmp[kWarps + 1];
-    int n_groups;
+    int warp_n[kWarps];
+    int n_nodes;
+    int item;
+    int wmax;                                   // largest record weight of the chunk (FP32 bits)
+    int emax;
 };
+
+static_assert(sizeof(Smem) <= 75 * 1024, "three CTAs per SM");
 
 // Exclusive scan of one int per thread across the CTA; returns the prefix
 // and the total in *tot.
@@ -115,71 +149,6 @@ __device__ __forceinline__ int block_scan(int v, Smem *s, int *tot)
     return r;
 }
 
-// Table row of corner c of bin b0; corners outside the table read row b0
-// (their weight is zero).  b0 / nb is formed in FP32: exact, since
-// (b0 + 1/2) / nb stays >= 1/(2 nb) away from an integer.
-__device__ __forceinline__ const float *corner_row(const CurArgs &a, int b0, int c)
-{
-    const int bx = (int)(((float)b0 + 0.5f) * a.inv_nb), by = b0 - bx * a.nb;
-    const int dx = c & 1, dy = c >> 1;
-    const int row = (bx + dx < a.nb && by + dy < a.nb) ? b0 + dx * a.nb + dy : b0;
-    return a.lut + (size_t)row * a.ld;
-}
-
-// Thread t stages positions t + 256 i (i < 8) of the four rows: coalesced
-// 4-byte global reads into registers, one bin ahead.
-struct RowRegs {
-    float v[4][kPosPerThread];
-};
-
-__device__ __forceinline__ void load_rows(const CurArgs &a, int b0, RowRegs &r)
-{
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const float *row = corner_row(a, b0, c);
-#pragma unroll
-        for (int i = 0; i < kPosPerThread; ++i) {
-            const int j = threadIdx.x + kThreads * i;
-            r.v[c][i] = (j < a.nt) ? __ldg(row + j) : 0.f;
-        }
-    }
-}
-
-__device__ __forceinline__ void store_rows(Smem *s, const RowRegs &r)
-{
-#pragma unroll
-    for (int i = 0; i < kPosPerThread; ++i)
-        s->quad[threadIdx.x + kThreads * i + kEdge] = make_float4(r.v[0][i], r.v[1][i], r.v[2][i], r.v[3][i]);
-}
-
-__device__ __forceinline__ float dot4(const float4 &w, const float4 &q)
-{
-    return w.x * q.x + w.y * q.y + w.z * q.z + w.w * q.w;
-}
-
-// One record on one block of a warp.  p1 is the position of v(j) at the
-// block's first tick; lane l at iteration i handles tick 32 i + l, reading
-// v(j) at p1 + 32 i + l and taking v(j - 1) from lane l - 1 (lane 0: from
-// lane 31 of the previous iteration, or read directly at i = 0).
-__device__ __forceinline__ void apply_block(const Smem *s, int p1, int L, int lane, const float4 &w, float f,
-                                            float (&acc)[kTPL])
-{
-    if (p1 + kHalf - 1 < 0 || p1 - 1 > L - 1) return;     // block outside the row
-    const float4 *q = s->quad + kEdge + p1 + lane;
-    float carry = 0.f;
-    if (lane == 0) carry = dot4(w, q[-1]);
-    const float g = 1.f - f;
-#pragma unroll
-    for (int i = 0; i < kTPL; ++i) {
-        const float v = dot4(w, q[32 * i]);
-        float vm = __shfl_up_sync(0xffffffffu, v, 1);
-        if (lane == 0) vm = carry;
-        carry = __shfl_sync(0xffffffffu, v, 31);
-        acc[i] = fmaf(g, v, acc[i]);
-        acc[i] = fmaf(f, vm, acc[i]);
-    }
-}
-
 // tot += x with compensation c (Kahan): tot - c is the running sum to a few
 // FP32 roundings of the final value, however many partial sums are added.
 __device__ __forceinline__ void kahan_add(float &tot, float &c, float x)
@@ -190,197 +159,449 @@ __device__ __forceinline__ void kahan_add(float &tot, float &c, float x)
     tot = t;
 }
 
-// Adds a lane's chunk sums (ticks t0 + 32 i of the pass) into the compensated
-// totals tot[t] / tot[kPass + t] (starting them on the first chunk) and clears
-// the sums.
-__device__ __forceinline__ void add_chunk(float *tot, int t0, float (&acc)[kTPL], bool first)
+// Generation cursor of a pixel's records: next segment batch and the
+// candidate offset within it where the previous chunk stopped.
+struct GenState {
+    int e;
+    int c0;
+};
+
+// Records of the pixel (centre (ix, iy)) from its segments [st.e, e1), in
+// point order, into recs, with the bin histogram in s->hist.  Stops when
+// the next step of 128 candidates would overflow the chunk (st keeps the
+// place) or after the last segment (st.e = e1).  Returns the records.
+__device__ int gen_chunk(const CurArgs &a, Smem *s, GenState &st, int e1, int ix, int iy, uint64_t key,
+                         int64_t seg0, Rec *recs)
 {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int M = a.c.mc_per_sample;
+    const float clip = a.c.diff_clip_sigma, fbpp = (float)a.bpp;
+    int nrec = 0;
+    while (st.e < e1) {
+        const int nbat = min(kSegBatch, e1 - st.e);
+        int cnt = 0;
+        if (tid < nbat) {
+            const int sg = a.segs[st.e + tid];
+            const Anchor A = a.anch[sg];
+            s->u.g.anc[tid] = A;
+            s->u.g.sg[tid] = sg;
+            cnt = A.N * M;
+        }
+        int C;
+        const int pre = block_scan(cnt, s, &C);
+        if (tid < nbat) s->u.g.coff[tid] = pre;
+        if (tid == 0) s->u.g.coff[nbat] = C;
+        __syncthreads();
+        for (int c = st.c0; c < C; c += kThreads) {
+            const int cc = c + tid;
+            bool ok = false;
+            Rec r;
+            if (cc < C) {
+                int lo = 0;                                  // last j with coff[j] <= cc
 #pragma unroll
-    for (int i = 0; i < kTPL; ++i) {
-        const int t = t0 + 32 * i;
-        float sum = first ? 0.f : tot[t], c = first ? 0.f : tot[kPass + t];
-        kahan_add(sum, c, acc[i]);
-        tot[t] = sum;
-        tot[kPass + t] = c;
-        acc[i] = 0.f;
+                for (int step = kSegBatch / 2; step > 0; step >>= 1)
+                    if (lo + step < nbat && s->u.g.coff[lo + step] <= cc) lo += step;
+                const Anchor &A = s->u.g.anc[lo];
+                const float cx = (float)(ix - A.ix_ref) + 0.5f, cy = (float)(iy - A.iy_ref) + 0.5f;
+                const PointPos pp = point_position(A, cc - s->u.g.coff[lo], M, key,
+                                                   (uint32_t)(s->u.g.sg[lo] - seg0), clip, a.dp);
+                ok = point_record(A, pp, cx, cy, fbpp, a.nb, a.c.nearest_lut, r);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, ok);
+            if (lane == 0) s->warp_n[warp] = __popc(m);
+            __syncthreads();
+            int wb = 0, nq = 0;
+#pragma unroll
+            for (int w2 = 0; w2 < kWarps; ++w2) {
+                const int c2 = s->warp_n[w2];
+                wb += (w2 < warp) ? c2 : 0;
+                nq += c2;
+            }
+            if (nrec + nq > kRecCap) {           // chunk full: process it, then redo this step
+                st.c0 = c;
+                __syncthreads();
+                return nrec;
+            }
+            if (ok) {
+                recs[nrec + wb + __popc(m & ((1u << lane) - 1u))] = r;
+                atomicAdd(&s->hist[r.b0], 1);
+            }
+            // weights are >= 0: their FP32 bits order as integers
+            const int wb_max = __reduce_max_sync(
+                0xffffffffu, ok ? __float_as_int(fmaxf(fmaxf(r.w.x, r.w.y), fmaxf(r.w.z, r.w.w))) : 0);
+            if (lane == 0 && wb_max > 0) atomicMax(&s->wmax, wb_max);
+            nrec += nq;
+            __syncthreads();                     // warp_n reused by the next step
+        }
+        st.e += nbat;
+        st.c0 = 0;
+        __syncthreads();                         // the batch area is reloaded
+    }
+    return nrec;
+}
+
+// Thread t's share of a table row: elements 4 t + 512 i (i < 4) as 16-byte
+// loads (rows are 16-byte aligned; elements at or beyond L read as zero).
+struct RowRegs {
+    float4 v[4];
+};
+
+__device__ __forceinline__ void load_row(const CurArgs &a, int n, RowRegs &r)
+{
+    const float *row = a.lut + (size_t)n * a.ld;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int j = 4 * threadIdx.x + 512 * i;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j < a.nt) v = __ldg(reinterpret_cast<const float4 *>(row + j));
+        if (j + 1 >= a.nt) v.y = 0.f;
+        if (j + 2 >= a.nt) v.z = 0.f;
+        if (j + 3 >= a.nt) v.w = 0.f;
+        r.v[i] = v;
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a)
+__device__ __forceinline__ void store_row(float *dst, const RowRegs &r)
 {
-    if (a.counts[3] != 0) return;
-    const int64_t npix = min(a.counts[1], a.pix_end);
-    if (a.counts[1] > a.pix_cap) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem *s = reinterpret_cast<Smem *>(smem_raw);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)      // four values inside one 16-position group: one 16-byte store
+        *reinterpret_cast<float4 *>(dst + row_word(4 * threadIdx.x + 512 * i + kEdge)) = r.v[i];
+}
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int T = a.c.n_ticks, L = a.nt, M = a.c.mc_per_sample, nb2 = a.nb * a.nb;
-    const float clip = a.c.diff_clip_sigma;
-    const float fbpp = (float)a.bpp;
-    const int npx = a.g.npx_x * a.g.npx_y;
-    Rec *recs = a.recs + (size_t)blockIdx.x * kRecCap;
-    Rec *sorted = a.sorted + (size_t)blockIdx.x * kRecCap;
-    float *tot = a.tot + (size_t)blockIdx.x * 2 * kPass;
-    for (int i = tid; i < kQuads; i += kThreads) s->quad[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int blo_tick = kHalf * warp;                            // first tick of my low block
-    const int bhi_tick = kPass - kHalf * (warp + 1);              // first tick of my high block
+// The four record lists of node n (corner c of the bins (nx - (c & 1),
+// ny - (c >> 1))) in bin order: begin of each and prefix counts.
+struct NodeLists {
+    int beg[4];
+    int pre[5];
+};
 
-    for (int64_t pi = a.pix_begin + blockIdx.x; pi < npix; pi += gridDim.x) {
-        const int32_t pid = a.active[pi];
-        const int an = pid / npx;
-        const int rem = pid - an * npx;
-        const int iy = rem / a.g.npx_x, ix = rem - iy * a.g.npx_x;
-        // event of this (virtual) pixel: key and first segment of its slot
-        const int slot = an / a.g.n_anodes;
-        const uint64_t key = slot_key(a.seed, a.ev, slot);
-        const int64_t seg0 = slot_first(a.ev, slot);
-        const int e0 = a.off[pi], e1 = a.off[pi + 1];
-        for (int k0 = 0; k0 < T; k0 += kPass) {
-            float acc_lo[kTPL], acc_hi[kTPL];               // the current chunk's records
+__device__ __forceinline__ NodeLists node_lists(const Smem *s, int n, int nb)
+{
+    NodeLists L;
+    const int nx = n / nb, ny = n - nx * nb;
+    L.pre[0] = 0;
 #pragma unroll
-            for (int i = 0; i < kTPL; ++i) acc_lo[i] = acc_hi[i] = 0.f;
-            bool first_chunk = true;
-            int e = e0, base = 0;                                     // generation cursor
-            while (e < e1) {
-                // ---- 1. records of this chunk -------------------------------------
-                for (int b = tid; b < nb2; b += kThreads) s->hist[b] = 0;
-                __syncthreads();
-                int nrec = 0;
-                while (e < e1) {
-                    const int sg = a.segs[e];
-                    const Anchor A = a.anch[sg];
-                    const int total = A.N * M;
-                    if (base >= total) {
-                        ++e;
-                        base = 0;
-                        continue;
-                    }
-                    const float cx = (float)(ix - A.ix_ref) + 0.5f;
-                    const float cy = (float)(iy - A.iy_ref) + 0.5f;
-                    const int idx = base + tid;
-                    bool ok = false;
-                    Rec r;
-                    if (idx < total) {
-                        const PointPos pp = point_position(A, idx, M, key, (uint32_t)(sg - seg0), clip, a.dp);
-                        ok = point_record(A, pp, cx, cy, fbpp, a.nb, a.c.nearest_lut, r);
-                    }
-                    const unsigned m = __ballot_sync(0xffffffffu, ok);
-                    if (lane == 0) s->warp_n[warp] = __popc(m);
-                    __syncthreads();
-                    int wb = 0, nq = 0;
+    for (int c = 0; c < 4; ++c) {
+        const int bx = nx - (c & 1), by = ny - (c >> 1);
+        int b = 0, e = 0;
+        if (bx >= 0 && by >= 0) {
+            const int bin = bx * nb + by;
+            b = bin > 0 ? s->hist[bin - 1] : 0;
+            e = s->hist[bin];
+        }
+        L.beg[c] = b;
+        L.pre[c + 1] = L.pre[c] + (e - b);
+    }
+    return L;
+}
+
+// Record and corner of entry e of a node's concatenated lists.
+__device__ __forceinline__ void node_entry(const NodeLists &L, const Rec *sorted, int e, Rec &r, int &c)
+{
+    c = (e >= L.pre[1]) + (e >= L.pre[2]) + (e >= L.pre[3]);
+    // selects, not a runtime index (which would place the lists in local memory)
+    const int b = c == 0 ? L.beg[0] : c == 1 ? L.beg[1] : c == 2 ? L.beg[2] : L.beg[3];
+    const int p = c == 0 ? L.pre[0] : c == 1 ? L.pre[1] : c == 2 ? L.pre[2] : L.pre[3];
+    r = sorted[b + (e - p)];
+}
+
+// Fixed-point scale of a node's charge cells: 2^k with k the largest keeping
+// n_entries x wmax (a bound of every cell: each entry adds at most one tap of
+// at most wmax to a cell) below 2^30, so no cell overflows and a tap is
+// rounded to ~n_entries wmax 2^-30.  A power of two: converting back is exact.
+// Deterministic: a count and a maximum.
+__device__ __forceinline__ float node_scale(int n_entries, float wmax)
+{
+    const float x = (float)n_entries * wmax;
+    if (!(x > 0.f)) return 1.f;
+    const int ex = ((__float_as_int(x) >> 23) & 0xff) - 127;      // floor(log2 x) (x normal)
+    const int k = min(100, max(-100, 29 - ex));
+    return __int_as_float((k + 127) << 23);
+}
+
+// Deposits the two ticks of a record's corner c into the fixed-point cells.
+__device__ __forceinline__ void deposit(int *cell, uint32_t *mask, const Rec &r, int c, int k0, float scale)
+{
+    const float w = c == 0 ? r.w.x : c == 1 ? r.w.y : c == 2 ? r.w.z : r.w.w;
+    uint32_t bits[2] = {0u, 0u};
+    int word[2] = {0, 0};
 #pragma unroll
-                    for (int w2 = 0; w2 < kWarps; ++w2) {
-                        const int c2 = s->warp_n[w2];
-                        wb += (w2 < warp) ? c2 : 0;
-                        nq += c2;
-                    }
-                    __syncthreads();
-                    if (nrec + nq > kRecCap) break;      // chunk full: process it, then redo this batch
-                    if (ok) {
-                        const int slot = nrec + wb + __popc(m & ((1u << lane) - 1u));
-                        recs[slot] = r;
-                        s->rbin[slot] = (unsigned short)r.b0;
-                        atomicAdd(&s->hist[r.b0], 1);
-                    }
-                    nrec += nq;
-                    base += kThreads;
-                }
-                __syncthreads();
-                if (nrec == 0) continue;
-                // ---- 2. bin offsets, bin list, stable move to bin order -----------
-                {
-                    constexpr int kB = kMaxBins / kThreads;
-                    int v[kB], fl[kB], sv = 0, sf = 0;
+    for (int tap = 0; tap < 2; ++tap) {
+        const float val = tap ? r.f * w : (1.f - r.f) * w;
+        const int rel = r.A - k0 + tap;
+        if (val == 0.f || rel < 0 || rel >= kBlocks * kBlk) continue;
+        atomicAdd(cell + rel, __float2int_rn(val * scale));
+        word[tap] = rel >> 9;
+        bits[tap] = 1u << ((rel >> 4) & 31);
+    }
+    if (bits[0] && bits[1] && word[0] == word[1]) {
+        atomicOr(mask + word[0], bits[0] | bits[1]);
+    } else {
+        if (bits[0]) atomicOr(mask + word[0], bits[0]);
+        if (bits[1]) atomicOr(mask + word[1], bits[1]);
+    }
+}
+
+// Node applied to a thread's 16 ticks: for each present block bl, the table
+// window W[m] = R[j0 + m] (m < 32, j0 = 16 (t - bl) + L - 16 - sigma) and the
+// block's cells q_d: the thread's tick i gains q_d R[j0 + i - d + 15] =
+// q_d W[i - d + 15] (zero cells skipped: a CTA-uniform branch).  The cells
+// are in fixed point (x the chunk's scale).
+__device__ __forceinline__ void apply_node(const float *row, const int *cf, const uint32_t *mask, int L, int sig,
+                                           bool live, float (&acc)[kTPT])
+{
+    const int t = threadIdx.x;
+#pragma unroll 1
+    for (int w = 0; w < kBlocks / 32; ++w) {
+        uint32_t m = mask[w];
+        while (m) {
+            const int bl = 32 * w + __ffs(m) - 1;
+            m &= m - 1;
+            const int j0 = kTPT * (t - bl) + L - kTPT - sig;
+            if (!live || j0 < -30 || j0 > L - 1) continue;      // the window misses the row
+            const float *wp = row + row_word(j0 + kEdge);      // j0 + kEdge = 0 (mod 16)
+            float W[32];
 #pragma unroll
-                    for (int i = 0; i < kB; ++i) {
-                        const int b = tid * kB + i;
-                        v[i] = (b < nb2) ? s->hist[b] : 0;
-                        fl[i] = v[i] > 0 ? 1 : 0;
-                        sv += v[i];
-                        sf += fl[i];
-                    }
-                    int tv, tf;
-                    int pv = block_scan(sv, s, &tv);
-                    int pf = block_scan(sf, s, &tf);
-#pragma unroll
-                    for (int i = 0; i < kB; ++i) {
-                        const int b = tid * kB + i;
-                        if (b < nb2) {
-                            s->hist[b] = pv;             // scatter cursor
-                            if (fl[i]) {
-                                s->glist[pf] = (unsigned short)b;
-                                s->gstart[pf] = (unsigned short)pv;
-                            }
-                        }
-                        pv += v[i];
-                        pf += fl[i];
-                    }
-                    if (tid == 0) {
-                        s->n_groups = tf;
-                        s->gstart[tf] = (unsigned short)tv;
-                    }
-                }
-                __syncthreads();
-                if (warp == 0) {
-                    // destination of record i (stable within a bin) replaces its bin in rbin[i]
-                    for (int i0 = 0; i0 < nrec; i0 += 32) {
-                        const int i = i0 + lane;
-                        const bool v = i < nrec;
-                        const int bin = v ? (int)s->rbin[i] : -1 - lane;
-                        const unsigned peers = __match_any_sync(0xffffffffu, bin);
-                        const int rank = __popc(peers & ((1u << lane) - 1u));
-                        const int pos = v ? s->hist[bin] : 0;
-                        __syncwarp();
-                        if (v) {
-                            if (lane == __ffs(peers) - 1) s->hist[bin] = pos + __popc(peers);
-                            s->rbin[i] = (unsigned short)(pos + rank);
-                        }
-                        __syncwarp();
-                    }
-                }
-                __syncthreads();
-                for (int i = tid; i < nrec; i += kThreads) sorted[s->rbin[i]] = recs[i];
-                __syncthreads();
-                // ---- 3. per bin: stage rows, apply records ------------------------
-                const int ng = s->n_groups;
-                const int Pbase = k0 + L - 1;            // position of v(j) at tick k0 is Pbase - A
-                RowRegs nxt;
-                load_rows(a, s->glist[0], nxt);
-                for (int g = 0; g < ng; ++g) {
-                    const int gbeg = s->gstart[g], gend = s->gstart[g + 1];
-                    __syncthreads();                     // previous bin's rows no longer read
-                    store_rows(s, nxt);
-                    if (g + 1 < ng) load_rows(a, s->glist[g + 1], nxt);
-                    __syncthreads();
-                    Rec rn = sorted[gbeg];
-                    for (int ri = gbeg; ri < gend; ++ri) {
-                        const Rec rc = rn;
-                        if (ri + 1 < gend) rn = sorted[ri + 1];         // prefetch the next record
-                        const int P = Pbase - rc.A;
-                        apply_block(s, P + blo_tick, L, lane, rc.w, rc.f, acc_lo);
-                        apply_block(s, P + bhi_tick, L, lane, rc.w, rc.f, acc_hi);
-                    }
-                }
-                // the chunk's sums into the compensated totals (each lane its own ticks)
-                add_chunk(tot, blo_tick + lane, acc_lo, first_chunk);
-                add_chunk(tot, bhi_tick + lane, acc_hi, first_chunk);
-                first_chunk = false;
-                __syncthreads();
+            for (int k = 0; k < 8; ++k) {
+                const float4 v = *reinterpret_cast<const float4 *>(wp + 4 * k + 4 * (k >> 2));
+                W[4 * k] = v.x;
+                W[4 * k + 1] = v.y;
+                W[4 * k + 2] = v.z;
+                W[4 * k + 3] = v.w;
             }
-            float *out = a.current + (size_t)pi * T;
+            int q[kBlk];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int t0 = (h ? bhi_tick : blo_tick) + lane;
+            for (int k = 0; k < 4; ++k) {
+                const int4 v = reinterpret_cast<const int4 *>(cf + bl * kBlk)[k];
+                q[4 * k] = v.x;
+                q[4 * k + 1] = v.y;
+                q[4 * k + 2] = v.z;
+                q[4 * k + 3] = v.w;
+            }
 #pragma unroll
-                for (int i = 0; i < kTPL; ++i) {
-                    const int k = k0 + t0 + 32 * i;
-                    const float v = first_chunk ? 0.f : __fsub_rn(tot[t0 + 32 * i], tot[kPass + t0 + 32 * i]);
-                    if (k < T) out[k] = v;
+            for (int d = 0; d < kBlk; ++d) {
+                if (q[d] != 0) {
+                    const float qf = (float)q[d];
+#pragma unroll
+                    for (int i = 0; i < kTPT; ++i) acc[i] = fmaf(qf, W[i - d + 15], acc[i]);
                 }
             }
         }
     }
+}
+
+__global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a, int64_t n_items_cap)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem *s = reinterpret_cast<Smem *>(smem_raw);
+    const int tid = threadIdx.x;
+    const bool go = a.counts[3] == 0 && a.counts[1] <= a.pix_cap;
+    const int64_t npix = go ? min(a.counts[1], a.pix_end) : 0;
+    const int64_t n_items = min(n_items_cap, max((int64_t)0, npix - a.pix_begin));
+    const int T = a.c.n_ticks, L = a.nt, nb = a.nb, nb2 = nb * nb;
+    const int sig = tick_shift(L);
+    const int npx = a.g.npx_x * a.g.npx_y;
+    Rec *recs = a.recs + (size_t)blockIdx.x * kRecCap;
+    Rec *sorted = a.sorted + (size_t)blockIdx.x * kRecCap;
+    for (int i = tid; i < 2 * kRowWords; i += kThreads) (&s->row[0][0])[i] = 0.f;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s->item = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int64_t it = s->item;
+        if (it >= n_items) break;
+        const int64_t pi = a.pix_begin + a.order[it];
+        const int32_t pid = a.active[pi];
+        const int an = pid / npx, rem = pid - an * npx;
+        const int iy = rem / a.g.npx_x, ix = rem - iy * a.g.npx_x;
+        const int slot = an / a.g.n_anodes;            // event of this (virtual) pixel
+        const uint64_t key = slot_key(a.seed, a.ev, slot);
+        const int64_t seg0 = slot_first(a.ev, slot);
+        const int e0 = a.off[pi], e1 = a.off[pi + 1];
+        float *out = a.current + (size_t)pi * T;
+        for (int k0 = 0; k0 < T; k0 += kPass) {
+            const int t_lo = kTPT * tid - sig;                      // my first tick of the pass
+            const bool live = t_lo + kTPT > 0 && t_lo < kPass && k0 + t_lo < T;
+            float acc[kTPT], tot[kTPT], cmp[kTPT];
+#pragma unroll
+            for (int i = 0; i < kTPT; ++i) acc[i] = tot[i] = cmp[i] = 0.f;
+            GenState st{e0, 0};
+            while (st.e < e1) {
+                // ---- 1. records of this chunk ------------------------------------------
+                for (int b = tid; b <= nb2; b += kThreads) s->hist[b] = 0;
+                for (int b = tid; b < nb2; b += kThreads) s->nflag[b] = 0;
+                if (tid == 0) s->wmax = 0, s->emax = 0;
+                __syncthreads();
+                const int nrec = gen_chunk(a, s, st, e1, ix, iy, key, seg0, recs);
+                if (nrec == 0) continue;
+                // ---- 2. bin order, nodes reached -----------------------------------------
+                {
+                    constexpr int kB = kMaxBins / kThreads;
+                    int v[kB], sv = 0;
+#pragma unroll
+                    for (int i = 0; i < kB; ++i) {
+                        const int b = tid * kB + i;
+                        v[i] = b < nb2 ? s->hist[b] : 0;
+                        sv += v[i];
+                    }
+                    int tv;
+                    int pv = block_scan(sv, s, &tv);
+#pragma unroll
+                    for (int i = 0; i < kB; ++i) {
+                        const int b = tid * kB + i;
+                        if (b < nb2) {
+                            s->hist[b] = pv;                  // scatter cursor, then the end of bin b
+                            if (v[i] > 0) {                   // the bin's corner nodes inside the table
+                                const int bx = b / nb, by = b - bx * nb;
+                                s->nflag[b] = 1;
+                                if (bx + 1 < nb) s->nflag[b + nb] = 1;
+                                if (by + 1 < nb) s->nflag[b + 1] = 1;
+                                if (bx + 1 < nb && by + 1 < nb) s->nflag[b + nb + 1] = 1;
+                            }
+                        }
+                        pv += v[i];
+                    }
+                }
+                __syncthreads();
+                for (int i = tid; i < nrec; i += kThreads) {
+                    const Rec r = recs[i];
+                    sorted[atomicAdd(&s->hist[r.b0], 1)] = r;
+                }
+                {
+                    constexpr int kB = kMaxBins / kThreads;
+                    int fl[kB], sf = 0;
+#pragma unroll
+                    for (int i = 0; i < kB; ++i) {
+                        const int b = tid * kB + i;
+                        fl[i] = b < nb2 ? s->nflag[b] : 0;
+                        sf += fl[i];
+                    }
+                    int tf;
+                    int pf = block_scan(sf, s, &tf);            // (its barriers also order the scatter)
+#pragma unroll
+                    for (int i = 0; i < kB; ++i)
+                        if (fl[i]) s->nodes[pf++] = (unsigned short)(tid * kB + i);
+                    if (tid == 0) s->n_nodes = tf;
+                }
+                __syncthreads();
+                {   // largest node entry count (a deterministic bound of the cells with the chunk's weights)
+                    const int nn0 = s->n_nodes;
+                    int em = 0;
+                    for (int i = tid; i < nn0; i += kThreads) em = max(em, node_lists(s, s->nodes[i], nb).pre[4]);
+                    em = __reduce_max_sync(0xffffffffu, em);
+                    if ((tid & 31) == 0) atomicMax(&s->emax, em);
+                }
+                for (int i = tid; i < 2 * kBlocks * kBlk / 4; i += kThreads)
+                    reinterpret_cast<int4 *>(&s->u.cell[0][0])[i] = make_int4(0, 0, 0, 0);
+                if (tid < 3 * (kBlocks / 32)) (&s->mask[0][0])[tid] = 0u;
+                __syncthreads();
+                // ---- 3. node loop ----------------------------------------------------------
+                const int nn = s->n_nodes;
+                RowRegs rv;
+                load_row(a, s->nodes[0], rv);
+                store_row(s->row[0], rv);
+                if (nn > 1) load_row(a, s->nodes[1], rv);
+                const float sc_next = node_scale(s->emax, __int_as_float(s->wmax));   // of the whole chunk
+                const float inv_sc = 1.f / sc_next;
+                {
+                    const NodeLists nl = node_lists(s, s->nodes[0], nb);
+                    for (int e = tid; e < nl.pre[4]; e += kThreads) {
+                        Rec r;
+                        int c;
+                        node_entry(nl, sorted, e, r, c);
+                        deposit(s->u.cell[0], s->mask[0], r, c, k0, sc_next);
+                    }
+                }
+                __syncthreads();
+                for (int u = 0; u < nn; ++u) {
+                    const int x = u & 1;
+                    const bool nxt = u + 1 < nn;
+                    if (nxt) store_row(s->row[x ^ 1], rv);
+                    if (u + 2 < nn) load_row(a, s->nodes[u + 2], rv);
+                    NodeLists nl;
+                    Rec r0;
+                    int c0 = 0;
+                    bool h0 = false;
+                    if (nxt) {                                  // first entry of node u + 1 in flight
+                        nl = node_lists(s, s->nodes[u + 1], nb);
+                        h0 = tid < nl.pre[4];
+                        if (h0) node_entry(nl, sorted, tid, r0, c0);
+                    }
+                    apply_node(s->row[x], s->u.cell[x], s->mask[u % 3], L, sig, live, acc);
+                    if (u % kKahanNodes == kKahanNodes - 1 || u == nn - 1) {
+#pragma unroll
+                        for (int i = 0; i < kTPT; ++i) {
+                            kahan_add(tot[i], cmp[i], acc[i] * inv_sc);
+                            acc[i] = 0.f;
+                        }
+                    }
+                    if (nxt) {
+                        int *cell = s->u.cell[x ^ 1];
+                        uint32_t *mk = s->mask[(u + 1) % 3];
+                        if (h0) deposit(cell, mk, r0, c0, k0, sc_next);
+                        for (int e = tid + kThreads; e < nl.pre[4]; e += kThreads) {
+                            Rec r;
+                            int c;
+                            node_entry(nl, sorted, e, r, c);
+                            deposit(cell, mk, r, c, k0, sc_next);
+                        }
+                    }
+                    if (tid < kBlocks / 32) s->mask[(u + 2) % 3][tid] = 0u;   // node u - 1's, free since
+                    __syncthreads();
+                    // node u's cells cleared for node u + 2 (the whole buffer: fewer steps than walking its blocks)
+                    for (int i = tid; i < kBlocks * kBlk / 4; i += kThreads)
+                        reinterpret_cast<int4 *>(s->u.cell[x])[i] = make_int4(0, 0, 0, 0);
+                    __syncthreads();
+                }
+            }
+            // compensated totals (zero for a pixel without records)
+#pragma unroll
+            for (int i = 0; i < kTPT; ++i) {
+                const int k = t_lo + i;
+                if (k >= 0 && k < kPass && k0 + k < T) out[k0 + k] = __fsub_rn(tot[i], cmp[i]);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------- queue order ----
+// Pixels ordered by decreasing work (their candidate points sum_{s -> p} N_s
+// M, in 32 classes of floor(log2)), so that the heavy ones start first and the
+// tail of the queue is short work.  The order within a class is immaterial:
+// each pixel is computed alone.
+__global__ void k_fp_classify(const int64_t *counts, int64_t pix_cap, int64_t begin, int64_t end,
+                              const int32_t *off, const int32_t *segs, const int32_t *n_samples, int M,
+                              int32_t *cls, int32_t *ccount)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (counts[3] != 0 || counts[1] > pix_cap) return;
+    const int64_t n = min(counts[1], end) - begin;
+    if (j >= n) return;
+    const int64_t pi = begin + j;
+    long long w = 1;
+    for (int e = off[pi]; e < off[pi + 1]; ++e) w += (long long)n_samples[segs[e]] * M;
+    const int c = min(31, 63 - __clzll(w));
+    cls[j] = c;
+    atomicAdd(&ccount[c], 1);
+}
+
+__global__ void k_fp_order(const int64_t *counts, int64_t pix_cap, int64_t begin, int64_t end, const int32_t *cls,
+                           const int32_t *ccount, int32_t *cursor, int32_t *order)
+{
+    __shared__ int start[32];
+    if (threadIdx.x < 32) {
+        int s0 = 0;
+        for (int c = 31; c > threadIdx.x; --c) s0 += ccount[c];     // heavier classes first
+        start[threadIdx.x] = s0;
+    }
+    __syncthreads();
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (counts[3] != 0 || counts[1] > pix_cap) return;
+    const int64_t n = min(counts[1], end) - begin;
+    if (j >= n) return;
+    const int c = cls[j];
+    order[start[c] + atomicAdd(&cursor[c], 1)] = (int32_t)j;
 }
 
 int grid_for(int64_t pix_cap, int ctas_per_sm = 3)
@@ -392,15 +613,37 @@ int grid_for(int64_t pix_cap, int ctas_per_sm = 3)
     if (g > pix_cap) g = pix_cap;
     return (int)(g < 1 ? 1 : g);
 }
+
+struct FpLayout {
+    size_t queue, cls, order, recs, sorted, total;
+};
+
+FpLayout fp_layout(int grid, int64_t pix_cap)
+{
+    FpLayout t;
+    size_t o = 0;
+    auto take = [&](size_t b) {
+        const size_t at = o;
+        o += align256(b);
+        return at;
+    };
+    t.queue = take(512);                        // [0] queue, [64] class counts, [256] class cursors
+    t.cls = take(sizeof(int32_t) * (size_t)pix_cap);
+    t.order = take(sizeof(int32_t) * (size_t)pix_cap);
+    t.recs = take((size_t)grid * kRecCap * sizeof(Rec));
+    t.sorted = take((size_t)grid * kRecCap * sizeof(Rec));
+    t.total = o;
+    return t;
+}
 }  // namespace
 
 size_t current_scratch_bytes(int64_t pix_cap)
 {
-    const int g = grid_for(pix_cap > 0 ? pix_cap : 1);
-    return 2 * align256((size_t)g * kRecCap * sizeof(Rec)) + align256((size_t)g * 2 * kPass * sizeof(float));
+    const int64_t p = pix_cap > 0 ? pix_cap : 1;
+    return fp_layout(grid_for(p), p).total;
 }
 
-bool current_table_ok(int nb, int nt) { return nb * nb <= kMaxBins && ((nt + 3) / 4) * 4 <= kMaxRow; }
+bool current_table_ok(int nb, int nt) { return nb * nb <= kMaxBins && nt <= kMaxRow; }
 
 cudaError_t launch_induced_current(const sim_config &c, const sim_segments &s, const sim_drifted &d,
                                    const sim_response &r, const int32_t *active,
@@ -416,8 +659,6 @@ cudaError_t launch_induced_current(const sim_config &c, const sim_segments &s, c
     a.nt = r.nt;
     a.ld = r.ld;
     a.bpp = r.bins_per_pitch;
-    a.lp = ((r.nt + 3) / 4) * 4;
-    a.inv_nb = 1.0f / (float)r.nb;
     a.anch = reinterpret_cast<const Anchor *>(d.anchors);
     a.active = active;
     a.off = pix_seg_off;
@@ -431,16 +672,32 @@ cudaError_t launch_induced_current(const sim_config &c, const sim_segments &s, c
     a.ev = events_of(s);
     a.g = geo_of(c);
     a.dp = drift_par_of(c);
+    // the scratch is sized for the default grid: a smaller configured one fits it
     const int grid = grid_for(pix_cap, c.direct_ctas_per_sm > 0 ? c.direct_ctas_per_sm : 3);
+    const FpLayout lay = fp_layout(grid_for(pix_cap), pix_cap);
     char *p = reinterpret_cast<char *>(scratch);
-    a.recs = reinterpret_cast<Rec *>(p);
-    a.sorted = reinterpret_cast<Rec *>(p + align256((size_t)grid * kRecCap * sizeof(Rec)));
-    a.tot = reinterpret_cast<float *>(p + 2 * align256((size_t)grid * kRecCap * sizeof(Rec)));
-    const size_t smem = sizeof(Smem);
-    const cudaError_t e = cudaFuncSetAttribute(k_induced_current, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem);
+    a.queue = reinterpret_cast<int *>(p + lay.queue);
+    int32_t *ccount = reinterpret_cast<int32_t *>(p + lay.queue + 64);
+    int32_t *cursor = reinterpret_cast<int32_t *>(p + lay.queue + 256);
+    int32_t *cls = reinterpret_cast<int32_t *>(p + lay.cls);
+    int32_t *order = reinterpret_cast<int32_t *>(p + lay.order);
+    a.order = order;
+    a.recs = reinterpret_cast<Rec *>(p + lay.recs);
+    a.sorted = reinterpret_cast<Rec *>(p + lay.sorted);
+    cudaError_t e = cudaMemsetAsync(p + lay.queue, 0, 512, st);
     if (e != cudaSuccess) return e;
-    k_induced_current<<<grid, kThreads, smem, st>>>(a);
+    const int64_t n_cap = pix_cap - (pix_begin < pix_cap ? pix_begin : pix_cap);    // pixels the range can hold
+    if (n_cap <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((n_cap + 255) / 256);
+    k_fp_classify<<<blocks, 256, 0, st>>>(counts, pix_cap, pix_begin, pix_end, pix_seg_off, pix_seg_ids,
+                                          d.n_samples, c.mc_per_sample, cls, ccount);
+    k_fp_order<<<blocks, 256, 0, st>>>(counts, pix_cap, pix_begin, pix_end, cls, ccount, cursor, order);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = sizeof(Smem);
+    e = cudaFuncSetAttribute(k_induced_current, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_induced_current<<<grid, kThreads, smem, st>>>(a, n_cap);
     return cudaGetLastError();
 }
 
