@@ -31,7 +31,7 @@
 //     atomics: order-independent, so the result is bitwise reproducible; the
 //     scale, a power of two, follows the node's entries and the chunk's
 //     largest weight, so that taps round to ~1e-9 of the node's charge)
-//     and its table row staged, while node n is applied: for each present
+//     and its table row copied in (cp.async), while node n is applied: for each present
 //     16-tick arrival block every thread loads the 31 table values its 16
 //     ticks need (eight 16-byte shared reads; 4 words of padding after every
 //     16 keep consecutive threads' windows conflict-free) and adds
@@ -240,33 +240,25 @@ __device__ int gen_chunk(const CurArgs &a, Smem *s, GenState &st, int e1, int ix
     return nrec;
 }
 
-// Thread t's share of a table row: elements 4 t + 512 i (i < 4) as 16-byte
-// loads (rows are 16-byte aligned; elements at or beyond L read as zero).
-struct RowRegs {
-    float4 v[4];
-};
-
-__device__ __forceinline__ void load_row(const CurArgs &a, int n, RowRegs &r)
+// Thread t's share of a table row, copied asynchronously (cp.async, 16 bytes
+// each: elements 4 t + 512 i, i < 4) into the staged layout; elements at or
+// beyond L are zero-filled.  Rows are 16-byte aligned, and four values at
+// p = 0 (mod 4) stay inside one 16-position group.
+__device__ __forceinline__ void stage_row(float *dst, const CurArgs &a, int n)
 {
     const float *row = a.lut + (size_t)n * a.ld;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int j = 4 * threadIdx.x + 512 * i;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (j < a.nt) v = __ldg(reinterpret_cast<const float4 *>(row + j));
-        if (j + 1 >= a.nt) v.y = 0.f;
-        if (j + 2 >= a.nt) v.z = 0.f;
-        if (j + 3 >= a.nt) v.w = 0.f;
-        r.v[i] = v;
+        const int bytes = j < a.nt ? 4 * min(4, a.nt - j) : 0;
+        const float *src = row + (j < a.nt ? j : 0);
+        const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + row_word(j + kEdge));
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(bytes) : "memory");
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-__device__ __forceinline__ void store_row(float *dst, const RowRegs &r)
-{
-#pragma unroll
-    for (int i = 0; i < 4; ++i)      // four values inside one 16-position group: one 16-byte store
-        *reinterpret_cast<float4 *>(dst + row_word(4 * threadIdx.x + 512 * i + kEdge)) = r.v[i];
-}
+__device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // The four record lists of node n (corner c of the bins (nx - (c & 1),
 // ny - (c >> 1))) in bin order: begin of each and prefix counts.
@@ -498,10 +490,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a, int6
                 __syncthreads();
                 // ---- 3. node loop ----------------------------------------------------------
                 const int nn = s->n_nodes;
-                RowRegs rv;
-                load_row(a, s->nodes[0], rv);
-                store_row(s->row[0], rv);
-                if (nn > 1) load_row(a, s->nodes[1], rv);
+                stage_row(s->row[0], a, s->nodes[0]);
                 const float sc_next = node_scale(s->emax, __int_as_float(s->wmax));   // of the whole chunk
                 const float inv_sc = 1.f / sc_next;
                 {
@@ -513,12 +502,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a, int6
                         deposit(s->u.cell[0], s->mask[0], r, c, k0, sc_next);
                     }
                 }
+                stage_wait();
                 __syncthreads();
                 for (int u = 0; u < nn; ++u) {
                     const int x = u & 1;
                     const bool nxt = u + 1 < nn;
-                    if (nxt) store_row(s->row[x ^ 1], rv);
-                    if (u + 2 < nn) load_row(a, s->nodes[u + 2], rv);
+                    if (nxt) stage_row(s->row[x ^ 1], a, s->nodes[u + 1]);   // lands before the next apply
                     NodeLists nl;
                     Rec r0;
                     int c0 = 0;
@@ -548,6 +537,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a, int6
                         }
                     }
                     if (tid < kBlocks / 32) s->mask[(u + 2) % 3][tid] = 0u;   // node u - 1's, free since
+                    stage_wait();
                     __syncthreads();
                     // node u's cells cleared for node u + 2 (the whole buffer: fewer steps than walking its blocks)
                     for (int i = tid; i < kBlocks * kBlk / 4; i += kThreads)
