@@ -34,9 +34,9 @@ sys.path.insert(0, ROOT)
 from synth import events, params, response  # noqa: E402
 
 # kernels per step: 1 quench/drift + 14 pixel map + 6 electronics, plus the induced current:
-# 1 (FP32 direct) or 15 (tensor cores: work plan 5 + two 3-kernel scans, table rounding 1,
-# table unfolding 1, contraction 1, reduction of split groups 1)
-KERNELS_PER_STEP = {0: 22, 1: 36, 2: 36}
+# 3 (FP32: work classes, queue order, sum) or 15 (tensor cores: work plan 5 + two 3-kernel
+# scans, table rounding 1, table unfolding 1, contraction 1, reduction of split groups 1)
+KERNELS_PER_STEP = {0: 24, 1: 36, 2: 36}
 FP32_LANES_PER_SM = 128
 
 
@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--precision", type=int, choices=[0, 1, 2], default=2,
-                    help="induced-current form of the headline: 0 FP32 direct, 1 BF16 / 2 FP16 tensor cores")
+                    help="induced-current form of the headline: 0 FP32, 1 BF16 / 2 FP16 tensor cores")
     ap.add_argument("--no-forms", action="store_true", help="skip timing the other induced-current forms")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-vs-plain request stream")
     ap.add_argument("--no-post", action="store_true", help="skip timing truth, hit points and dQ/dx")
@@ -359,7 +359,7 @@ def batched_vs_plain(cfg, lut, dev, n_events=256, lo=1.0e3, hi=2.0e5, n_sub=4):
                        "candidates_ms": [[c, round(ms, 3)] for c, ms in table]}}
 
 
-FORMS = {0: ("fp32_direct", "f32"), 1: ("bf16_tensor", "bf16"), 2: ("fp16_tensor", "f16")}
+FORMS = {0: ("fp32_cells", "f32"), 1: ("bf16_tensor", "bf16"), 2: ("fp16_tensor", "f16")}
 
 
 def time_form(cfg, seg, lut, dev, precision, steps, warmup, rank):
@@ -600,13 +600,14 @@ def light_path(dev, names=("module", "spill"), reps=5):
 
 
 def form_roofline(run, cfg, precision, a4_s, fp32_peak, dev, wl_key=""):
-    """Roofline of the induced-current kernel of one form.  FP32 direct:
-    against the measured FP32 FMA rate (sim_probe_fma), work 2 flop per (point,
-    pixel within the table's reach, table tick).  Tensor-core forms: against
-    the measured dense 16-bit tensor peak, achieved = the algorithmic work
-    2 flop x nnz(Q) x L (one multiply-add per nonzero binned-charge cell and
-    table tick, cells counted on the device) over the call's time; the dense
-    MMA work (zeros inside the issued tiles included) is given beside it."""
+    """Roofline of the induced-current kernel of one form: achieved = the
+    algorithmic work 2 flop x nnz(Q) x L (one multiply-add per nonzero
+    binned-charge cell and table tick, cells counted on the device) over the
+    call's time.  FP32 form: against the measured FP32 FMA rate
+    (sim_probe_fma).  Tensor-core forms: against the measured dense 16-bit
+    tensor peak; the dense MMA work (zeros inside the issued tiles included)
+    is given beside it.  per_point: 2 flop per (point, pixel within the
+    table's reach, table tick), the count of the term-by-term sum."""
     import torch
     from paper_2212_09807_gb300 import sim
     S = run.max_segments
@@ -618,17 +619,19 @@ def form_roofline(run, cfg, precision, a4_s, fp32_peak, dev, wl_key=""):
     L = params.LUT["nt"]
     w_alg = 2.0 * 9 * L * samples                       # flop per launch (9 pixels per point)
     per_point = w_alg / a4_s / 1e12
-    if precision == 0:
-        return {"bound": "alu", "achieved": per_point, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": per_point / fp32_peak, "traffic": stored_traffic("induced_current.cu", wl_key),
-                "kernel": "k_induced_current",
-                "peak_note": "FP32 FMA rate measured on this GPU by sim_probe_fma (independent FMA chains), "
-                             "of measured",
-                "work_note": "2 flop x 9 pixels x 1950 table ticks per (point, perturbation)"}, samples
     n_mma = int(run.ws[4].item())
     nnz = int(run.ws[5].item())
-    dense = 2.0 * 128 * 32 * 16 * n_mma / a4_s / 1e12
     useful = 2.0 * nnz * L / a4_s / 1e12
+    work_note = ("achieved: 2 flop x nnz(Q) x 1950 table ticks (nonzero binned-charge cells Q[p, node, tick], "
+                 "counted on the device); per_point: 2 flop x 9 pixels x 1950 ticks per (point, perturbation)")
+    if precision == 0:
+        return {"bound": "alu", "achieved": useful, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": useful / fp32_peak, "traffic": stored_traffic("induced_current.cu", wl_key),
+                "kernel": "k_induced_current", "nnz_charge_cells": nnz, "per_point_achieved": per_point,
+                "peak_note": "FP32 FMA rate measured on this GPU by sim_probe_fma (independent FMA chains), "
+                             "of measured",
+                "work_note": work_note}, samples
+    dense = 2.0 * 128 * 32 * 16 * n_mma / a4_s / 1e12
     tpk = measured_peaks().get("bf16_tflops_sustained") or 1700.0
     return {"bound": "tensor", "achieved": useful, "peak": tpk, "unit": "TFLOP/s", "frac": useful / tpk,
             "traffic": stored_traffic("induced_current_tc.cu", wl_key), "kernel": "k_induced_current_tc",
@@ -636,9 +639,7 @@ def form_roofline(run, cfg, precision, a4_s, fp32_peak, dev, wl_key=""):
             "dense_achieved": dense, "dense_frac": dense / tpk, "per_point_achieved": per_point,
             "peak_note": "measured dense bf16 sustained (kernel timed inside a step), of measured; fp16 has the "
                          "same nominal rate",
-            "work_note": "achieved: 2 flop x nnz(Q) x 1950 table ticks (nonzero binned-charge cells Q[p, node, "
-                         "tick], counted on the device); dense: 2 x 128 x 32 x 16 flop per issued MMA; "
-                         "per_point: 2 flop x 9 pixels x 1950 ticks per (point, perturbation)"}, samples
+            "work_note": work_note + "; dense: 2 x 128 x 32 x 16 flop per issued MMA"}, samples
 
 
 SLICE = 32768        # active pixels per current launch of a large request (serving form)

@@ -78,7 +78,7 @@ typedef struct sim_config {
     /* counter-based RNG seed (Philox4x32-10 key = seed ^ event_id) */
     uint64_t seed;
     /* arithmetic form of the induced-current step (sim_induced_current):
-     * 0 = FP32 direct gather; 1 = tensor-core contraction with BF16 operands,
+     * 0 = FP32 form on the CUDA cores; 1 = tensor-core contraction with BF16 operands,
      * 2 = with FP16 operands (FP32 accumulation in both) */
     int32_t precision;
     /* running CSA charge of the front end (sim_electronics): 0 = FP32,
@@ -105,7 +105,7 @@ typedef struct sim_config {
      * default 2) and records per CTA chunk (a power of two, 4096..1048576;
      * default 1048576 for calls sized for at least 131072 active pixels, else
      * 262144; the workspace holds two record buffers of 32 bytes per record
-     * and CTA); FP32 direct form: resident CTAs per SM (1..3, default 3).
+     * and CTA); FP32 form: resident CTAs per SM (1..3, default 3).
      * paper_2212_09807_gb300/tune.py picks them by timing a sample. */
     int32_t tc_units_per_sm, tc_record_chunk, direct_ctas_per_sm;
     /* polls of a bounded device-side wait of the tensor-core forms before it
@@ -226,26 +226,28 @@ int sim_pixel_map(const sim_config *cfg, const sim_segments *seg, const sim_drif
  *   I[p, k] = sum over segments s mapped to p, points mu < N_s, perturbations
  *             nu < M of q_s * Rt(x - x_p, y - y_p, k - a),  q_s = Q_a/(N_s M),
  * the table read bilinearly at the folded transverse offset and linearly at
- * the fractional arrival tick a; summed over segments in increasing index
- * order.  current: FP32 [pix_cap][n_ticks]; rows [0, counts[1]) are written.
- * counts: device int64[6] counts block as written by sim_pixel_map ([1] =
- * active pixels, [3] = status); nothing is computed when the status word is
- * nonzero or counts[1] > pix_cap.
- * cfg->precision selects the arithmetic: 0 sums the terms in FP32 in the
- * order above; 1 (BF16) and 2 (FP16) regroup them as I[p, k] = sum over table
- * nodes n and arrival ticks a of Q[p, n, a] R[n, k - a + L - 1] (Q: charge
- * deposited on node n at tick a by the linear weights) and contract Q with the
- * Toeplitz unfolding of each table row on the tensor cores.  Q is accumulated
- * in fixed point (2^-12 e-) and rounded to the operand type, as is R; FP16 Q
- * cells saturate at 262016 e-.  Results are bitwise reproducible for a given
- * call; counts[4] receives the number of tensor-core MMA instructions
- * (M = 128, N = 32, K = 16) of the call and counts[5] the number of nonzero
- * charge cells Q[p, n, a] it contracted, and SIM_STATUS_TIMEOUT is set if a
- * bounded device-side wait gave up.
+ * the fractional arrival tick a.  current: FP32 [pix_cap][n_ticks]; rows
+ * [0, counts[1]) are written.  counts: device int64[6] counts block as
+ * written by sim_pixel_map ([1] = active pixels, [3] = status); nothing is
+ * computed when the status word is nonzero or counts[1] > pix_cap.
+ * Every form regroups the terms as I[p, k] = sum over table nodes n and
+ * arrival ticks a of Q[p, n, a] R[n, k - a + L - 1] (Q: charge deposited on
+ * node n at tick a by the linear weights, accumulated in fixed point with
+ * integer atomics); cfg->precision selects the arithmetic of the sum:
+ * 0 FP32 on the CUDA cores (Q at a power-of-two scale per chunk of a pixel's
+ * points, ~1e-9 of its charge; partial sums added into compensated totals);
+ * 1 (BF16) and 2 (FP16) contract Q with the Toeplitz blocks of each table row
+ * on the tensor cores (Q in fixed point 2^-12 e-, then rounded to the operand
+ * type, as is R; FP16 Q cells saturate at 262016 e-).  Results are bitwise
+ * reproducible for a given call, and with precision 0 a pixel's current does
+ * not depend on the other pixels of the call; counts[4] receives the number
+ * of tensor-core MMA instructions (M = 128, N = 32, K = 16) of the call and
+ * counts[5] the number of nonzero charge cells Q[p, n, a] it summed, and
+ * SIM_STATUS_TIMEOUT is set if a bounded device-side wait gave up.
  * Workspace (scratch from byte 256 on): sim_workspace_size(cfg, 0, 0, 0,
- * pix_cap) bytes, sized for the current device (per-CTA record buffers; with
- * precision 1/2 also the unfolded table, ~1.4 GB in all on 152 SMs).  Table
- * limits: nb * nb <= 2048, nt <= 2048. */
+ * pix_cap) bytes, sized for the current device (per-CTA record buffers, up to
+ * ~1.8 GB for precision 0 on 152 SMs; with precision 1/2 also the phase
+ * tables).  Table limits: nb * nb <= 2048, nt <= 2048. */
 int sim_induced_current(const sim_config *cfg, const sim_segments *seg, const sim_drifted *dr,
                         const sim_response *resp, const int32_t *active_pixels,
                         const int32_t *pix_seg_off, const int32_t *pix_seg_ids,
@@ -332,7 +334,7 @@ int sim_event_view_of(const sim_config *cfg, int64_t max_events, int64_t n_segme
  * `blocks` CTAs of 256 threads that issues only independent FP32 fused
  * multiply-adds, iters x 128 per thread, and writes the flops it performs to
  * *flops (host).  Timed with events on `stream`, it gives the device's FP32
- * FMA rate, the bound of the FP32 direct form of sim_induced_current.  sink:
+ * FMA rate, the bound of the FP32 form of sim_induced_current.  sink:
  * device FP32 [blocks * 256] (never written in practice; it keeps the
  * arithmetic live).  1 <= blocks <= 2^20, iters >= 1. */
 int sim_probe_fma(int64_t blocks, int32_t iters, float *sink, double *flops, void *stream);

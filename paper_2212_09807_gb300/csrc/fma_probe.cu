@@ -1,6 +1,6 @@
 // fma_probe.cu -- measurement support, not a step of the method: a kernel
 // that issues only independent FP32 fused multiply-adds, so that its rate is
-// the device's FP32 FMA throughput.  The benchmark divides the direct form's
+// the device's FP32 FMA throughput.  The benchmark divides the FP32 form's
 // algorithmic flops by this measured rate (its "alu" roofline).
 #include "sim_internal.cuh"
 

@@ -92,6 +92,7 @@ struct CurArgs {
     const int32_t *order;                       // pixel (relative to pix_begin) of each queue entry
     Rec *recs;                                  // [grid][kRecCap], point order
     Rec *sorted;                                // [grid][kRecCap], bin order
+    unsigned long long *n_cells;                // counts[5]: nonzero charge cells (statistics)
 };
 
 struct __align__(16) Smem {
@@ -311,8 +312,10 @@ __device__ __forceinline__ float node_scale(int n_entries, float wmax)
     return __int_as_float((k + 127) << 23);
 }
 
-// Deposits the two ticks of a record's corner c into the fixed-point cells.
-__device__ __forceinline__ void deposit(int *cell, uint32_t *mask, const Rec &r, int c, int k0, float scale)
+// Deposits the two ticks of a record's corner c into the fixed-point cells;
+// n_cells counts the cells it makes nonzero (all deposits are >= 0).
+__device__ __forceinline__ void deposit(int *cell, uint32_t *mask, const Rec &r, int c, int k0, float scale,
+                                        unsigned &n_cells)
 {
     const float w = c == 0 ? r.w.x : c == 1 ? r.w.y : c == 2 ? r.w.z : r.w.w;
     uint32_t bits[2] = {0u, 0u};
@@ -322,7 +325,9 @@ __device__ __forceinline__ void deposit(int *cell, uint32_t *mask, const Rec &r,
         const float val = tap ? r.f * w : (1.f - r.f) * w;
         const int rel = r.A - k0 + tap;
         if (val == 0.f || rel < 0 || rel >= kBlocks * kBlk) continue;
-        atomicAdd(cell + rel, __float2int_rn(val * scale));
+        const int add = __float2int_rn(val * scale);
+        if (add == 0) continue;
+        n_cells += atomicAdd(cell + rel, add) == 0;
         word[tap] = rel >> 9;
         bits[tap] = 1u << ((rel >> 4) & 31);
     }
@@ -396,13 +401,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a, int6
     Rec *recs = a.recs + (size_t)blockIdx.x * kRecCap;
     Rec *sorted = a.sorted + (size_t)blockIdx.x * kRecCap;
     for (int i = tid; i < 2 * kRowWords; i += kThreads) (&s->row[0][0])[i] = 0.f;
+    unsigned n_cells = 0;                       // nonzero charge cells made by this thread
 
     for (;;) {
         __syncthreads();
         if (tid == 0) s->item = atomicAdd(a.queue, 1);
         __syncthreads();
         const int64_t it = s->item;
-        if (it >= n_items) break;
+        if (it >= n_items) break;      // (uniform)
         const int64_t pi = a.pix_begin + a.order[it];
         const int32_t pid = a.active[pi];
         const int an = pid / npx, rem = pid - an * npx;
@@ -499,7 +505,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a, int6
                         Rec r;
                         int c;
                         node_entry(nl, sorted, e, r, c);
-                        deposit(s->u.cell[0], s->mask[0], r, c, k0, sc_next);
+                        deposit(s->u.cell[0], s->mask[0], r, c, k0, sc_next, n_cells);
                     }
                 }
                 stage_wait();
@@ -528,12 +534,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a, int6
                     if (nxt) {
                         int *cell = s->u.cell[x ^ 1];
                         uint32_t *mk = s->mask[(u + 1) % 3];
-                        if (h0) deposit(cell, mk, r0, c0, k0, sc_next);
+                        if (h0) deposit(cell, mk, r0, c0, k0, sc_next, n_cells);
                         for (int e = tid + kThreads; e < nl.pre[4]; e += kThreads) {
                             Rec r;
                             int c;
                             node_entry(nl, sorted, e, r, c);
-                            deposit(cell, mk, r, c, k0, sc_next);
+                            deposit(cell, mk, r, c, k0, sc_next, n_cells);
                         }
                     }
                     if (tid < kBlocks / 32) s->mask[(u + 2) % 3][tid] = 0u;   // node u - 1's, free since
@@ -553,6 +559,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a, int6
             }
         }
     }
+    // nonzero charge cells of the call (counts[5], as the tensor-core form reports them)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) n_cells += __shfl_down_sync(0xffffffffu, n_cells, o);
+    if ((tid & 31) == 0 && n_cells) atomicAdd(a.n_cells, (unsigned long long)n_cells);
 }
 
 // ---------------------------------------------------------- queue order ----
@@ -674,7 +684,9 @@ cudaError_t launch_induced_current(const sim_config &c, const sim_segments &s, c
     a.order = order;
     a.recs = reinterpret_cast<Rec *>(p + lay.recs);
     a.sorted = reinterpret_cast<Rec *>(p + lay.sorted);
+    a.n_cells = reinterpret_cast<unsigned long long *>(const_cast<int64_t *>(counts) + 5);
     cudaError_t e = cudaMemsetAsync(p + lay.queue, 0, 512, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(const_cast<int64_t *>(counts) + 4, 0, 2 * sizeof(int64_t), st);
     if (e != cudaSuccess) return e;
     const int64_t n_cap = pix_cap - (pix_begin < pix_cap ? pix_begin : pix_cap);    // pixels the range can hold
     if (n_cap <= 0) return cudaSuccess;

@@ -1,7 +1,7 @@
 // induced_current_tc.cu -- step 4 of the charge path (arXiv:2212.09807
 // Sec. 3.3.2, Eq. (current)) as a tensor-core contraction on sm_103a:
 // tcgen05 MMAs with FP16 or BF16 operands and FP32 accumulators in tensor
-// memory.  Same terms as the FP32 direct form (the records of
+// memory.  Same terms and the same charge cells as the FP32 form (the records of
 // current_records.cuh), different arithmetic.
 //
 // With the table read bilinearly in the folded offset and linearly in the

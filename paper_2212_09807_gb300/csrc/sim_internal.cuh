@@ -165,7 +165,7 @@ cudaError_t launch_pixel_map(const sim_config &c, const sim_segments &s, const s
                              int32_t *pix_seg_ids, int64_t pix_cap, int64_t *counts, void *scratch,
                              cudaStream_t st);
 
-// Induced current, FP32 direct form (precision 0) and tensor-core form
+// Induced current, FP32 form (precision 0) and tensor-core form
 // (precision 1 BF16, 2 FP16 operands); same arguments.  Rows of the active
 // pixels [pix_begin, min(counts[1], pix_end)) are computed.
 size_t current_scratch_bytes(int64_t pix_cap);

@@ -7,7 +7,7 @@ up to their accumulation rounding), only its speed does:
     ranges into units of about total / (units x SMs) work), and
     ``tc_record_chunk``, the records a CTA generates and sorts per chunk before
     its node loop;
-  * FP32 direct form (precision 0): ``direct_ctas_per_sm``.
+  * FP32 form (precision 0): ``direct_ctas_per_sm``.
 ``autotune`` times every candidate on a sample of the workload (one event,
 or a batch of events, already on the device) with CUDA events, after one
 untimed run that sizes the buffers, and returns the fastest.  It runs all

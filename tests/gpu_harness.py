@@ -101,7 +101,7 @@ class Steps:
 
 
 # Tie band (electrons) of the end-to-end hit comparison, per current form: the
-# charge error each form leaves at the front end's decisions (FP32 direct: a
+# charge error each form leaves at the front end's decisions (FP32: a
 # few 1e-2 e- on the densest pixels; FP16 tensor cores: ~0.5 e-, from their
 # truncating FP32 accumulation).  Mismatches were measured at 0.05 e- (FP32)
 # and 0.5 e- (FP16) on the full-size module event and spill, none above.

@@ -6,7 +6,7 @@ Tolerances (stated once, used below):
     anode and point count N: exact (decided in FP64 on both sides);
   * pixel map: set-equal, except pairs whose oracle distance margin is within
     1e-5 cm of the map radius (FP32 geometry on the GPU);
-  * current (FP32 direct gather): per pixel ||I_gpu - I_ref||_inf <= 1e-4 ||I_ref||_inf
+  * current (FP32 form on the CUDA cores): per pixel ||I_gpu - I_ref||_inf <= 1e-4 ||I_ref||_inf
     (hard) with the median <= 1e-5; every prefix sum of each pixel's current
     (the charge integrated by each tick) within 1e-5 of the pixel's largest one
     plus 2e-6 of the event's peak pixel charge (gpu_harness.prefix_charge_ok:

@@ -1,7 +1,7 @@
 """Parity at full size, in the benchmark's launch configuration (one sim_event
 call per event): the one-module neutrino interaction (~2e4 segments) on EVERY
 active pixel, and the 35-module beam spill (~1.2e6 segments) on 2000 random
-active pixels plus every active pixel of its densest tile, for the FP32 direct
+active pixels plus every active pixel of its densest tile, for the FP32
 and the FP16 tensor-core forms of the current, against the FP64 oracle's own
 map, currents and front end (the oracle shares its many pixels among the host
 cores; nothing it computes comes from the GPU).

@@ -1,6 +1,6 @@
 """The 35-module beam spill (~1.2e6 segments, 50 interactions + 100 rock
 muons, t0 spread over 10 us) at full size through sim_event: the FP16
-tensor-core form against the FP32 direct form on every active pixel (the
+tensor-core form against the FP32 form on every active pixel (the
 oracle comparison of both forms, on a sample, is tests/test_gpu_scale.py)."""
 import numpy as np
 import pytest

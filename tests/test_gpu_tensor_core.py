@@ -2,7 +2,7 @@
 (sim_config.precision 1 = BF16, 2 = FP16 operands, FP32 accumulation in
 tensor memory) against the FP64 oracle, called through the C ABI.
 
-The tensor-core form sums exactly the terms of the FP32 direct form; it
+The tensor-core form sums exactly the terms of the FP32 form; it
 differs by the rounding of the charge tiles and of the table to the operand
 type (relative 2^-11 for FP16, 2^-8 for BF16, per operand) and by the
 fixed-point accumulation of the charge tiles (2^-12 e-).  Tolerances:
@@ -115,7 +115,7 @@ def _module_run(precision, seg, lut_dev):
 
 def test_tensor_core_module_event_against_direct_and_oracle():
     """The ~20k-segment module event at full size (several record chunks per
-    pixel group): every pixel against the FP32 direct form, sampled pixels
+    pixel group): every pixel against the FP32 form, sampled pixels
     against the oracle, and bitwise reproducibility of the call."""
     cfg = params.module_config()
     seg = events.module_event(cfg, seed=params.BASE["seed"] + 1)

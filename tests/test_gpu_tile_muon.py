@@ -1,7 +1,7 @@
 """The plain-method configuration at full size: one 70x70-pixel anode tile,
 one straight muon of 200 x 0.5 cm segments (Moyal dE/dx, MPV 2.1 MeV/cm,
 isotropic direction, centred), FP64 oracle vs the GPU path through the C ABI:
-every active pixel's current (FP32 direct and FP16 tensor-core forms) and the
+every active pixel's current (FP32 and FP16 tensor-core forms) and the
 hits end to end (bit-exact up to the oracle's first decision within the
 form's band, gpu_harness.BAND; tied pixels at most gpu_harness.tie_cap of the
 oracle's own tie probabilities)."""
