@@ -35,7 +35,8 @@
 //     16-tick arrival block every thread loads the 31 table values its 16
 //     ticks need (eight 16-byte shared reads; 4 words of padding after every
 //     16 keep consecutive threads' windows conflict-free) and adds
-//     q_d R[.] for each nonzero cell d (a CTA-uniform branch).
+//     q_d R[.] for each nonzero cell d (a CTA-uniform branch), two ticks per
+//     paired FMA instruction (fma.rn.f32x2).
 // Per tick the terms are summed in a fixed order (chunks in point order,
 // nodes increasing, blocks increasing, cells increasing) in FP32, and every
 // kKahanNodes nodes the partial sums are added into compensated (Kahan)
@@ -344,10 +345,35 @@ __device__ __forceinline__ void deposit(int *cell, uint32_t *mask, const Rec &r,
 // block's cells q_d: the thread's tick i gains q_d R[j0 + i - d + 15] =
 // q_d W[i - d + 15] (zero cells skipped: a CTA-uniform branch).  The cells
 // are in fixed point (x the chunk's scale).
-__device__ __forceinline__ void apply_node(const float *row, const int *cf, const uint32_t *mask, int L, int sig,
-                                           bool live, float (&acc)[kTPT])
+// The thread's 16 accumulators as packed pairs for the paired FP32 FMA
+// (fma.rn.f32x2, two lanes of independent round-to-nearest FMAs): cells with
+// odd d meet even-aligned pairs of the window, (W[m], W[m+1]) with m even, on
+// the tick pairs (2k, 2k+1) (ev); cells with even d meet them on the tick
+// pairs (2k+1, 2k+2) (od, k < 7; ticks 0 and 15 by single FMAs into ev).
+// Tick i is ev[i] + od[i] (od holding ticks 1..14).
+struct Acc {
+    float2 ev[8];
+    float2 od[7];
+};
+
+template <int D>
+__device__ __forceinline__ void fma_cell(float qf, const float2 (&Wp)[16], Acc &acc)
 {
-    const int t = threadIdx.x;
+    const float2 q2 = make_float2(qf, qf);
+    if (D & 1) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc.ev[k] = __ffma2_rn(q2, Wp[(2 * k - D + 15) >> 1], acc.ev[k]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) acc.od[k] = __ffma2_rn(q2, Wp[(2 * k + 16 - D) >> 1], acc.od[k]);
+        acc.ev[0].x = fmaf(qf, Wp[(15 - D) >> 1].y, acc.ev[0].x);        // tick 0: W[15 - D] (odd)
+        acc.ev[7].y = fmaf(qf, Wp[(30 - D) >> 1].x, acc.ev[7].y);        // tick 15: W[30 - D] (even)
+    }
+}
+
+__device__ __forceinline__ void apply_node(const float *row, const int *cf, const uint32_t *mask, int L, int sig,
+                                           int t, bool live, Acc &acc)
+{
 #pragma unroll 1
     for (int w = 0; w < kBlocks / 32; ++w) {
         uint32_t m = mask[w];
@@ -357,14 +383,12 @@ __device__ __forceinline__ void apply_node(const float *row, const int *cf, cons
             const int j0 = kTPT * (t - bl) + L - kTPT - sig;
             if (!live || j0 < -30 || j0 > L - 1) continue;      // the window misses the row
             const float *wp = row + row_word(j0 + kEdge);      // j0 + kEdge = 0 (mod 16)
-            float W[32];
+            float2 Wp[16];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const float4 v = *reinterpret_cast<const float4 *>(wp + 4 * k + 4 * (k >> 2));
-                W[4 * k] = v.x;
-                W[4 * k + 1] = v.y;
-                W[4 * k + 2] = v.z;
-                W[4 * k + 3] = v.w;
+                Wp[2 * k] = make_float2(v.x, v.y);
+                Wp[2 * k + 1] = make_float2(v.z, v.w);
             }
             int q[kBlk];
 #pragma unroll
@@ -375,14 +399,12 @@ __device__ __forceinline__ void apply_node(const float *row, const int *cf, cons
                 q[4 * k + 2] = v.z;
                 q[4 * k + 3] = v.w;
             }
-#pragma unroll
-            for (int d = 0; d < kBlk; ++d) {
-                if (q[d] != 0) {
-                    const float qf = (float)q[d];
-#pragma unroll
-                    for (int i = 0; i < kTPT; ++i) acc[i] = fmaf(qf, W[i - d + 15], acc[i]);
-                }
-            }
+#define LARSIM_CELL(D) \
+    if (q[D] != 0) fma_cell<D>((float)q[D], Wp, acc);
+            LARSIM_CELL(0) LARSIM_CELL(1) LARSIM_CELL(2) LARSIM_CELL(3) LARSIM_CELL(4) LARSIM_CELL(5)
+            LARSIM_CELL(6) LARSIM_CELL(7) LARSIM_CELL(8) LARSIM_CELL(9) LARSIM_CELL(10) LARSIM_CELL(11)
+            LARSIM_CELL(12) LARSIM_CELL(13) LARSIM_CELL(14) LARSIM_CELL(15)
+#undef LARSIM_CELL
         }
     }
 }
@@ -419,11 +441,21 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a, int6
         const int e0 = a.off[pi], e1 = a.off[pi + 1];
         float *out = a.current + (size_t)pi * T;
         for (int k0 = 0; k0 < T; k0 += kPass) {
-            const int t_lo = kTPT * tid - sig;                      // my first tick of the pass
+            // tick chunk of this thread: the warps take the four quarters of the pass in an order
+            // rotated per pixel.  The early quarters do the most work (a block reaches the ticks
+            // before its arrival), and warp w of every CTA runs on scheduler w: rotating spreads
+            // the heavy quarters of the CTAs sharing an SM over its schedulers.
+            const int tq = ((((tid >> 5) + (int)(it & 3)) & 3) << 5) | (tid & 31);
+            const int t_lo = kTPT * tq - sig;                       // my first tick of the pass
             const bool live = t_lo + kTPT > 0 && t_lo < kPass && k0 + t_lo < T;
-            float acc[kTPT], tot[kTPT], cmp[kTPT];
+            Acc acc;
+            float tot[kTPT], cmp[kTPT];
 #pragma unroll
-            for (int i = 0; i < kTPT; ++i) acc[i] = tot[i] = cmp[i] = 0.f;
+            for (int k = 0; k < 8; ++k) acc.ev[k] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < 7; ++k) acc.od[k] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < kTPT; ++i) tot[i] = cmp[i] = 0.f;
             GenState st{e0, 0};
             while (st.e < e1) {
                 // ---- 1. records of this chunk ------------------------------------------
@@ -523,13 +555,18 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a, int6
                         h0 = tid < nl.pre[4];
                         if (h0) node_entry(nl, sorted, tid, r0, c0);
                     }
-                    apply_node(s->row[x], s->u.cell[x], s->mask[u % 3], L, sig, live, acc);
+                    apply_node(s->row[x], s->u.cell[x], s->mask[u % 3], L, sig, tq, live, acc);
                     if (u % kKahanNodes == kKahanNodes - 1 || u == nn - 1) {
 #pragma unroll
                         for (int i = 0; i < kTPT; ++i) {
-                            kahan_add(tot[i], cmp[i], acc[i] * inv_sc);
-                            acc[i] = 0.f;
+                            float v = (i & 1) ? acc.ev[i >> 1].y : acc.ev[i >> 1].x;
+                            if (i >= 1 && i <= 14) v = __fadd_rn(v, (i & 1) ? acc.od[i >> 1].x : acc.od[(i >> 1) - 1].y);
+                            kahan_add(tot[i], cmp[i], v * inv_sc);
                         }
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) acc.ev[k] = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int k = 0; k < 7; ++k) acc.od[k] = make_float2(0.f, 0.f);
                     }
                     if (nxt) {
                         int *cell = s->u.cell[x ^ 1];
