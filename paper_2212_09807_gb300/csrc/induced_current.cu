@@ -108,7 +108,7 @@ struct __align__(16) Smem {
     } u;
     int hist[kMaxBins + 1];                     // bin counts; after the scatter, the end of each bin
     unsigned char nflag[kMaxBins];
-    unsigned short nodes[kMaxBins];
+    unsigned short nodes[kMaxBins];             // nodes reached, as (nx << 6) | ny
     uint32_t mask[3][kBlocks / 32];             // arrival blocks present, per node (three in flight)
     int scan_tmp[kWarps + 1];
     int warp_n[kWarps];
@@ -246,9 +246,9 @@ __device__ int gen_chunk(const CurArgs &a, Smem *s, GenState &st, int e1, int ix
 // each: elements 4 t + 512 i, i < 4) into the staged layout; elements at or
 // beyond L are zero-filled.  Rows are 16-byte aligned, and four values at
 // p = 0 (mod 4) stay inside one 16-position group.
-__device__ __forceinline__ void stage_row(float *dst, const CurArgs &a, int n)
+__device__ __forceinline__ void stage_row(float *dst, const CurArgs &a, int nxy)
 {
-    const float *row = a.lut + (size_t)n * a.ld;
+    const float *row = a.lut + (size_t)((nxy >> 6) * a.nb + (nxy & 63)) * a.ld;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int j = 4 * threadIdx.x + 512 * i;
@@ -272,7 +272,7 @@ struct NodeLists {
 __device__ __forceinline__ NodeLists node_lists(const Smem *s, int n, int nb)
 {
     NodeLists L;
-    const int nx = n / nb, ny = n - nx * nb;
+    const int nx = n >> 6, ny = n & 63;
     L.pre[0] = 0;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -511,7 +511,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a, int6
                     int pf = block_scan(sf, s, &tf);            // (its barriers also order the scatter)
 #pragma unroll
                     for (int i = 0; i < kB; ++i)
-                        if (fl[i]) s->nodes[pf++] = (unsigned short)(tid * kB + i);
+                        if (fl[i]) {                            // node as (nx << 6) | ny (nb <= 45)
+                            const int n = tid * kB + i, nx = n / nb;
+                            s->nodes[pf++] = (unsigned short)((nx << 6) | (n - nx * nb));
+                        }
                     if (tid == 0) s->n_nodes = tf;
                 }
                 __syncthreads();
