@@ -7,7 +7,8 @@ Tolerances (stated once, used below):
   * pixel map: set-equal, except pairs whose oracle distance margin is within
     1e-5 cm of the map radius (FP32 geometry on the GPU);
   * current (FP32 form on the CUDA cores): per pixel ||I_gpu - I_ref||_inf <= 1e-4 ||I_ref||_inf
-    (hard) with the median <= 1e-5; every prefix sum of each pixel's current
+    (hard; faint neighbour pixels whose bipolar current nearly cancels reach ~1e-4)
+    with the median <= 1e-6; every prefix sum of each pixel's current
     (the charge integrated by each tick) within 1e-5 of the pixel's largest one
     plus 2e-6 of the event's peak pixel charge (gpu_harness.prefix_charge_ok:
     the floor covers pixels fed through small interpolation weights, whose
@@ -34,7 +35,7 @@ from gpu_harness import (BAND, Steps, compare_pixel_hits, current_errors, hits_o
 pytestmark = pytest.mark.gpu
 
 MAP_BAND = 1e-5
-CUR_HARD, CUR_MED, Q_TOL = 1e-4, 1e-5, 1e-5
+CUR_HARD, CUR_MED, Q_TOL = 1e-4, 1e-6, 1e-5
 
 
 def _edge_segments(cfg):
@@ -160,6 +161,7 @@ def test_induced_current_all_pixels(small):
     rel, qrel, ref, q_ok, q_worst = _current_parity(small["cfg"], small["seg"], small["lut_dev"], small["lut64"],
                                                     event_id=5)
     assert len(rel) > 200
+    print(f"all pixels: rel max {rel.max():.2e} med {np.median(rel):.2e}, prefix-charge worst {q_worst:.2e}")
     assert rel.max() <= CUR_HARD, rel.max()
     assert np.median(rel) <= CUR_MED, np.median(rel)
     assert q_ok, q_worst
@@ -181,6 +183,7 @@ def test_induced_current_variants(case):
     seg = _event(cfg, 300 + len(case), 25, t_range=tr)
     lut_dev, lut64 = lut_pair(cfg, **lut_kw)
     rel, qrel, _, q_ok, q_worst = _current_parity(cfg, seg, lut_dev, lut64, event_id=11)
+    print(f"{case}: rel max {rel.max():.2e} med {np.median(rel):.2e}, prefix-charge worst {q_worst:.2e}")
     assert rel.max() <= CUR_HARD, rel.max()
     assert np.median(rel) <= CUR_MED
     if case != "bipolar":                  # bipolar pixels can integrate to ~0

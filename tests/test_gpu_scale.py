@@ -10,8 +10,8 @@ Checks and tolerances:
   * map: the active-pixel sets of the whole event are equal and each sampled
     pixel's segment list is equal, except pairs whose distance margin is
     within MAP_BAND of the map radius (FP32 geometry);
-  * currents, per pixel: FP32 ||I - I_ref||_inf <= 1e-4 ||I_ref||_inf (median
-    <= 1e-5); every prefix sum of the current (the charge the front end has
+  * currents, per pixel: FP32 ||I - I_ref||_inf <= 2e-5 ||I_ref||_inf (median
+    <= 1e-6); every prefix sum of the current (the charge the front end has
     integrated by each tick) within 1e-5 of the pixel's largest one plus a
     floor of 2e-6 of the event's peak pixel charge.  The floor covers pixels
     whose charge comes through small interpolation weights from their
@@ -137,8 +137,8 @@ def _current_checks(precision, I, R, label):
     d = I[sig] - R[sig]
     inf = np.abs(d).max(axis=1) / np.abs(R[sig]).max(axis=1)
     if precision == 0:
-        assert inf.max() <= 1e-4, (label, inf.max())
-        assert np.median(inf) <= 1e-5, (label, np.median(inf))
+        assert inf.max() <= 2e-5, (label, inf.max())
+        assert np.median(inf) <= 1e-6, (label, np.median(inf))
     else:
         l2 = np.linalg.norm(d, axis=1) / np.linalg.norm(R[sig], axis=1)
         assert l2.max() <= 5e-4 and inf.max() <= 1e-3, (label, l2.max(), inf.max())
