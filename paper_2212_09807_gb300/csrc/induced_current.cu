@@ -44,6 +44,8 @@
 // FP32 sum would drift by ~1e-5 of its value.  A pixel's current depends on
 // its own segments only: the same bits alone, in a batch or in any range of
 // a call.
+#include <algorithm>
+
 #include "current_records.cuh"
 
 namespace larsim {
@@ -56,7 +58,7 @@ constexpr int kSpan = kThreads * kTPT;          // ticks the threads hold
 constexpr int kPass = kSpan - kTPT;             // ticks per pass (see tick_shift)
 constexpr int kBlk = 16;                        // arrival ticks per block
 constexpr int kBlocks = 256;                    // blocks of a pass: relative arrival ticks [0, 4096)
-constexpr int kRecCap = 65536;                  // records per chunk (per-CTA scratch; ~1 chunk per pixel)
+constexpr int kRecCap = 65536;                  // records per chunk at most (per-CTA scratch; ~1 chunk per pixel)
 constexpr int kMaxBins = 2048;                  // nb * nb <= kMaxBins
 constexpr int kMaxRow = 2048;                   // table length nt <= kMaxRow
 constexpr int kSegBatch = 128;                  // segments loaded together by the generation
@@ -94,6 +96,7 @@ struct CurArgs {
     Rec *recs;                                  // [grid][kRecCap], point order
     Rec *sorted;                                // [grid][kRecCap], bin order
     unsigned long long *n_cells;                // counts[5]: nonzero charge cells (statistics)
+    int rec_cap;                                // records per chunk (<= kRecCap)
 };
 
 struct __align__(16) Smem {
@@ -219,7 +222,7 @@ __device__ int gen_chunk(const CurArgs &a, Smem *s, GenState &st, int e1, int ix
                 wb += (w2 < warp) ? c2 : 0;
                 nq += c2;
             }
-            if (nrec + nq > kRecCap) {           // chunk full: process it, then redo this step
+            if (nrec + nq > a.rec_cap) {         // chunk full: process it, then redo this step
                 st.c0 = c;
                 __syncthreads();
                 return nrec;
@@ -725,6 +728,7 @@ cudaError_t launch_induced_current(const sim_config &c, const sim_segments &s, c
     a.recs = reinterpret_cast<Rec *>(p + lay.recs);
     a.sorted = reinterpret_cast<Rec *>(p + lay.sorted);
     a.n_cells = reinterpret_cast<unsigned long long *>(const_cast<int64_t *>(counts) + 5);
+    a.rec_cap = c.tc_record_chunk > 0 ? std::min(c.tc_record_chunk, kRecCap) : kRecCap;
     cudaError_t e = cudaMemsetAsync(p + lay.queue, 0, 512, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(const_cast<int64_t *>(counts) + 4, 0, 2 * sizeof(int64_t), st);
     if (e != cudaSuccess) return e;

@@ -201,3 +201,31 @@ def test_full_size_event_against_oracle(ref, precision):
     _hit_checks(r, precision, gh, label)
     del run
     torch.cuda.empty_cache()
+
+
+def test_fp32_form_in_short_record_chunks(ref):
+    """The FP32 form with chunks of 4096 records (tc_record_chunk): the module
+    event's dense pixels then take several chunks each (a pixel's records are
+    generated, binned and applied chunk by chunk, the generation resuming
+    where the full chunk stopped); every pixel against the same oracle, with
+    the same tolerances."""
+    if ref["name"] != "module":
+        pytest.skip("module event only")
+    r = ref
+    cfg = dict(r["cfg"], precision=0, tc_record_chunk=4096)
+    lut_dev = torch.as_tensor(r["lut"], device="cuda")
+    seg, n = r["seg"], len(r["seg"]["x0"])
+    run, (n_pairs, n_pix, n_hits, _) = _run(cfg, lut_dev, seg, r["eid"])
+    act = run.active_pixels(n, n_pix).cpu().numpy()
+    pos = np.searchsorted(act, r["pix"])
+    assert np.all(pos < n_pix) and np.array_equal(act[pos], r["pix"])
+    # candidate points of the densest pixels: several times a chunk (about half become records)
+    ns = r["d"]["n_samples"].astype(np.int64) * int(cfg["mc_per_sample"])
+    cand = np.array([ns[r["segs"][r["off"][j]:r["off"][j + 1]]].sum() for j in range(len(r["pix"]))])
+    assert (cand > 4 * 4096).sum() > 100, cand.max()
+    I = run.current(n, n_pix)[torch.as_tensor(pos, device="cuda")].cpu().numpy().astype(np.float64)
+    _current_checks(0, I, r["I"], "module precision 0, 4096-record chunks")
+    gh = run.hits.to_numpy(min(n_hits, run.hits.capacity))
+    _hit_checks(r, 0, gh, "module precision 0, 4096-record chunks")
+    del run
+    torch.cuda.empty_cache()
