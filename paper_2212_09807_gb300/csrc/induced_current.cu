@@ -29,12 +29,12 @@
 //  3. node loop, pipelined over two barriers per node: the charge of node
 //     n + 1 is deposited into fixed-point cells (integer shared-memory
 //     atomics: order-independent, so the result is bitwise reproducible; the
-//     scale, a power of two, follows the node's entries and the chunk's
-//     largest weight, so that taps round to ~1e-9 of the node's charge)
-//     and its table row copied in (cp.async), while node n is applied: for each present
-//     16-tick arrival block every thread loads the 31 table values its 16
-//     ticks need (eight 16-byte shared reads; 4 words of padding after every
-//     16 keep consecutive threads' windows conflict-free) and adds
+//     scale, a power of two, follows the chunk's largest node entry count and
+//     largest weight, so that taps round to ~1e-9 of a node's charge) and its
+//     table row copied in (cp.async), while node n is applied: for each
+//     present 16-tick arrival block every thread loads the 31 table values its
+//     16 ticks need (eight 16-byte shared reads; 4 words of padding after
+//     every 16 keep consecutive threads' windows conflict-free) and adds
 //     q_d R[.] for each nonzero cell d (a CTA-uniform branch), two ticks per
 //     paired FMA instruction (fma.rn.f32x2).
 // Per tick the terms are summed in a fixed order (chunks in point order,
@@ -102,7 +102,7 @@ struct CurArgs {
 struct __align__(16) Smem {
     float row[2][kRowWords];                    // staged table rows of two nodes
     union {
-        int cell[2][kBlocks * kBlk];            // charge cells of two nodes (fixed point, then FP32 in place)
+        int cell[2][kBlocks * kBlk];            // fixed-point charge cells of two nodes [block][tick]
         struct {
             Anchor anc[kSegBatch];              // a batch of the pixel's segments
             int sg[kSegBatch];
@@ -265,8 +265,8 @@ __device__ __forceinline__ void stage_row(float *dst, const CurArgs &a, int nxy)
 
 __device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// The four record lists of node n (corner c of the bins (nx - (c & 1),
-// ny - (c >> 1))) in bin order: begin of each and prefix counts.
+// The four record lists of node n = (nx << 6) | ny (corner c of the bins
+// (nx - (c & 1), ny - (c >> 1))) in bin order: begin of each and prefix counts.
 struct NodeLists {
     int beg[4];
     int pre[5];
