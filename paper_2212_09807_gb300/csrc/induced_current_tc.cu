@@ -1075,19 +1075,27 @@ __device__ void flush_acc(const TcArgs &a, TcSmem *s, uint32_t tm, uint32_t &flu
     __syncwarp();
     const bool ok = bar_wait(s, &s->done, flushes & 1, true) && !*(volatile int *)&s->abort;
     tc_fence_after();
+    // the rows' previous values of tile t + 1 are loaded while tile t is read and stored
+    const int lrow = (kTileM - 1) - (32 * warp + lane);     // accumulator rows run backwards in a tile
+    float old[kGroup], nxt[kGroup];
+    auto load_old = [&](int t, float (&dst)[kGroup]) {
+        const int tick = k0 + kTileM * t + lrow;
+        const bool use = ok && !first && k0 + kTileM * t < T && tick < T;
+#pragma unroll
+        for (int p = 0; p < kGroup; ++p) dst[p] = (use && p < npg) ? rows[tick + s->rowoff[p]] : 0.f;
+    };
+    load_old(0, old);
     for (int t = 0; t < kTiles; ++t) {
         const int tick0 = k0 + kTileM * t;
         if (tick0 >= T) break;
+        if (t + 1 < kTiles) load_old(t + 1, nxt);
         const uint32_t ta = tm + ((uint32_t)(32 * warp) << 16) + kGroup * t;
         float v[32];
         tmem_ld32(ta, v);
-        const int tick = tick0 + (kTileM - 1) - (32 * warp + lane);   // accumulator rows run backwards in a tile
+        const int tick = tick0 + lrow;
         if (ok && tick < T) {
             float *base = rows + tick;
             if (!first) {
-                float old[kGroup];                  // all loads in flight before the stores
-#pragma unroll
-                for (int p = 0; p < kGroup; ++p) old[p] = p < npg ? base[s->rowoff[p]] : 0.f;
 #pragma unroll
                 for (int p = 0; p < kGroup; ++p) v[p] = fmaf(v[p], a.out_scale, old[p]);
             } else {
@@ -1099,6 +1107,8 @@ __device__ void flush_acc(const TcArgs &a, TcSmem *s, uint32_t tm, uint32_t &flu
                 if (p < npg) base[s->rowoff[p]] = v[p];
         }
         tmem_zero32(ta);
+#pragma unroll
+        for (int p = 0; p < kGroup; ++p) old[p] = nxt[p];
     }
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     tc_fence_before();
