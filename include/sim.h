@@ -105,9 +105,9 @@ typedef struct sim_config {
      * per CTA chunk (a power of two, 4096..1048576; default 1048576 for calls
      * sized for at least 131072 active pixels, else 262144; the workspace holds
      * two record buffers of 32 bytes per record and CTA); FP32 form: resident
-     * CTAs per SM (1..3, default 3; results bitwise the same for every value)
+     * CTAs per SM (1..4, default 4; results bitwise the same for every value)
      * and, from tc_record_chunk, the records per chunk of a pixel (at most and
-     * by default 65536).  paper_2212_09807_gb300/tune.py picks them by timing a
+     * by default 65520).  paper_2212_09807_gb300/tune.py picks them by timing a
      * sample. */
     int32_t tc_units_per_sm, tc_record_chunk, direct_ctas_per_sm;
     /* polls of a bounded device-side wait of the tensor-core forms before it

@@ -38,7 +38,7 @@ bool cfg_ok(const sim_config *c)
     if (c->tc_record_chunk != 0 && (c->tc_record_chunk < 4096 || c->tc_record_chunk > (1 << 20) ||
                                     (c->tc_record_chunk & (c->tc_record_chunk - 1)) != 0))
         return false;
-    if (c->direct_ctas_per_sm < 0 || c->direct_ctas_per_sm > 3) return false;
+    if (c->direct_ctas_per_sm < 0 || c->direct_ctas_per_sm > 4) return false;
     if (c->wait_spin_limit < 0 || c->wait_spin_limit > (1 << 30)) return false;
     return true;
 }

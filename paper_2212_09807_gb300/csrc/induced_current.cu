@@ -17,7 +17,7 @@
 // instead of eight per record and tick.
 //
 // Design: one CTA of 128 threads per active pixel (dynamic queue, pixels of
-// the most candidate points first; three CTAs per SM), output stationary:
+// the most candidate points first; four CTAs per SM), output stationary:
 // thread t holds 16 consecutive ticks of a 2032-tick pass in registers.
 //  1. records: the pixel's segments are taken 128 at a time (one thread
 //     loads each anchor) and their candidate points walked 128 per step
@@ -58,13 +58,18 @@ constexpr int kSpan = kThreads * kTPT;          // ticks the threads hold
 constexpr int kPass = kSpan - kTPT;             // ticks per pass (see tick_shift)
 constexpr int kBlk = 16;                        // arrival ticks per block
 constexpr int kBlocks = 256;                    // blocks of a pass: relative arrival ticks [0, 4096)
-constexpr int kRecCap = 65536;                  // records per chunk at most (per-CTA scratch; ~1 chunk per pixel)
+constexpr int kRecCap = 65520;                  // records per chunk at most (per-CTA scratch; ~1 chunk per pixel;
+                                                // bin ends fit 16 bits)
 constexpr int kMaxBins = 2048;                  // nb * nb <= kMaxBins
 constexpr int kMaxRow = 2048;                   // table length nt <= kMaxRow
 constexpr int kSegBatch = 128;                  // segments loaded together by the generation
 constexpr int kKahanNodes = 8;                  // nodes per plain FP32 partial sum
-// Staged table row: value j at position p = j + kEdge, word address
-// p + 4 (p / 16) (4 words of padding after every 16).  Thread t holds the
+constexpr int kMaxNb = 45;                      // nb <= 45 (nb * nb <= kMaxBins)
+constexpr int kNodeWords = (kMaxNb << 6) / 32;  // bit (nx << 6) | ny per node
+// Staged table row: value j at position p = j + kEdge, in 16-byte chunk
+// c = p / 4 stored at chunk c ^ ((c / 8) mod 8) (an XOR swizzle within each
+// group of 8 chunks: the 16-byte window reads of 8 consecutive threads, whose
+// windows are 4 chunks apart, fall on 8 different bank groups).  Thread t holds the
 // pass ticks 16 t - sigma + i (i < 16), sigma = L mod 16, so that its
 // 32-value window of block bl starts at j0 = 16 (t - bl) + L - 16 - sigma, a
 // multiple of 16; windows that touch the row have j0 in [-30, L - 1], so
@@ -73,9 +78,9 @@ constexpr int kKahanNodes = 8;                  // nodes per plain FP32 partial 
 // a pass writes its first kPass ticks.
 constexpr int kEdge = 32;
 constexpr int kRowPos = kMaxRow + kEdge + 48;
-constexpr int kRowWords = kRowPos + kRowPos / 4 + 4;
+constexpr int kRowWords = ((kRowPos / 4 + 7) / 8) * 32;
 
-__device__ __forceinline__ int row_word(int p) { return p + 4 * (p >> 4); }
+__device__ __forceinline__ int row_chunk(int c) { return c ^ ((c >> 3) & 7); }
 __host__ __device__ constexpr int tick_shift(int L) { return L & 15; }
 
 struct CurArgs {
@@ -107,11 +112,11 @@ struct __align__(16) Smem {
             Anchor anc[kSegBatch];              // a batch of the pixel's segments
             int sg[kSegBatch];
             int coff[kSegBatch + 1];            // candidate offsets of the batch
+            int hist[kMaxBins + 1];             // bin counts, then scatter cursors
         } g;
     } u;
-    int hist[kMaxBins + 1];                     // bin counts; after the scatter, the end of each bin
-    unsigned char nflag[kMaxBins];
-    unsigned short nodes[kMaxBins];             // nodes reached, as (nx << 6) | ny
+    unsigned short bend[kMaxBins];              // end of each bin in bin order (the node loop's lists)
+    uint32_t nfl[kNodeWords];                   // nodes reached: bit (nx << 6) | ny
     uint32_t mask[3][kBlocks / 32];             // arrival blocks present, per node (three in flight)
     int scan_tmp[kWarps + 1];
     int warp_n[kWarps];
@@ -121,7 +126,7 @@ struct __align__(16) Smem {
     int emax;
 };
 
-static_assert(sizeof(Smem) <= 75 * 1024, "three CTAs per SM");
+static_assert(sizeof(Smem) + 1024 <= 233472 / 4, "four CTAs per SM");
 
 // Exclusive scan of one int per thread across the CTA; returns the prefix
 // and the total in *tot.
@@ -172,7 +177,7 @@ struct GenState {
 };
 
 // Records of the pixel (centre (ix, iy)) from its segments [st.e, e1), in
-// point order, into recs, with the bin histogram in s->hist.  Stops when
+// point order, into recs, with the bin histogram in s->u.g.hist.  Stops when
 // the next step of 128 candidates would overflow the chunk (st keeps the
 // place) or after the last segment (st.e = e1).  Returns the records.
 __device__ int gen_chunk(const CurArgs &a, Smem *s, GenState &st, int e1, int ix, int iy, uint64_t key,
@@ -229,7 +234,7 @@ __device__ int gen_chunk(const CurArgs &a, Smem *s, GenState &st, int e1, int ix
             }
             if (ok) {
                 recs[nrec + wb + __popc(m & ((1u << lane) - 1u))] = r;
-                atomicAdd(&s->hist[r.b0], 1);
+                atomicAdd(&s->u.g.hist[r.b0], 1);
             }
             // weights are >= 0: their FP32 bits order as integers
             const int wb_max = __reduce_max_sync(
@@ -248,7 +253,7 @@ __device__ int gen_chunk(const CurArgs &a, Smem *s, GenState &st, int e1, int ix
 // Thread t's share of a table row, copied asynchronously (cp.async, 16 bytes
 // each: elements 4 t + 512 i, i < 4) into the staged layout; elements at or
 // beyond L are zero-filled.  Rows are 16-byte aligned, and four values at
-// p = 0 (mod 4) stay inside one 16-position group.
+// p = 0 (mod 4) form one chunk.
 __device__ __forceinline__ void stage_row(float *dst, const CurArgs &a, int nxy)
 {
     const float *row = a.lut + (size_t)((nxy >> 6) * a.nb + (nxy & 63)) * a.ld;
@@ -257,7 +262,7 @@ __device__ __forceinline__ void stage_row(float *dst, const CurArgs &a, int nxy)
         const int j = 4 * threadIdx.x + 512 * i;
         const int bytes = j < a.nt ? 4 * min(4, a.nt - j) : 0;
         const float *src = row + (j < a.nt ? j : 0);
-        const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + row_word(j + kEdge));
+        const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + 4 * row_chunk((j + kEdge) >> 2));
         asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(bytes) : "memory");
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
@@ -283,8 +288,8 @@ __device__ __forceinline__ NodeLists node_lists(const Smem *s, int n, int nb)
         int b = 0, e = 0;
         if (bx >= 0 && by >= 0) {
             const int bin = bx * nb + by;
-            b = bin > 0 ? s->hist[bin - 1] : 0;
-            e = s->hist[bin];
+            b = bin > 0 ? s->bend[bin - 1] : 0;
+            e = s->bend[bin];
         }
         L.beg[c] = b;
         L.pre[c + 1] = L.pre[c] + (e - b);
@@ -314,6 +319,20 @@ __device__ __forceinline__ float node_scale(int n_entries, float wmax)
     const int ex = ((__float_as_int(x) >> 23) & 0xff) - 127;      // floor(log2 x) (x normal)
     const int k = min(100, max(-100, 29 - ex));
     return __int_as_float((k + 127) << 23);
+}
+
+// The first node after `after` in the bit set (-1: none); uniform across the CTA.
+__device__ __forceinline__ int next_node(const uint32_t *nfl, int after)
+{
+    const int x = after + 1;
+    int w = x >> 5;
+    if (w >= kNodeWords) return -1;
+    uint32_t m = nfl[w] & (0xffffffffu << (x & 31));
+    while (m == 0u) {
+        if (++w >= kNodeWords) return -1;
+        m = nfl[w];
+    }
+    return (w << 5) + __ffs(m) - 1;
 }
 
 // Deposits the two ticks of a record's corner c into the fixed-point cells;
@@ -385,11 +404,11 @@ __device__ __forceinline__ void apply_node(const float *row, const int *cf, cons
             m &= m - 1;
             const int j0 = kTPT * (t - bl) + L - kTPT - sig;
             if (!live || j0 < -30 || j0 > L - 1) continue;      // the window misses the row
-            const float *wp = row + row_word(j0 + kEdge);      // j0 + kEdge = 0 (mod 16)
+            const int c0 = (j0 + kEdge) >> 2;                   // j0 + kEdge = 0 (mod 16)
             float2 Wp[16];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-                const float4 v = *reinterpret_cast<const float4 *>(wp + 4 * k + 4 * (k >> 2));
+                const float4 v = *reinterpret_cast<const float4 *>(row + 4 * row_chunk(c0 + k));
                 Wp[2 * k] = make_float2(v.x, v.y);
                 Wp[2 * k + 1] = make_float2(v.z, v.w);
             }
@@ -412,7 +431,7 @@ __device__ __forceinline__ void apply_node(const float *row, const int *cf, cons
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a, int64_t n_items_cap)
+__global__ void __launch_bounds__(kThreads, 4) k_induced_current(CurArgs a, int64_t n_items_cap)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem *s = reinterpret_cast<Smem *>(smem_raw);
@@ -462,8 +481,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a, int6
             GenState st{e0, 0};
             while (st.e < e1) {
                 // ---- 1. records of this chunk ------------------------------------------
-                for (int b = tid; b <= nb2; b += kThreads) s->hist[b] = 0;
-                for (int b = tid; b < nb2; b += kThreads) s->nflag[b] = 0;
+                for (int b = tid; b <= nb2; b += kThreads) s->u.g.hist[b] = 0;
+                if (tid < kNodeWords) s->nfl[tid] = 0u;
                 if (tid == 0) s->wmax = 0, s->emax = 0;
                 __syncthreads();
                 const int nrec = gen_chunk(a, s, st, e1, ix, iy, key, seg0, recs);
@@ -475,7 +494,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a, int6
 #pragma unroll
                     for (int i = 0; i < kB; ++i) {
                         const int b = tid * kB + i;
-                        v[i] = b < nb2 ? s->hist[b] : 0;
+                        v[i] = b < nb2 ? s->u.g.hist[b] : 0;
                         sv += v[i];
                     }
                     int tv;
@@ -484,13 +503,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a, int6
                     for (int i = 0; i < kB; ++i) {
                         const int b = tid * kB + i;
                         if (b < nb2) {
-                            s->hist[b] = pv;                  // scatter cursor, then the end of bin b
+                            s->u.g.hist[b] = pv;              // scatter cursor, then the end of bin b
                             if (v[i] > 0) {                   // the bin's corner nodes inside the table
-                                const int bx = b / nb, by = b - bx * nb;
-                                s->nflag[b] = 1;
-                                if (bx + 1 < nb) s->nflag[b + nb] = 1;
-                                if (by + 1 < nb) s->nflag[b + 1] = 1;
-                                if (bx + 1 < nb && by + 1 < nb) s->nflag[b + nb + 1] = 1;
+                                const int bx = b / nb, by = b - bx * nb, id = (bx << 6) | by;
+                                atomicOr(&s->nfl[id >> 5], 1u << (id & 31));
+                                if (bx + 1 < nb) atomicOr(&s->nfl[(id + 64) >> 5], 1u << ((id + 64) & 31));
+                                if (by + 1 < nb) atomicOr(&s->nfl[(id + 1) >> 5], 1u << ((id + 1) & 31));
+                                if (bx + 1 < nb && by + 1 < nb)
+                                    atomicOr(&s->nfl[(id + 65) >> 5], 1u << ((id + 65) & 31));
                             }
                         }
                         pv += v[i];
@@ -499,46 +519,36 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a, int6
                 __syncthreads();
                 for (int i = tid; i < nrec; i += kThreads) {
                     const Rec r = recs[i];
-                    sorted[atomicAdd(&s->hist[r.b0], 1)] = r;
-                }
-                {
-                    constexpr int kB = kMaxBins / kThreads;
-                    int fl[kB], sf = 0;
-#pragma unroll
-                    for (int i = 0; i < kB; ++i) {
-                        const int b = tid * kB + i;
-                        fl[i] = b < nb2 ? s->nflag[b] : 0;
-                        sf += fl[i];
-                    }
-                    int tf;
-                    int pf = block_scan(sf, s, &tf);            // (its barriers also order the scatter)
-#pragma unroll
-                    for (int i = 0; i < kB; ++i)
-                        if (fl[i]) {                            // node as (nx << 6) | ny (nb <= 45)
-                            const int n = tid * kB + i, nx = n / nb;
-                            s->nodes[pf++] = (unsigned short)((nx << 6) | (n - nx * nb));
-                        }
-                    if (tid == 0) s->n_nodes = tf;
+                    sorted[atomicAdd(&s->u.g.hist[r.b0], 1)] = r;
                 }
                 __syncthreads();
+                for (int b = tid; b < nb2; b += kThreads) s->bend[b] = (unsigned short)s->u.g.hist[b];
+                {
+                    const int cnt = tid < kNodeWords ? __popc(s->nfl[tid]) : 0;
+                    int tf;
+                    block_scan(cnt, s, &tf);                    // (its barriers also publish bend)
+                    if (tid == 0) s->n_nodes = tf;
+                }
                 {   // largest node entry count (a deterministic bound of the cells with the chunk's weights)
-                    const int nn0 = s->n_nodes;
                     int em = 0;
-                    for (int i = tid; i < nn0; i += kThreads) em = max(em, node_lists(s, s->nodes[i], nb).pre[4]);
+                    for (int i = tid; i < kNodeWords * 32; i += kThreads)
+                        if ((s->nfl[i >> 5] >> (i & 31)) & 1u) em = max(em, node_lists(s, i, nb).pre[4]);
                     em = __reduce_max_sync(0xffffffffu, em);
                     if ((tid & 31) == 0) atomicMax(&s->emax, em);
                 }
+                __syncthreads();                                // the union becomes the cell buffers
                 for (int i = tid; i < 2 * kBlocks * kBlk / 4; i += kThreads)
                     reinterpret_cast<int4 *>(&s->u.cell[0][0])[i] = make_int4(0, 0, 0, 0);
                 if (tid < 3 * (kBlocks / 32)) (&s->mask[0][0])[tid] = 0u;
                 __syncthreads();
                 // ---- 3. node loop ----------------------------------------------------------
                 const int nn = s->n_nodes;
-                stage_row(s->row[0], a, s->nodes[0]);
+                int n_cur = next_node(s->nfl, -1);
+                stage_row(s->row[0], a, n_cur);
                 const float sc_next = node_scale(s->emax, __int_as_float(s->wmax));   // of the whole chunk
                 const float inv_sc = 1.f / sc_next;
                 {
-                    const NodeLists nl = node_lists(s, s->nodes[0], nb);
+                    const NodeLists nl = node_lists(s, n_cur, nb);
                     for (int e = tid; e < nl.pre[4]; e += kThreads) {
                         Rec r;
                         int c;
@@ -551,13 +561,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a, int6
                 for (int u = 0; u < nn; ++u) {
                     const int x = u & 1;
                     const bool nxt = u + 1 < nn;
-                    if (nxt) stage_row(s->row[x ^ 1], a, s->nodes[u + 1]);   // lands before the next apply
+                    const int n_nxt = nxt ? next_node(s->nfl, n_cur) : -1;
+                    if (nxt) stage_row(s->row[x ^ 1], a, n_nxt);   // lands before the next apply
                     NodeLists nl;
                     Rec r0;
                     int c0 = 0;
                     bool h0 = false;
                     if (nxt) {                                  // first entry of node u + 1 in flight
-                        nl = node_lists(s, s->nodes[u + 1], nb);
+                        nl = node_lists(s, n_nxt, nb);
                         h0 = tid < nl.pre[4];
                         if (h0) node_entry(nl, sorted, tid, r0, c0);
                     }
@@ -592,6 +603,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_induced_current(CurArgs a, int6
                     for (int i = tid; i < kBlocks * kBlk / 4; i += kThreads)
                         reinterpret_cast<int4 *>(s->u.cell[x])[i] = make_int4(0, 0, 0, 0);
                     __syncthreads();
+                    n_cur = n_nxt;
                 }
             }
             // compensated totals (zero for a pixel without records)
@@ -647,7 +659,7 @@ __global__ void k_fp_order(const int64_t *counts, int64_t pix_cap, int64_t begin
     order[start[c] + atomicAdd(&cursor[c], 1)] = (int32_t)j;
 }
 
-int grid_for(int64_t pix_cap, int ctas_per_sm = 3)
+int grid_for(int64_t pix_cap, int ctas_per_sm = 4)
 {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -716,7 +728,7 @@ cudaError_t launch_induced_current(const sim_config &c, const sim_segments &s, c
     a.g = geo_of(c);
     a.dp = drift_par_of(c);
     // the scratch is sized for the default grid: a smaller configured one fits it
-    const int grid = grid_for(pix_cap, c.direct_ctas_per_sm > 0 ? c.direct_ctas_per_sm : 3);
+    const int grid = grid_for(pix_cap, c.direct_ctas_per_sm > 0 ? c.direct_ctas_per_sm : 4);
     const FpLayout lay = fp_layout(grid_for(pix_cap), pix_cap);
     char *p = reinterpret_cast<char *>(scratch);
     a.queue = reinterpret_cast<int *>(p + lay.queue);

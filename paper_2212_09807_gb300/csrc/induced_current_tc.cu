@@ -1220,14 +1220,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_induced_current_tc(TcArgs a)
                         issue_mmas(a, s, warp, s->nodes + u0, cnt, S, q, k0, n_mma, im_last);
                     }
                     S += cnt;
-                    __syncthreads();
+                    // warps 0-3 flush the accumulators while the builders go on with the next
+                    // window's first operand batches (the flush touches none of their state;
+                    // the operand buffers hand over through their mbarriers as always)
                     if (warp < 4) {
+                        __syncwarp();
                         q = __shfl_sync(0xffffffffu, q, 0);   // the two roles agree unless a wait gave up
                         flush_acc(a, s, tm, flushes, k0, rows, npg, first);
+                        // every accumulator lane is read and zeroed before an issuer starts the next window
+                        asm volatile("bar.sync 2, 128;" ::: "memory");
                     }
                     first = false;
-                    __syncthreads();
                 }
+                __syncthreads();                // the chunk's windows are done (the next chunk regenerates)
             }
             // a pass without records still writes its (zero) currents
             if (first) {

@@ -22,7 +22,7 @@ from . import sim
 
 TC_UNITS = (1, 2, 4, 8)
 TC_CHUNKS = (1 << 16, 1 << 17, 1 << 18, 1 << 19, 1 << 20)
-DIRECT_CTAS = (1, 2, 3)
+DIRECT_CTAS = (2, 3, 4)
 
 
 def candidates(precision: int) -> list[dict]:

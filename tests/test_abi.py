@@ -107,7 +107,7 @@ def test_tuning_fields_are_checked(L):
     from synth import params
     b = C.c_size_t()
     for bad in (dict(tc_units_per_sm=17), dict(tc_record_chunk=5000), dict(tc_record_chunk=1 << 21),
-                dict(direct_ctas_per_sm=4)):
+                dict(direct_ctas_per_sm=5)):
         cfg = sim.make_config(params.module_config(**bad))
         assert L.sim_workspace_size(C.byref(cfg), 0, 100, 1000, 100, C.byref(b)) == -1, bad
     cfg = sim.make_config(params.module_config(precision=2, tc_units_per_sm=8, tc_record_chunk=1 << 16))
