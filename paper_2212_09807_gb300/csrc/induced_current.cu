@@ -67,9 +67,11 @@ constexpr int kKahanNodes = 8;                  // nodes per plain FP32 partial 
 constexpr int kMaxNb = 45;                      // nb <= 45 (nb * nb <= kMaxBins)
 constexpr int kNodeWords = (kMaxNb << 6) / 32;  // bit (nx << 6) | ny per node
 // Staged table row: value j at position p = j + kEdge, in 16-byte chunk
-// c = p / 4 stored at chunk c ^ ((c / 8) mod 8) (an XOR swizzle within each
+// c = p / 4 stored at chunk c ^ ((c / 8) mod 4) (an XOR swizzle within each
 // group of 8 chunks: the 16-byte window reads of 8 consecutive threads, whose
-// windows are 4 chunks apart, fall on 8 different bank groups).  Thread t holds the
+// windows are 4 chunks apart, span 4 or 5 groups and fall on 8 different bank
+// groups for every start and offset; XOR by (c / 8) mod 8 would pair groups 4
+// apart and cost 1.5 wavefronts per read).  Thread t holds the
 // pass ticks 16 t - sigma + i (i < 16), sigma = L mod 16, so that its
 // 32-value window of block bl starts at j0 = 16 (t - bl) + L - 16 - sigma, a
 // multiple of 16; windows that touch the row have j0 in [-30, L - 1], so
@@ -80,7 +82,7 @@ constexpr int kEdge = 32;
 constexpr int kRowPos = kMaxRow + kEdge + 48;
 constexpr int kRowWords = ((kRowPos / 4 + 7) / 8) * 32;
 
-__device__ __forceinline__ int row_chunk(int c) { return c ^ ((c >> 3) & 7); }
+__device__ __forceinline__ int row_chunk(int c) { return c ^ ((c >> 3) & 3); }
 __host__ __device__ constexpr int tick_shift(int L) { return L & 15; }
 
 struct CurArgs {
