@@ -36,7 +36,7 @@ from synth import events, params, response  # noqa: E402
 # kernels per step: 1 quench/drift + 14 pixel map + 6 electronics, plus the induced current:
 # 3 (FP32: work classes, queue order, sum) or 15 (tensor cores: work plan 5 + two 3-kernel
 # scans, table rounding 1, table unfolding 1, contraction 1, reduction of split groups 1)
-KERNELS_PER_STEP = {0: 24, 1: 36, 2: 36}
+KERNELS_PER_STEP = {0: 24, 1: 36, 2: 36, 3: 22}
 FP32_LANES_PER_SM = 128
 
 
@@ -49,8 +49,9 @@ def parse():
     ap.add_argument("--workload", choices=["module", "tile", "spill"], default="spill")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--precision", type=int, choices=[0, 1, 2], default=2,
-                    help="induced-current form of the headline: 0 FP32, 1 BF16 / 2 FP16 tensor cores")
+    ap.add_argument("--precision", type=int, choices=[0, 1, 2, 3], default=2,
+                    help="induced-current form of the headline: 0 FP32 (node-binned cells), 1 BF16 / 2 FP16 "
+                         "tensor cores, 3 FP32 term by term")
     ap.add_argument("--no-forms", action="store_true", help="skip timing the other induced-current forms")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-vs-plain request stream")
     ap.add_argument("--no-post", action="store_true", help="skip timing truth, hit points and dQ/dx")
@@ -359,7 +360,7 @@ def batched_vs_plain(cfg, lut, dev, n_events=256, lo=1.0e3, hi=2.0e5, n_sub=4):
                        "candidates_ms": [[c, round(ms, 3)] for c, ms in table]}}
 
 
-FORMS = {0: ("fp32_cells", "f32"), 1: ("bf16_tensor", "bf16"), 2: ("fp16_tensor", "f16")}
+FORMS = {0: ("fp32_cells", "f32"), 1: ("bf16_tensor", "bf16"), 2: ("fp16_tensor", "f16"), 3: ("fp32_terms", "f32")}
 
 
 def time_form(cfg, seg, lut, dev, precision, steps, warmup, rank):
@@ -624,6 +625,12 @@ def form_roofline(run, cfg, precision, a4_s, fp32_peak, dev, wl_key=""):
     useful = 2.0 * nnz * L / a4_s / 1e12
     work_note = ("achieved: 2 flop x nnz(Q) x 1950 table ticks (nonzero binned-charge cells Q[p, node, tick], "
                  "counted on the device); per_point: 2 flop x 9 pixels x 1950 ticks per (point, perturbation)")
+    if precision == 3:                                  # term by term: the per-point count is its work
+        return {"bound": "alu", "achieved": per_point, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": per_point / fp32_peak, "traffic": None, "kernel": "k_induced_current_terms",
+                "peak_note": "FP32 FMA rate measured on this GPU by sim_probe_fma (independent FMA chains), "
+                             "of measured",
+                "work_note": "2 flop x 9 pixels x 1950 table ticks per (point, perturbation)"}, samples
     if precision == 0:
         return {"bound": "alu", "achieved": useful, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": useful / fp32_peak, "traffic": stored_traffic("induced_current.cu", wl_key),

@@ -78,8 +78,11 @@ typedef struct sim_config {
     /* counter-based RNG seed (Philox4x32-10 key = seed ^ event_id) */
     uint64_t seed;
     /* arithmetic form of the induced-current step (sim_induced_current):
-     * 0 = FP32 form on the CUDA cores; 1 = tensor-core contraction with BF16 operands,
-     * 2 = with FP16 operands (FP32 accumulation in both) */
+     * 0 = FP32 form on the CUDA cores (charge binned per table node); 1 =
+     * tensor-core contraction with BF16 operands, 2 = with FP16 operands (FP32
+     * accumulation in both); 3 = FP32 term-by-term gather (each point record's
+     * bilinear and linear table reads summed directly: slower, kept as an
+     * independent FP32 evaluation) */
     int32_t precision;
     /* running CSA charge of the front end (sim_electronics): 0 = FP32,
      * 1 = FP64 (for long windows, where FP32 sums drift); decisions compare
@@ -238,18 +241,21 @@ int sim_pixel_map(const sim_config *cfg, const sim_segments *seg, const sim_drif
  * integer atomics); cfg->precision selects the arithmetic of the sum:
  * 0 FP32 on the CUDA cores (Q at a power-of-two scale per chunk of a pixel's
  * points, ~1e-9 of its charge; partial sums added into compensated totals);
+ * 3 FP32 without the regrouping: each point record's terms summed per tick
+ * (the table rows of its bin staged in shared memory; records of a chunk in
+ * point order, bins increasing; chunk sums added into compensated totals);
  * 1 (BF16) and 2 (FP16) contract Q with the Toeplitz blocks of each table row
  * on the tensor cores (Q in fixed point 2^-12 e-, then rounded to the operand
  * type, as is R; FP16 Q cells saturate at 262016 e-).  Results are bitwise
- * reproducible for a given call, and with precision 0 a pixel's current does
- * not depend on the other pixels of the call; counts[4] receives the number
+ * reproducible for a given call, and with precision 0 or 3 a pixel's current
+ * does not depend on the other pixels of the call; counts[4] receives the number
  * of tensor-core MMA instructions (M = 128, N = 32, K = 16) of the call and
  * counts[5] the number of nonzero charge cells Q[p, n, a] it summed, and
  * SIM_STATUS_TIMEOUT is set if a bounded device-side wait gave up.
  * Workspace (scratch from byte 256 on): sim_workspace_size(cfg, 0, 0, 0,
  * pix_cap) bytes, sized for the current device (per-CTA record buffers, up to
- * ~1.8 GB for precision 0 on 152 SMs; with precision 1/2 also the phase
- * tables).  Table limits: nb * nb <= 2048, nt <= 2048. */
+ * ~2.5 GB for precision 0 and 0.24 GB for 3 on 152 SMs; with precision 1/2
+ * also the phase tables).  Table limits: nb * nb <= 2048, nt <= 2048. */
 int sim_induced_current(const sim_config *cfg, const sim_segments *seg, const sim_drifted *dr,
                         const sim_response *resp, const int32_t *active_pixels,
                         const int32_t *pix_seg_off, const int32_t *pix_seg_ids,

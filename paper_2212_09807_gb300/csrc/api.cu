@@ -30,7 +30,7 @@ bool cfg_ok(const sim_config *c)
     if (c->mc_per_sample < 1 || !(c->diff_clip_sigma >= 0.f) || !(c->lifetime_us > 0.f)) return false;
     if (c->recomb_model != 0 && c->recomb_model != 1) return false;
     if (c->adc_bits < 1 || c->adc_bits > 16 || c->hold_ticks < 0 || c->min_adc_interval_ticks < 0) return false;
-    if (c->periodic_reset_ticks < 0 || c->precision < 0 || c->precision > 2) return false;
+    if (c->periodic_reset_ticks < 0 || c->precision < 0 || c->precision > 3) return false;
     if (c->fp64_charge != 0 && c->fp64_charge != 1) return false;
     if (c->per_point_drift != 0 && c->per_point_drift != 1) return false;
     if (c->nearest_lut != 0 && c->nearest_lut != 1) return false;
@@ -81,6 +81,7 @@ bool hits_ok(const sim_hits *h)
 // Scratch and launch of the induced-current form selected by cfg.precision.
 size_t current_scratch(const sim_config &c, int64_t pixels)
 {
+    if (c.precision == 3) return current_direct_scratch_bytes(pixels);
     return c.precision == 0 ? current_scratch_bytes(pixels)
                             : current_tc_scratch_bytes(pixels, c.n_ticks, c.tc_units_per_sm, c.tc_record_chunk);
 }
@@ -93,6 +94,9 @@ cudaError_t launch_current(const sim_config &c, const sim_segments &s, const sim
     if (c.precision == 0)
         return launch_induced_current(c, s, d, r, active, off, ids, counts, pix_cap, pix_begin, pix_end, current,
                                       scratch, st);
+    if (c.precision == 3)
+        return launch_induced_current_direct(c, s, d, r, active, off, ids, counts, pix_cap, pix_begin, pix_end,
+                                             current, scratch, st);
     return launch_induced_current_tc(c, s, d, r, active, off, ids, counts, pix_cap, pix_begin, pix_end, current,
                                      scratch, st);
 }

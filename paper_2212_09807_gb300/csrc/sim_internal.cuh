@@ -175,6 +175,13 @@ cudaError_t launch_induced_current(const sim_config &c, const sim_segments &s, c
                                    const int32_t *pix_seg_off, const int32_t *pix_seg_ids,
                                    const int64_t *counts, int64_t pix_cap, int64_t pix_begin, int64_t pix_end,
                                    float *current, void *scratch, cudaStream_t st);
+// FP32 term-by-term form (precision 3): the per-record sum, same arguments.
+size_t current_direct_scratch_bytes(int64_t pix_cap);
+cudaError_t launch_induced_current_direct(const sim_config &c, const sim_segments &s, const sim_drifted &d,
+                                          const sim_response &r, const int32_t *active,
+                                          const int32_t *pix_seg_off, const int32_t *pix_seg_ids,
+                                          const int64_t *counts, int64_t pix_cap, int64_t pix_begin, int64_t pix_end,
+                                          float *current, void *scratch, cudaStream_t st);
 size_t current_tc_scratch_bytes(int64_t pix_cap, int n_ticks, int units_per_sm, int rec_chunk);
 cudaError_t launch_induced_current_tc(const sim_config &c, const sim_segments &s, const sim_drifted &d,
                                       const sim_response &r, const int32_t *active,

@@ -156,3 +156,17 @@ def test_autotuner_candidates_are_valid_configurations(L):
     assert chunks[-1] == 1 << 20
     for lo, hi in zip(chunks, chunks[1:]):
         assert sizes[hi] - sizes[lo] >= 2 * 32 * (hi - lo)        # at least one CTA's two record buffers
+
+
+def test_precision_range(L):
+    """precision 0..3 are the four forms of the current; 4 and -1 are rejected."""
+    from paper_2212_09807_gb300 import sim
+    from synth import params
+    b = C.c_size_t()
+    for prec in (0, 1, 2, 3):
+        cfg = sim.make_config(params.module_config(precision=prec))
+        assert L.sim_workspace_size(C.byref(cfg), 0, 1000, 40000, 4000, C.byref(b)) == 0, prec
+        assert b.value > 0
+    for bad in (-1, 4):
+        cfg = sim.make_config(params.module_config(precision=bad))
+        assert L.sim_workspace_size(C.byref(cfg), 0, 1000, 40000, 4000, C.byref(b)) == -1, bad

@@ -167,6 +167,20 @@ def test_induced_current_all_pixels(small):
     assert q_ok, q_worst
 
 
+def test_term_by_term_form_all_pixels(small):
+    """precision 3, the FP32 term-by-term gather (each record's bilinear and
+    linear table reads summed per tick, no regrouping by table node): every
+    pixel against the oracle at the FP32 tolerances of the first build of
+    this form (max 1e-4, median 1e-5, prefix charge 1e-5 plus the floor)."""
+    cfg = dict(small["cfg"], precision=3)
+    rel, qrel, ref, q_ok, q_worst = _current_parity(cfg, small["seg"], small["lut_dev"], small["lut64"], event_id=5)
+    print(f"term by term: rel max {rel.max():.2e} med {np.median(rel):.2e}, prefix-charge worst {q_worst:.2e}")
+    assert len(rel) > 200
+    assert rel.max() <= 1e-4, rel.max()
+    assert np.median(rel) <= 1e-5, np.median(rel)
+    assert q_ok, q_worst
+
+
 @pytest.mark.parametrize("case", ["M4", "ragged_window", "box_shifted", "bipolar"])
 def test_induced_current_variants(case):
     over, lut_kw, tr = {}, {}, (0.0, 0.0)
