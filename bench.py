@@ -21,6 +21,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -181,16 +182,26 @@ def measured_peaks():
         return {}
 
 
+def code_sha256(src: str) -> str:
+    """SHA-256 of a CUDA source with its comments removed and blank space
+    collapsed: the key of a stored measurement, which a comment edit leaves
+    valid and any change to the code invalidates."""
+    s = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    s = re.sub(r"//[^\n]*", " ", s)
+    s = " ".join(s.split())
+    return hashlib.sha256(s.encode()).hexdigest()
+
+
 def stored_traffic(kernel_file: str, workload_key: str):
     """DRAM bytes per launch from a committed ncu summary of this kernel on this
-    workload (entry "<file>@<workload>"), if taken on this exact source."""
+    workload (entry "<file>@<workload>"), if taken on this source's code."""
     try:
         t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
     except OSError:
         return None
-    src = open(os.path.join(ROOT, "paper_2212_09807_gb300", "csrc", kernel_file), "rb").read()
+    src = open(os.path.join(ROOT, "paper_2212_09807_gb300", "csrc", kernel_file)).read()
     ent = t.get(f"{kernel_file}@{workload_key}")
-    if not ent or ent.get("src_sha256") != hashlib.sha256(src).hexdigest():
+    if not ent or ent.get("code_sha256") != code_sha256(src):
         return None
     return ent.get("dram_bytes_per_launch_full")
 

@@ -33,8 +33,8 @@
 //     largest weight, so that taps round to ~1e-9 of a node's charge) and its
 //     table row copied in (cp.async), while node n is applied: for each
 //     present 16-tick arrival block every thread loads the 31 table values its
-//     16 ticks need (eight 16-byte shared reads; 4 words of padding after
-//     every 16 keep consecutive threads' windows conflict-free) and adds
+//     16 ticks need (eight 16-byte shared reads from the row's XOR-swizzled
+//     chunks, conflict-free across consecutive threads' windows) and adds
 //     q_d R[.] for each nonzero cell d (a CTA-uniform branch), two ticks per
 //     paired FMA instruction (fma.rn.f32x2).
 // Per tick the terms are summed in a fixed order (chunks in point order,
