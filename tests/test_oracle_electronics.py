@@ -81,6 +81,48 @@ def test_periodic_reset_discards_subthreshold_charge():
     assert len(o2.electronics(9, I)["t_cross"]) == 0
 
 
+def test_adc_code_is_clamped_to_its_range():
+    """ADC = clamp(floor(v / lsb), 0, 2^bits - 1) (Sec. 3.4): a current far
+    above the range saturates at 2^bits - 1 for 8 and 10 bits, and a charge
+    that crossed the threshold and then fell below zero during the hold (a
+    bipolar induced current) digitises as 0."""
+    for bits in (8, 10):
+        cfg = _quiet(adc_bits=bits)
+        o = oracle.Oracle(cfg, params.LUT)
+        r = o.electronics(11, np.full(2000, 1.0e7))
+        lsb_e = float(np.float32(cfg["gain_e_per_mV"])) * float(np.float32(cfg["adc_lsb_mV"]))
+        assert len(r["adc"]) > 10 and np.all(r["adc"] == (1 << bits) - 1)
+        assert np.all(r["q"] / lsb_e > 2 * (1 << bits))         # far beyond the range
+    cfg = _quiet()
+    o = oracle.Oracle(cfg, params.LUT)
+    thr = float(np.float32(cfg["thr_e"]))
+    I = np.zeros(2000)
+    I[10] = thr + 10.0                      # crosses at tick 10
+    I[11] = -4.0 * thr                      # the charge is negative when the ADC samples it
+    r = o.electronics(12, I)
+    assert list(r["t_cross"]) == [10] and list(r["t_adc"]) == [10 + cfg["hold_ticks"]]
+    assert r["q"][0] < 0 and list(r["adc"]) == [0]
+
+
+def test_window_starts_discharged_and_periodic_resets_fall_on_multiples():
+    """The CSA starts the window discharged, and periodic resets (while idle)
+    set it to a pedestal at ticks j * period, j >= 1.  With zero current and
+    no other noise the charge changes only at resets, so a pixel's first
+    crossing is at one of those ticks, never before the first period."""
+    P = 97
+    cfg = _quiet(sigma_reset_e=900.0, thr_e=450.0, periodic_reset_ticks=P)
+    o = oracle.Oracle(cfg, params.LUT)
+    firsts = []
+    for pix in range(600):
+        t = o.electronics(pix, np.zeros(2000))["t_cross"]
+        if len(t):
+            firsts.append(int(t[0]))
+    f = np.array(firsts)
+    assert len(f) > 500                     # P(n0 >= 1/2) = 0.31 per reset, 20 resets per window
+    assert np.all(f >= P) and np.all(f % P == 0)
+    assert np.sum(f == P) > 120             # the first reset already fires ~31 % of the pixels
+
+
 def test_noise_statistics_of_idle_comparisons():
     """With zero current and zero threshold the first comparison fires when
     s_unc n_unc >= s_disc n_disc, i.e. with probability 1/2."""

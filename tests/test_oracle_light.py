@@ -88,6 +88,16 @@ def test_yield_sum_rule_voxel_and_tick():
         assert abs(tick[j] - (float(tm) + 0.05) / 0.001) <= 1.0
         ng = npe[j] / (tab["eff"].astype(np.float64) * tab["vis"].reshape(-1, L["n_det"])[vox[j]])
         assert np.allclose(ng + d["QR"][j], float(np.float32(0.9)) / float(np.float32(L["w_ph_MeV"])), rtol=1e-12)
+    # the voxel's depth is the distance from the segment's own anode: mirrored segments of
+    # the second drift volume (anode at z = 2D) land in the same voxels
+    D = float(np.float32(cfg["drift_len_cm"]))
+    mirror = {k: v.copy() for k, v in seg.items()}
+    mirror["z0"] = np.float32(2 * D) - seg["z1"]
+    mirror["z1"] = np.float32(2 * D) - seg["z0"]
+    dm = o.quench_drift(mirror)
+    assert np.all(dm["anode"] == d["anode"] + 1)           # the other TPC of the same module
+    _, tick_m, vox_m = lo.segments(mirror, dm)
+    assert np.array_equal(vox_m, vox) and np.array_equal(tick_m, tick)
 
 
 def test_photocurrent_single_segment_is_a_table_row():

@@ -327,6 +327,118 @@ def test_longitudinal_spread_matches_sigma_L():
     assert abs((var(I) - var(I0)) / (sa2 - 1.0 / 12) - 1) < 0.08
 
 
+def test_transverse_perturbations_are_clipped():
+    """Diffusion offsets are normals clipped at +-clip (reading 15): a point
+    charge with sigma_T = one pitch and clip 0.5 reaches no pixel beyond the
+    table's reach plus 0.5 sigma_T, in any direction, while the clipped
+    offsets do reach pixels beyond the table's reach alone."""
+    p, h = 0.46875, 0.46875 / 30
+    z = 1.0                                          # 8 us of drift at 0.125 cm/us
+    cfg = _exact_cfg(diff_tran_cm2_s=p * p / (2e-6 * z / 0.125), diff_clip_sigma=0.5, mc_per_sample=200)
+    o = oracle.Oracle(cfg, LUT_SMALL, np.random.default_rng(4).random((45, 45, 64)) + 0.1)
+    xc, yc = 10.5 * p, 20.5 * p
+    seg = _seg([_point(xc, yc, 0.0, 0.0, z)])
+    d = o.quench_drift(seg)
+    sT = float(d["sigma_T"][0])
+    assert abs(sT / p - 1.0) < 1e-3
+    reach_table = 45.5 * h
+    reach = reach_table + 0.5 * sT
+    x, y = float(seg["x0"][0]), float(seg["y0"][0])
+    beyond_table = 0
+    for iy in range(16, 25):
+        for ix in range(6, 15):
+            dist = max(abs((ix + 0.5) * p - x), abs((iy + 0.5) * p - y))
+            I = o.pixel_current(seg, d, iy * 70 + ix, [0])
+            if dist > reach + 1e-6:
+                assert not np.any(I), (ix, iy)
+            elif dist > reach_table + 1e-6 and np.any(I):
+                beyond_table += 1
+    assert beyond_table >= 8                         # the ring at two pitches, reached only by clipped offsets
+
+
+def test_isochronous_segment_arrives_as_one_point():
+    """Points are spaced evenly along the segment in space and in time
+    (Sec. 3.3.2): a segment drifting straight to the anode whose time runs back
+    by exactly its extra drift time (t1 - t0 = -(z1 - z0) / v) delivers all of
+    its points at one instant, so without diffusion its current per unit charge
+    is that of a point charge at its midpoint."""
+    cfg = _exact_cfg()
+    lut = np.random.default_rng(6).random((45, 45, 64))
+    o = oracle.Oracle(cfg, LUT_SMALL, lut)
+    p, h = 0.46875, 0.46875 / 30
+    xc, yc = 10.5 * p, 20.5 * p
+    x, y = xc + 7.3 * h, yc - 11.6 * h
+    seg = _seg([(x, y, 1.0, 4.0, x, y, 1.5, 0.0, 1.0)])       # arrival 4 + 8 = 0 + 12 us for every point
+    d = o.quench_drift(seg)
+    assert d["n_samples"][0] > 100
+    pid = 20 * 70 + 10
+    I = o.pixel_current(seg, d, pid, [0]) / d["Qa"][0]
+    pt = _seg([(x, y, 1.25 - 2 ** -12, 2.0, x, y, 1.25 + 2 ** -12, 2.0, 1.0)])
+    dp = o.quench_drift(pt)
+    assert dp["n_samples"][0] == 1
+    Ip = o.pixel_current(pt, dp, pid, [0]) / dp["Qa"][0]
+    assert np.any(Ip)
+    np.testing.assert_allclose(I, Ip, rtol=1e-9, atol=1e-12 * np.abs(Ip).max())
+
+
+def _onset(I):
+    nz = np.nonzero(I)[0]
+    return int(nz[0]) if len(nz) else len(I)
+
+
+def test_per_point_transverse_width_bounds_the_reach_along_the_drift():
+    """Per-point drift: each point diffuses with sigma_T of its own drift time
+    (Eq. (lifetime) and sigma = sqrt(2 D t) at the point), so on a segment
+    running away from the anode only the points beyond the depth z* where
+    clip sigma_T(z*) covers the gap can reach a pixel two pitches off the
+    track: that pixel's current starts no earlier than the response window of
+    a charge arriving from z*, while the pixel under the track sees the near
+    points from the first ticks."""
+    p, h, v, tick = 0.46875, 0.46875 / 30, 0.125, 0.125
+    clip, z0, z1 = 1.5, 0.25, 8.0
+    DT = (p / clip) ** 2 / (2e-6 * z1 / v)                     # clip sigma_T(z1) = one pitch
+    cfg = _exact_cfg(per_point_drift=1, diff_tran_cm2_s=DT, diff_clip_sigma=clip, mc_per_sample=16, n_ticks=1024)
+    o = oracle.Oracle(cfg, LUT_SMALL, np.random.default_rng(8).random((45, 45, 64)) + 0.1)
+    xc, yc = 10.5 * p, 20.5 * p
+    seg = _seg([(xc, yc, z0, 0.0, xc, yc, z1, 0.0, 2.0)])
+    d = o.quench_drift(seg)
+    gap = 2 * p - 45.5 * h                                      # offset needed to reach the pixel at +2 pitches
+    k_sig = 2e-6 * DT / v                                       # sigma_T(z)^2 = k_sig z
+    z_star = (gap / clip) ** 2 / k_sig
+    assert z0 + 0.5 < z_star < z1 - 0.5
+    k_bound = int(np.floor(z_star / v / tick)) - 64 + 1 - 2    # two ticks of margin for the FP32 inputs
+    far = o.pixel_current(seg, d, 20 * 70 + 12, [0])
+    near = o.pixel_current(seg, d, 20 * 70 + 10, [0])
+    assert _onset(far) >= k_bound
+    assert np.any(far)
+    assert _onset(near) < k_bound - 20
+
+
+def test_per_point_longitudinal_width_bounds_the_onset():
+    """Per-point drift with longitudinal diffusion only: a point at depth z
+    arrives no earlier than from z - clip sigma_L(z) (offsets clipped at
+    +-clip, sigma_L of the point's own drift time), so the current starts no
+    earlier than the response window of the earliest such arrival over the
+    segment; a width taken at the midpoint, or unclipped offsets, would bring
+    charge from the near end earlier."""
+    p, v, tick = 0.46875, 0.125, 0.125
+    clip, z0, z1 = 1.5, 4.0, 12.0
+    DL = (3.0 / clip) ** 2 / (2e-6 * z1 / v)                     # clip sigma_L(z1) = 3 cm
+    cfg = _exact_cfg(per_point_drift=1, diff_long_cm2_s=DL, diff_clip_sigma=clip, mc_per_sample=16, n_ticks=1280)
+    o = oracle.Oracle(cfg, LUT_SMALL, np.random.default_rng(9).random((45, 45, 64)) + 0.1)
+    xc, yc = 10.5 * p, 20.5 * p
+    seg = _seg([(xc, yc, z0, 0.0, xc, yc, z1, 0.0, 2.0)])
+    d = o.quench_drift(seg)
+    zs = np.linspace(z0, z1, 8001)
+    g = zs - clip * np.sqrt(2e-6 * DL / v * zs)                 # earliest depth each point can arrive from
+    assert np.all(np.diff(g) > 0) and g[0] > 0                  # earliest at the near end, on the near side of the anode
+    k_bound = int(np.floor(g[0] / v / tick)) - 64 + 1 - 2
+    I = o.pixel_current(seg, d, 20 * 70 + 10, [0])
+    assert _onset(I) >= k_bound
+    # the near end's offsets do reach close to the bound (the clip is met)
+    assert _onset(I) <= k_bound + 12
+
+
 def test_per_point_drift_charge_is_the_pointwise_lifetime_sum():
     """Per-point drift: each point carries Q_a/N exp(-(t_mu - t_mid)/tau) with
     t_mu its own drift time (Eq. (lifetime) at the point), so the charge
