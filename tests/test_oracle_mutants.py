@@ -2,11 +2,12 @@
 
 Each mutant below is one plausible slip in the FP64 oracle -- a dropped term,
 a wrong sign, index or constant, a transposed operand -- planted in a copy of
-``oracle/larsim_oracle.c`` in a temporary folder.  The copy is compiled there,
-the oracle module is pointed at it, and the oracle's pin tests
-(tests/test_oracle_*.py) run against it: every mutant must fail at least one
-pin.  An unchanged copy run the same way must pass them all (the control), so
-that a failure means the pins saw the mistake and not the harness.
+the oracle package (``larsim_oracle.c`` or ``__init__.py``) in a temporary
+folder.  The copy is compiled there and imported as ``oracle``, and the
+oracle's pin tests (tests/test_oracle_*.py) run against it: every mutant must
+fail at least one pin.  An unchanged copy run the same way must pass them all
+(the control), so that a failure means the pins saw the mistake and not the
+harness.
 
 The committed oracle is never modified: the mistakes live only in the copies.
 """
@@ -20,6 +21,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "larsim_oracle.c")
+PY = os.path.join(ROOT, "oracle", "__init__.py")
 PIN_FILES = ["test_oracle_rng_quench_drift.py", "test_oracle_map_current.py", "test_oracle_electronics.py",
              "test_oracle_hits_post.py", "test_oracle_light.py"]
 
@@ -146,29 +148,49 @@ MUTANTS = [
      "int umax = t < L->n_trunc ? t : L->n_trunc;", "int umax = t < L->n_trunc ? t : L->n_trunc - 1;"),
 ]
 
+# the same, planted in the Python half of the oracle (configuration marshalling, interval sums, light lengths)
+PY_MUTANTS = [
+    ("cfg_diffusion_swapped", "Sec. 3.2 (D_L and D_T)", "rng",
+     'c.DL, c.DT = _f32(cfg["diff_long_cm2_s"]), _f32(cfg["diff_tran_cm2_s"])',
+     'c.DT, c.DL = _f32(cfg["diff_long_cm2_s"]), _f32(cfg["diff_tran_cm2_s"])'),
+    ("cfg_noise_swapped", "Sec. 3.4 (discriminator and uncorrelated noise)", "elec",
+     'c.s_disc, c.s_unc = _f32(cfg["sigma_disc_e"]), _f32(cfg["sigma_unc_e"])',
+     'c.s_unc, c.s_disc = _f32(cfg["sigma_disc_e"]), _f32(cfg["sigma_unc_e"])'),
+    ("hit_truth_drops_adc_tick", "Sec. 3.4 (integration up to the ADC tick)", "hits",
+     "Q = cs[:, k1 + 1].T - cs[:, k0].T", "Q = cs[:, k1].T - cs[:, k0].T"),
+    ("scintillation_truncation_floored", "Sec. 4.2 (truncation length)", "light",
+     "/ tick + 0.5))", "/ tick))"),
+    ("light_samples_short", "Sec. 4.3 (samples of the window)", "light",
+     "n_samples = int(np.floor((n_ticks - 1) / ratio)) + 1", "n_samples = int(np.floor((n_ticks - 1) / ratio))"),
+]
+
 FIRST = {"rng": "test_oracle_rng_quench_drift.py", "map": "test_oracle_map_current.py",
          "elec": "test_oracle_electronics.py", "hits": "test_oracle_hits_post.py", "light": "test_oracle_light.py"}
 
 PLUGIN = '''
-import oracle
-oracle.SRC = {src!r}
-oracle.LIB = {lib!r}
-oracle._lib = None
-oracle.build(force=True)
+import importlib.util
+import sys
+spec = importlib.util.spec_from_file_location("oracle", {init!r}, submodule_search_locations=[{pkg!r}])
+mod = importlib.util.module_from_spec(spec)
+sys.modules["oracle"] = mod
+spec.loader.exec_module(mod)
+mod.build(force=True)
 '''
 
 
-def _run_pins(workdir, source, first):
-    """Compile `source` as the oracle in `workdir` and run the pin tests on it
-    (the file `first` before the others, stopping at the first failure).
-    Returns (pytest exit code, the first failing test or '', output tail)."""
-    os.makedirs(workdir, exist_ok=True)
-    src = os.path.join(workdir, "larsim_oracle.c")
-    lib = os.path.join(workdir, "liblarsim_oracle.so")
-    with open(src, "w") as f:
-        f.write(source)
+def _run_pins(workdir, c_source, py_source, first):
+    """Copy the oracle package into `workdir` with the given sources, compile
+    it, import it as `oracle` and run the pin tests on it (the file `first`
+    before the others, stopping at the first failure).  Returns (pytest exit
+    code, the first failing test or '', output tail)."""
+    pkg = os.path.join(workdir, "oracle")
+    os.makedirs(pkg, exist_ok=True)
+    with open(os.path.join(pkg, "larsim_oracle.c"), "w") as f:
+        f.write(c_source)
+    with open(os.path.join(pkg, "__init__.py"), "w") as f:
+        f.write(py_source)
     with open(os.path.join(workdir, "mutant_oracle_plugin.py"), "w") as f:
-        f.write(PLUGIN.format(src=src, lib=lib))
+        f.write(PLUGIN.format(init=os.path.join(pkg, "__init__.py"), pkg=pkg))
     files = [first] + [p for p in PIN_FILES if p != first]
     env = dict(os.environ, PYTHONPATH=os.pathsep.join([workdir, ROOT]), OMP_NUM_THREADS="1",
                PYTHONDONTWRITEBYTECODE="1")
@@ -177,22 +199,25 @@ def _run_pins(workdir, source, first):
     r = subprocess.run(cmd, cwd=workdir, env=env, capture_output=True, text=True, timeout=600)
     out = r.stdout + r.stderr
     m = re.search(r"FAILED (\S+)", out)
-    if not os.path.exists(lib):
-        return -1, "", out[-2000:]                   # the copy did not compile: not a pin's catch
+    if not os.path.exists(os.path.join(pkg, "liblarsim_oracle.so")):
+        return -1, "", out[-2000:]                   # the copy did not build or load: not a pin's catch
     return r.returncode, m.group(1).split("/")[-1] if m else "", out[-2000:]
 
 
 @pytest.fixture(scope="module")
 def results(tmp_path_factory):
-    base = open(SRC).read()
-    jobs = {"control": (base, FIRST["rng"])}
+    base_c, base_py = open(SRC).read(), open(PY).read()
+    jobs = {"control": (base_c, base_py, FIRST["rng"])}
     for name, _, first, old, new in MUTANTS:
-        assert base.count(old) == 1, (name, "the planted text must match exactly one place")
-        jobs[name] = (base.replace(old, new), FIRST[first])
+        assert base_c.count(old) == 1, (name, "the planted text must match exactly one place")
+        jobs[name] = (base_c.replace(old, new), base_py, FIRST[first])
+    for name, _, first, old, new in PY_MUTANTS:
+        assert base_py.count(old) == 1, (name, "the planted text must match exactly one place")
+        jobs[name] = (base_c, base_py.replace(old, new), FIRST[first])
     root = tmp_path_factory.mktemp("mutants")
     workers = max(1, min(8, os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(workers) as ex:
-        fut = {k: ex.submit(_run_pins, str(root / k), s, f) for k, (s, f) in jobs.items()}
+        fut = {k: ex.submit(_run_pins, str(root / k), c, py, f) for k, (c, py, f) in jobs.items()}
         return {k: f.result() for k, f in fut.items()}
 
 
@@ -201,7 +226,7 @@ def test_unchanged_copy_passes_every_pin(results):
     assert rc == 0, (failed, tail)
 
 
-@pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
+@pytest.mark.parametrize("name", [m[0] for m in MUTANTS + PY_MUTANTS])
 def test_planted_mistake_fails_a_pin(results, name):
     rc, failed, tail = results[name]
     assert rc == 1 and failed, f"{name} was not caught by any pin (rc {rc}):\n{tail}"
