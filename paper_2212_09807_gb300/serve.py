@@ -212,6 +212,34 @@ class _Job:
                 delattr(self, k)
 
 
+def admission(waiting: list, n_running: int, large_running: bool, used: float, budget: float, max_jobs: int,
+              is_large, nbytes) -> list:
+    """The requests of `waiting` (in arrival order) to start in this turn of
+    the loop: first fit in arrival order within the HBM budget (`used` bytes
+    held, `nbytes(job)` more for each) and the job limit; a request that fits
+    no budget starts when nothing else is on the GPU.  Large requests
+    (`is_large(job)`) run one at a time and in arrival order: none starts
+    while one runs, and one that waits (for the budget) holds back the large
+    requests behind it.  Small requests may pass waiting ones."""
+    start = []
+    hold_large = large_running
+    for job in waiting:
+        on_gpu = n_running + len(start)
+        if on_gpu >= max_jobs:
+            break
+        large = bool(is_large(job))
+        if large and hold_large:
+            continue
+        b = float(nbytes(job))
+        if used + b > budget and on_gpu > 0:
+            hold_large = hold_large or large
+            continue
+        start.append(job)
+        used += b
+        hold_large = hold_large or large
+    return start
+
+
 class Server:
     """Continuous-batching request loop over one GPU (see the module docstring).
 
@@ -255,18 +283,10 @@ class Server:
             while nxt < len(reqs) and reqs[nxt].arrival <= now:
                 waiting.append(_Job(self, reqs[nxt]))
                 nxt += 1
-            # admission: first fit in arrival order, within the budget and the job limit; large
-            # requests one at a time, in arrival order (two sharing the GPU would both finish late)
+            # admission (see `admission`; two large requests sharing the GPU would both finish late)
             large_running = any(self.is_large(j.req.n) for j in running)
-            for job in list(waiting):
-                if len(running) >= self.max_jobs:
-                    break
-                if self.used + job.bytes > self.budget and running:
-                    continue
-                if self.is_large(job.req.n):
-                    if large_running:
-                        continue
-                    large_running = True
+            for job in admission(waiting, len(running), large_running, self.used, self.budget, self.max_jobs,
+                                 lambda j: self.is_large(j.req.n), lambda j: j.bytes):
                 pool = free_lo if self.is_large(job.req.n) else free_hi
                 stream = pool.pop()
                 job.pool = pool
