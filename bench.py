@@ -636,19 +636,23 @@ def form_roofline(run, cfg, precision, a4_s, fp32_peak, dev, wl_key=""):
     useful = 2.0 * nnz * L / a4_s / 1e12
     work_note = ("achieved: 2 flop x nnz(Q) x 1950 table ticks (nonzero binned-charge cells Q[p, node, tick], "
                  "counted on the device); per_point: 2 flop x 9 pixels x 1950 ticks per (point, perturbation)")
+    timing = {"duration_ms": a4_s * 1e3,
+              "duration_note": "mean CUDA-event time of the sim_induced_current call on its stream over the timed "
+                               "steps: the kernel plus the form's small preparation launches, so achieved is a "
+                               "lower bound of the kernel's own rate"}
     if precision == 3:                                  # term by term: the per-point count is its work
         return {"bound": "alu", "achieved": per_point, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": per_point / fp32_peak, "traffic": None, "kernel": "k_induced_current_terms",
                 "peak_note": "FP32 FMA rate measured on this GPU by sim_probe_fma (independent FMA chains), "
                              "of measured",
-                "work_note": "2 flop x 9 pixels x 1950 table ticks per (point, perturbation)"}, samples
+                "work_note": "2 flop x 9 pixels x 1950 table ticks per (point, perturbation)", **timing}, samples
     if precision == 0:
         return {"bound": "alu", "achieved": useful, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": useful / fp32_peak, "traffic": stored_traffic("induced_current.cu", wl_key),
                 "kernel": "k_induced_current", "nnz_charge_cells": nnz, "per_point_achieved": per_point,
                 "peak_note": "FP32 FMA rate measured on this GPU by sim_probe_fma (independent FMA chains), "
                              "of measured",
-                "work_note": work_note}, samples
+                "work_note": work_note, **timing}, samples
     dense = 2.0 * 128 * 32 * 16 * n_mma / a4_s / 1e12
     tpk = measured_peaks().get("bf16_tflops_sustained") or 1700.0
     return {"bound": "tensor", "achieved": useful, "peak": tpk, "unit": "TFLOP/s", "frac": useful / tpk,
@@ -657,7 +661,7 @@ def form_roofline(run, cfg, precision, a4_s, fp32_peak, dev, wl_key=""):
             "dense_achieved": dense, "dense_frac": dense / tpk, "per_point_achieved": per_point,
             "peak_note": "measured dense bf16 sustained (kernel timed inside a step), of measured; fp16 has the "
                          "same nominal rate",
-            "work_note": work_note + "; dense: 2 x 128 x 32 x 16 flop per issued MMA"}, samples
+            "work_note": work_note + "; dense: 2 x 128 x 32 x 16 flop per issued MMA", **timing}, samples
 
 
 SLICE = 32768        # active pixels per current launch of a large request (serving form)
