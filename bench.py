@@ -154,23 +154,34 @@ class ClockSampler:
             self.p.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.p.kill()
-        sm, mx, reasons, power = [], [], set(), []
+        return self.summarize(self.lines)
+
+    @staticmethod
+    def summarize(lines):
+        """Median and largest SM clock, largest power and the throttle reasons
+        seen in nvidia-smi lines of the query Q (CSV, no header, no units).  A
+        sample's reasons count even when its clocks or power do not parse."""
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        sm, mx, reasons, power = [], [], set(), []
+        for ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
-                power.append(float(f[3]))
-            except ValueError:
                 continue
             for nm, v in zip(names, f[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
+            try:
+                clk, clk_max = float(f[1]), float(f[2])
+            except ValueError:
+                continue
+            sm.append(clk)
+            mx.append(clk_max)
+            try:
+                power.append(float(f[3]))
+            except ValueError:
+                pass
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": sorted(reasons) + ["no samples"]}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "samples": len(sm),
                 "power_w_max": float(max(power)) if power else None, "reasons": sorted(reasons)}
 
