@@ -15,10 +15,12 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PKG = os.path.join(ROOT, "paper_2212_09807_gb300")
 
 
-def test_binding_raises_without_the_library(monkeypatch, tmp_path):
+def test_binding_raises_without_the_library(monkeypatch):
     from paper_2212_09807_gb300 import sim
     from synth import params
-    monkeypatch.setattr(sim, "LIB_PATH", str(tmp_path / "libsim.so"))
+    missing = os.path.join(ROOT, "_build", "no_such_folder", "libsim.so")
+    assert not os.path.exists(missing)
+    monkeypatch.setattr(sim, "LIB_PATH", missing)
     monkeypatch.setattr(sim, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         sim.lib()

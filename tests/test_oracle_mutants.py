@@ -2,8 +2,8 @@
 
 Each mutant below is one plausible slip in the FP64 oracle -- a dropped term,
 a wrong sign, index or constant, a transposed operand -- planted in a copy of
-the oracle package (``larsim_oracle.c`` or ``__init__.py``) in a temporary
-folder.  The copy is compiled there and imported as ``oracle``, and the
+the oracle package (``larsim_oracle.c`` or ``__init__.py``) in a scratch
+folder of the repository (``_build/``, git-ignored, removed afterwards).  The copy is compiled there and imported as ``oracle``, and the
 oracle's pin tests (tests/test_oracle_*.py) run against it: every mutant must
 fail at least one pin.  An unchanged copy run the same way must pass them all
 (the control), so that a failure means the pins saw the mistake and not the
@@ -14,6 +14,7 @@ The committed oracle is never modified: the mistakes live only in the copies.
 import concurrent.futures as cf
 import os
 import re
+import shutil
 import subprocess
 import sys
 
@@ -204,8 +205,11 @@ def _run_pins(workdir, c_source, py_source, first):
     return r.returncode, m.group(1).split("/")[-1] if m else "", out[-2000:]
 
 
+SCRATCH = os.path.join(ROOT, "_build", "oracle_mutants")     # git-ignored; removed after the run
+
+
 @pytest.fixture(scope="module")
-def results(tmp_path_factory):
+def results():
     base_c, base_py = open(SRC).read(), open(PY).read()
     jobs = {"control": (base_c, base_py, FIRST["rng"])}
     for name, _, first, old, new in MUTANTS:
@@ -214,11 +218,19 @@ def results(tmp_path_factory):
     for name, _, first, old, new in PY_MUTANTS:
         assert base_py.count(old) == 1, (name, "the planted text must match exactly one place")
         jobs[name] = (base_c, base_py.replace(old, new), FIRST[first])
-    root = tmp_path_factory.mktemp("mutants")
+    shutil.rmtree(SCRATCH, ignore_errors=True)
     workers = max(1, min(8, os.cpu_count() or 1))
-    with cf.ThreadPoolExecutor(workers) as ex:
-        fut = {k: ex.submit(_run_pins, str(root / k), c, py, f) for k, (c, py, f) in jobs.items()}
-        return {k: f.result() for k, f in fut.items()}
+    try:
+        with cf.ThreadPoolExecutor(workers) as ex:
+            fut = {k: ex.submit(_run_pins, os.path.join(SCRATCH, k), c, py, f) for k, (c, py, f) in jobs.items()}
+            out = {k: f.result() for k, f in fut.items()}
+    finally:
+        shutil.rmtree(SCRATCH, ignore_errors=True)
+        try:
+            os.rmdir(os.path.dirname(SCRATCH))            # _build/ too, when nothing else is in it
+        except OSError:
+            pass
+    return out
 
 
 def test_unchanged_copy_passes_every_pin(results):
