@@ -204,12 +204,15 @@ def test_digitiser_samples_a_ramp():
     V, vs, code, mg = lo2.electronics(n, 3, 0)
     g = float(tab["gain"][3])
     assert np.allclose(V, g * n, rtol=1e-14)
-    p = np.arange(lo2.n_samples) * lo2.ratio
-    assert np.allclose(vs, g * 0.37 * p, rtol=1e-12)
+    # a 62.5 MHz digitiser (16 ns) on 1 ns ticks samples every 16 ticks: 128 samples of 2048 ticks
+    assert (L["sample_us"], L["tick_us"]) == (0.016, 0.001)
+    assert lo2.n_samples == 128
+    p = np.arange(lo2.n_samples) * 16.0
+    assert np.allclose(vs, g * 0.37 * p, rtol=1e-6)              # FP32 config values: ratio 16 to ~1e-7
+    assert np.allclose(vs, g * 0.37 * np.arange(lo2.n_samples) * lo2.ratio, rtol=1e-12)
     ped = float(np.float32(L["pedestal"]))
     exp = np.clip(np.floor(vs + ped + 0.5), 0, 2 ** L["adc_bits"] - 1)
     assert np.array_equal(code, exp.astype(np.int32))
-    assert lo2.n_samples == int(np.floor(2047 / lo2.ratio)) + 1
 
 
 def test_light_truth_arrival_time_of_a_one_bin_row():

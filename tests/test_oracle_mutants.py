@@ -149,7 +149,7 @@ MUTANTS = [
      "int umax = t < L->n_trunc ? t : L->n_trunc;", "int umax = t < L->n_trunc ? t : L->n_trunc - 1;"),
 ]
 
-# the same, planted in the Python half of the oracle (configuration marshalling, interval sums, light lengths)
+# the same, planted in the Python half of the oracle (configuration marshalling, interval sums, light setup)
 PY_MUTANTS = [
     ("cfg_diffusion_swapped", "Sec. 3.2 (D_L and D_T)", "rng",
      'c.DL, c.DT = _f32(cfg["diff_long_cm2_s"]), _f32(cfg["diff_tran_cm2_s"])',
@@ -163,6 +163,34 @@ PY_MUTANTS = [
      "/ tick + 0.5))", "/ tick))"),
     ("light_samples_short", "Sec. 4.3 (samples of the window)", "light",
      "n_samples = int(np.floor((n_ticks - 1) / ratio)) + 1", "n_samples = int(np.floor((n_ticks - 1) / ratio))"),
+    ("light_sampling_ratio_inverted", "Sec. 4.3 (sampling period in ticks)", "light",
+     'ratio = _f32(L["sample_us"]) / tick', 'ratio = tick / _f32(L["sample_us"])'),
+    ("cfg_hold_and_interval_swapped", "Sec. 3.4 (hold, minimum ADC interval)", "elec",
+     'c.hold, c.min_int = int(cfg["hold_ticks"]), int(cfg["min_adc_interval_ticks"])',
+     'c.min_int, c.hold = int(cfg["hold_ticks"]), int(cfg["min_adc_interval_ticks"])'),
+    ("cfg_window_start_ignored", "Eq. (current), arrival tick", "map",
+     'c.tick, c.n_ticks, c.t_w0 = _f32(cfg["tick_us"]), int(cfg["n_ticks"]), _f32(cfg["t_window0_us"])',
+     'c.tick, c.n_ticks, c.t_w0 = _f32(cfg["tick_us"]), int(cfg["n_ticks"]), 0.0'),
+    ("cfg_box_parameters_swapped", "Sec. 3.1 Eq. (box)", "rng",
+     'c.alpha, c.beta = _f32(cfg["box_alpha"]), _f32(cfg["box_beta"])',
+     'c.beta, c.alpha = _f32(cfg["box_alpha"]), _f32(cfg["box_beta"])'),
+    ("cfg_density_typo", "Sec. 3.1 (epsilon = E rho)", "rng",
+     'c.efield, c.density = _f32(cfg["efield_kV_cm"]), _f32(cfg["lar_density_g_cm3"])',
+     'c.efield, c.density = _f32(cfg["efield_kV_cm"]), 1.396'),
+    ("cfg_per_point_ignored", "per-point drift variant", "map",
+     'c.per_point = int(cfg.get("per_point_drift", 0))', "c.per_point = 0"),
+    ("cfg_nearest_ignored", "nearest-lookup variant", "map",
+     'c.nearest = int(cfg.get("nearest_lut", 0))', "c.nearest = 0"),
+    ("cfg_seed_truncated", "Philox key = seed ^ event id", "rng",
+     'c.seed = int(cfg["seed"]) & 0xFFFFFFFFFFFFFFFF', 'c.seed = int(cfg["seed"]) & 0xFFFFFFFF'),
+    ("light_time_constants_swapped", "Sec. 4.2 (scintillation time profile)", "light",
+     'l.fast_frac, l.tau_fast, l.tau_slow = _f32(L["fast_frac"]), _f32(L["tau_fast_us"]), _f32(L["tau_slow_us"])',
+     'l.fast_frac, l.tau_slow, l.tau_fast = _f32(L["fast_frac"]), _f32(L["tau_fast_us"]), _f32(L["tau_slow_us"])'),
+    ("light_pedestal_dropped", "Sec. 4.3 (ADC pedestal)", "light",
+     'l.poisson_max, l.sample, l.pedestal = _f32(L["poisson_max_mean"]), _f32(L["sample_us"]), _f32(L["pedestal"])',
+     'l.poisson_max, l.sample, l.pedestal = _f32(L["poisson_max_mean"]), _f32(L["sample_us"]), 0.0'),
+    ("hit_signal_drops_adc_tick", "Sec. 3.4 (integration up to the ADC tick)", "hits",
+     "return Q, full[k1 + 1] - full[k0], k0, k1", "return Q, full[k1] - full[k0], k0, k1"),
 ]
 
 FIRST = {"rng": "test_oracle_rng_quench_drift.py", "map": "test_oracle_map_current.py",
