@@ -73,8 +73,8 @@ def test_yield_sum_rule_voxel_and_tick():
     o = oracle.Oracle(cfg, params.LUT)
     v = L["vox_cm"]
     rows = []
-    cells = [(2, 3, 1), (5, 1, 6), (0, 7, 3)]
-    for (ix, iy, iz), tm in zip(cells, (0.25, 1.0, 2.5)):
+    cells = [(2, 3, 1), (5, 1, 6), (0, 7, 3), (12, 14, 6)]     # the last one far from the corner: a
+    for (ix, iy, iz), tm in zip(cells, (0.25, 1.0, 2.5, 3.0)):  # voxel size a few % off moves it
         x, y, z = (ix + 0.5) * v, (iy + 0.5) * v, (iz + 0.5) * v
         rows.append((x - 0.2, y, z - 0.1, tm - 0.01, x + 0.2, y, z + 0.1, tm + 0.01, 0.9))
     seg = _seg(rows)

@@ -191,6 +191,11 @@ PY_MUTANTS = [
      'l.poisson_max, l.sample, l.pedestal = _f32(L["poisson_max_mean"]), _f32(L["sample_us"]), 0.0'),
     ("hit_signal_drops_adc_tick", "Sec. 3.4 (integration up to the ADC tick)", "hits",
      "return Q, full[k1 + 1] - full[k0], k0, k1", "return Q, full[k1] - full[k0], k0, k1"),
+    ("cfg_w_ion_doubled", "Sec. 3.1 (Q_0 = E / W_ion)", "rng",
+     'c.w_ion = _f32(cfg["w_ion_MeV"])', 'c.w_ion = 2 * _f32(cfg["w_ion_MeV"])'),
+    ("light_voxel_size_off", "Sec. 4.1 (visibility voxel)", "light",
+     'l.vox, l.w_ph, l.tick = _f32(L["vox_cm"]), _f32(L["w_ph_MeV"]), _f32(L["tick_us"])',
+     'l.vox, l.w_ph, l.tick = 1.05 * _f32(L["vox_cm"]), _f32(L["w_ph_MeV"]), _f32(L["tick_us"])'),
 ]
 
 FIRST = {"rng": "test_oracle_rng_quench_drift.py", "map": "test_oracle_map_current.py",

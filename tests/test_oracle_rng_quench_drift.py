@@ -97,6 +97,13 @@ def test_recombination_closed_form_values(model):
     assert len(rows) == 4
     for dedx, R in rows:
         assert abs(o.recomb(dedx) / R - 1.0) < 1e-5, (name, dedx, o.recomb(dedx), R)
+    # a MIP on 0.5 cm at the anode: 1.05 MeV / 23.6 eV = 44 491.5 electrons before recombination
+    # (W_ion = 23.6 eV, a reading: the paper does not give it), R(2.1 MeV/cm) of them survive it
+    mip = _seg([(5.0, 5.0, 0.1, 0.0, 5.5, 5.0, 0.1, 0.0, 1.05)])
+    R21 = dict((d, r) for d, r in rows)[2.1]
+    q0 = float(np.float32(1.05)) / float(np.float32(23.6e-6))
+    assert abs(q0 - 44491.5) < 0.1
+    assert abs(o.quench_drift(mip)["QR"][0] / (R21 * q0) - 1.0) < 1e-5
     # through the whole quench step: 0.5 cm segments at the anode carry Q_R = R dE / W_ion
     seg = _seg([(5.0, 5.0, 0.1, 0.0, 5.5, 5.0, 0.1, 0.0, 0.5 * d) for d, _ in rows])
     d = o.quench_drift(seg)
