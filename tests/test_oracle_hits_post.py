@@ -154,8 +154,11 @@ def test_track_dqdx_closed_form():
     s = (np.arange(int(nb * dx / delta)) + 0.5) * delta
     pts = o + s[:, None] * u + 0.3 * v
     far = o + s[:5, None] * u + 2.0 * v                  # beyond r_max
+    w = np.cross(u, v)                                    # across the track, with a z component
+    assert abs(w[2]) > 0.5 and 1.2 * np.hypot(w[0], w[1]) < 1.0
+    far_z = o + s[:5, None] * u + 1.2 * w                 # beyond r_max, though within it in x-y alone
     before = o - 0.6 * u                                  # s < 0
-    P = np.vstack([pts, far, before[None]])
+    P = np.vstack([pts, far, far_z, before[None]])
     q = np.full(len(P), c)
     dq, cnt, mg = oracle.Oracle.track_dqdx(P, q, o, u, dx, nb, 1.0)
     assert np.all(cnt == int(dx / delta))

@@ -61,6 +61,46 @@ def test_point_maps_to_3x3():
     assert sorted(ids.tolist()) == exp
 
 
+@pytest.mark.parametrize("mx,my,tpc,ix,iy", [(5, 3, 1, 250, 20), (1, 4, 0, 10, 340), (0, 0, 0, 279, 349)])
+def test_point_maps_to_3x3_on_non_square_anodes(mx, my, tpc, ix, iy):
+    """The 35-module array of 280 x 350-pixel anodes: a point charge on the
+    centre of pixel (ix, iy) of module (mx, my) maps to the 3x3 block of ids
+    around it, with ids laid out as anode * 280 * 350 + iy * 280 + ix and
+    anode = (my * 7 + mx) * 2 + tpc (clipped at the anode's edges)."""
+    cfg = params.spill_config(diff_tran_cm2_s=0.0, diff_long_cm2_s=0.0)
+    o = oracle.Oracle(cfg, params.LUT)
+    p = float(np.float32(0.4434))
+    nx, ny = 280, 350
+    x = mx * nx * p + (ix + 0.5) * p
+    y = my * ny * p + (iy + 0.5) * p
+    z = 10.0 if tpc == 0 else 50.0
+    seg = _seg([(x, y, z - 2 ** -12, 0, x, y, z + 2 ** -12, 0, 1.0)])
+    d = o.quench_drift(seg)
+    anode = (my * 7 + mx) * 2 + tpc
+    assert d["anode"][0] == anode
+    ids, _ = o.map_segment(seg, d, 0, box=False)
+    exp = sorted(anode * nx * ny + (iy + dy) * nx + ix + dx for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+                 if 0 <= ix + dx < nx and 0 <= iy + dy < ny)
+    assert sorted(ids.tolist()) == exp
+
+
+def test_a_segment_induces_only_on_its_own_anode():
+    """Charge drifts to the anode of its own drift volume: a segment of the
+    second volume listed for the pixel of the first anode directly below it
+    induces nothing there, and a current on its own anode's pixel."""
+    cfg = params.small_config(n_ticks=4000, t_window0_us=-200.0)
+    o = oracle.Oracle(cfg, params.LUT, response.lut_for(cfg, params.LUT))
+    p = float(np.float32(0.4434))
+    x, y = 20.5 * p, 30.5 * p
+    seg = _seg([(x, y, 40.0, 0, x + 0.2, y, 40.5, 0, 1.0)])            # TPC 1 (anode at z = 60)
+    d = o.quench_drift(seg)
+    assert d["anode"][0] == 1
+    below = 0 * o.npx_x * o.npx_y + 30 * o.npx_x + 20                     # the same pixel of anode 0
+    own = 1 * o.npx_x * o.npx_y + 30 * o.npx_x + 20
+    assert not np.any(o.pixel_current(seg, d, below, [0]))
+    assert np.any(o.pixel_current(seg, d, own, [0]))
+
+
 def test_axis_parallel_segment_maps_4x3():
     o = oracle.Oracle(_exact_cfg(), LUT_SMALL)
     p = 0.46875

@@ -63,6 +63,15 @@ MUTANTS = [
      "return ((double)c->nb + 0.5) * h + c->clip * sigma_T;", "return ((double)c->nb + 0.5) * h;"),
     ("chebyshev_candidate_dropped", "Sec. 3.3.2 (segment-pixel distance)", "map",
      "    if (du + dv != 0.0) cand[nc++] = -(u0 + v0) / (du + dv);\n", ""),
+    ("pixel_row_and_column_transposed", "pixel ids (row-major over the anode)", "map",
+     "int32_t iy = rem / nx, ix = rem % nx;", "int32_t iy = rem / ny, ix = rem % ny;"),
+    ("pixel_module_order_transposed", "pixel ids (modules row-major)", "map",
+     "int32_t mx = m % c->n_mod_x, my = m / c->n_mod_x;\n    double Wx",
+     "int32_t mx = m / c->n_mod_y, my = m % c->n_mod_y;\n    double Wx"),
+    ("module_row_from_width", "Sec. 6 geometry (module size)", "rng",
+     "int my = (int)floor(y / Wy);", "int my = (int)floor(y / Wx);"),
+    ("current_from_another_anode", "Sec. 3.2 (charge drifts to its own anode)", "map",
+     "if (anode[s] != g) continue;", "if (0) continue;"),
     # Sec. 3.3.2: charge density rho and Eq. (current)
     ("points_at_interval_starts", "Sec. 3.3.2 (charge density rho)", "map",
      "double u = ((double)mu + 0.5) / (double)N;", "double u = (double)mu / (double)N;"),
@@ -125,6 +134,8 @@ MUTANTS = [
      "out[2] = za == 0.0 ? za + dz : za - dz;", "out[2] = za + dz;"),
     ("dqdx_piece_rounded", "Sec. 6 (dQ/dx pieces)", "hits",
      "double fb = floor(s / dx);", "double fb = floor(s / dx + 0.5);"),
+    ("dqdx_distance_without_z", "Sec. 6 (distance from the track)", "hits",
+     "double d = sqrt(ex * ex + ey * ey + ez * ez);", "double d = sqrt(ex * ex + ey * ey);"),
     # Sec. 4: light
     ("photons_without_quenched_charge", "Sec. 4.1 (N_gamma)", "light",
      "double ngam = (double)p[8] / L->w_ph - QR;", "double ngam = (double)p[8] / L->w_ph;"),

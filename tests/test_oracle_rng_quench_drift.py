@@ -210,9 +210,12 @@ def test_anode_numbering_across_modules():
     H = 350 * np.float32(0.4434)
     rows = []
     expect = []
-    for (mx, my, tpc) in [(0, 0, 0), (6, 0, 1), (0, 4, 0), (3, 2, 1), (6, 4, 1)]:
-        x = mx * W + 5.0
-        y = my * H + 7.0
+    # near a module's first corner, and near its far corner (modules are 124 x 155 cm: there
+    # y / W and y / H floor to different rows)
+    for (mx, my, tpc, fx, fy) in [(0, 0, 0, 5.0, 7.0), (6, 0, 1, 5.0, 7.0), (0, 4, 0, 5.0, 7.0), (3, 2, 1, 5.0, 7.0),
+                                  (6, 4, 1, 5.0, 7.0), (2, 1, 0, 120.0, 150.0), (5, 3, 1, 120.0, 150.0)]:
+        x = mx * W + fx
+        y = my * H + fy
         z = 10.0 if tpc == 0 else 50.0
         rows.append((x, y, z, 0, x + 0.4, y, z, 0, 1.0))
         expect.append((my * 7 + mx) * 2 + tpc)
