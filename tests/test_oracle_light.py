@@ -161,6 +161,22 @@ def test_poisson_inverse_transform_is_the_quantile():
         else:
             z = oracle.normals(seed, ev, det, t, 6, 0)[0]
             assert n[t] == pytest.approx(max(0.0, l + math.sqrt(l) * z), rel=1e-12)
+    # the switch itself: a mean of exactly 30 counts by the Poisson branch (integers), the next
+    # double above it by the normal one (reading: the normal law for means above 30)
+    tick = float(np.float32(L["tick_us"]))
+    s30 = 30.0 / tick
+    while s30 * tick > 30.0:
+        s30 = math.nextafter(s30, 0.0)
+    while s30 * tick < 30.0:
+        s30 = math.nextafter(s30, math.inf)
+    assert s30 * tick == 30.0
+    s_up = s30
+    while s_up * tick <= 30.0:
+        s_up = math.nextafter(s_up, math.inf)
+    n30, _ = lo.fluctuate(np.full(3000, s30), 9, 1)
+    nup, _ = lo.fluctuate(np.full(3000, s_up), 9, 1)
+    assert np.all(n30 == np.round(n30))
+    assert np.mean(nup != np.round(nup)) > 0.99
     # statistics of the small-mean branch: mean and variance ~ lambda
     S2 = np.full(3000, 4.0 / float(np.float32(L["tick_us"])))
     n2, _ = lo.fluctuate(S2, 11, 0)

@@ -112,7 +112,10 @@ def test_axis_parallel_segment_maps_4x3():
     assert sorted(ids.tolist()) == exp
 
 
-def test_boundary_distance_counts_as_mapped():
+@pytest.mark.parametrize("box", [True, False])
+def test_boundary_distance_counts_as_mapped(box):
+    """A pixel whose centre lies exactly R_map from the segment is mapped, in
+    the box-restricted map and in the brute force over the whole anode."""
     o = oracle.Oracle(_exact_cfg(), LUT_SMALL)
     p = 0.46875
     R = o.map_radius(0.0)
@@ -121,7 +124,7 @@ def test_boundary_distance_counts_as_mapped():
     # a point exactly R to the right of pixel (10, 20): (10,20) mapped, (9,20) not
     seg = _seg([(xc + R, yc, 1.0 - 2 ** -12, 0, xc + R, yc, 1.0 + 2 ** -12, 0, 1.0)])
     d = o.quench_drift(seg)
-    ids, mg = o.map_segment(seg, d, 0)
+    ids, mg = o.map_segment(seg, d, 0, box=box)
     pid = 20 * 70 + 10
     assert pid in ids.tolist()
     assert mg[ids.tolist().index(pid)] == 0.0

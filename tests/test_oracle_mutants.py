@@ -63,6 +63,13 @@ MUTANTS = [
      "return ((double)c->nb + 0.5) * h + c->clip * sigma_T;", "return ((double)c->nb + 0.5) * h;"),
     ("chebyshev_candidate_dropped", "Sec. 3.3.2 (segment-pixel distance)", "map",
      "    if (du + dv != 0.0) cand[nc++] = -(u0 + v0) / (du + dv);\n", ""),
+    ("full_map_boundary_excluded", "Sec. 3.3.2 (distance exactly R_map is mapped)", "map",
+     "            if (d <= R) {\n                if (cnt < cap) {\n                    ids[cnt] = pid;\n"
+     "                    if (margin) margin[cnt] = R - d;\n                }\n                ++cnt;\n            }\n"
+     "        }\n    }\n    return cnt;\n}\n\n/* Same map",
+     "            if (d < R) {\n                if (cnt < cap) {\n                    ids[cnt] = pid;\n"
+     "                    if (margin) margin[cnt] = R - d;\n                }\n                ++cnt;\n            }\n"
+     "        }\n    }\n    return cnt;\n}\n\n/* Same map"),
     ("pixel_row_and_column_transposed", "pixel ids (row-major over the anode)", "map",
      "int32_t iy = rem / nx, ix = rem % nx;", "int32_t iy = rem / ny, ix = rem % ny;"),
     ("pixel_module_order_transposed", "pixel ids (modules row-major)", "map",
@@ -144,6 +151,8 @@ MUTANTS = [
      "double f = L->fast_frac * exp(-tu / L->tau_fast) +"),
     ("photocurrent_shift_reversed", "Sec. 4.2 Eq. (photocurrent)", "light",
      "int64_t t = (int64_t)tick[j] + u;", "int64_t t = (int64_t)tick[j] - u;"),
+    ("poisson_switch_excludes_its_bound", "Sec. 4.2 (Poisson up to a mean of 30)", "light",
+     "if (lam <= L->poisson_max) {", "if (lam < L->poisson_max) {"),
     ("poisson_term_index", "Sec. 4.2 (Poisson fluctuations)", "light",
      "pk *= lam / (double)k;", "pk *= lam / (double)(k + 1);"),
     ("digitiser_weights_swapped", "Sec. 4.3 (sampling)", "light",
