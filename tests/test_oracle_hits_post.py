@@ -163,4 +163,9 @@ def test_track_dqdx_closed_form():
     dq, cnt, mg = oracle.Oracle.track_dqdx(P, q, o, u, dx, nb, 1.0)
     assert np.all(cnt == int(dx / delta))
     assert np.allclose(dq / dx, c / delta, rtol=1e-12)
-    assert mg.min() > 0.05
+    # margins: the distance of each point's decisions from their edges, from the construction
+    # (arc length s and distance from the axis r): min(|r - r_max|, distance of s to a piece boundary)
+    arc = np.concatenate([s, s[:5], s[:5], [-0.6]])
+    r = np.concatenate([np.full(len(s), 0.3), np.full(5, 2.0), np.full(5, 1.2), [0.0]])
+    edge = np.abs(arc - dx * np.round(arc / dx))
+    assert np.allclose(mg, np.minimum(np.abs(r - 1.0), edge), rtol=0, atol=1e-9)

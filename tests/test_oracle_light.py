@@ -158,7 +158,13 @@ def test_poisson_inverse_transform_is_the_quantile():
             u = (float(x[0]) + 0.5) / 2.0 ** 32
             if mg[t] > 1e-9:
                 assert n[t] == stats.poisson.ppf(u, l), (t, l, u)
+            # margin: the distance of u from the two CDF values the count was decided between
+            # (one for a count of 0), and of the mean from the switch
+            k = int(n[t])
+            gaps = [abs(u - stats.poisson.cdf(k, l))] + ([abs(u - stats.poisson.cdf(k - 1, l))] if k else [])
+            assert abs(mg[t] - min(gaps + [abs(l - 30.0)])) < 1e-12, (t, l, u)
         else:
+            assert abs(mg[t] - (l - 30.0)) < 1e-12
             z = oracle.normals(seed, ev, det, t, 6, 0)[0]
             assert n[t] == pytest.approx(max(0.0, l + math.sqrt(l) * z), rel=1e-12)
     # the switch itself: a mean of exactly 30 counts by the Poisson branch (integers), the next
@@ -229,6 +235,9 @@ def test_digitiser_samples_a_ramp():
     ped = float(np.float32(L["pedestal"]))
     exp = np.clip(np.floor(vs + ped + 0.5), 0, 2 ** L["adc_bits"] - 1)
     assert np.array_equal(code, exp.astype(np.int32))
+    # each sample's margin: how far v + pedestal + 1/2 lies from the nearest integer (a code boundary)
+    w = g * 0.37 * p + ped + 0.5
+    assert np.allclose(mg, np.abs(w - np.round(w)), rtol=0, atol=1e-6)
 
 
 def test_light_truth_arrival_time_of_a_one_bin_row():

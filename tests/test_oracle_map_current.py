@@ -562,6 +562,11 @@ def test_nearest_lookup_reads_the_nearest_node_and_tick(bx, by, frac):
         if 0 <= j < 64:
             exp[k] = d["Qa"][0] * lut[bx, by, j]
     assert np.array_equal(I, exp)
+    # the point's roundings lie 0.2 bin / 0.2-0.3 tick from their half-way points: a tie
+    # within a band of 0.25, none within 0.1
+    for band, ties in ((0.1, 0), (0.25, 1)):
+        I2, n_ties = o.pixel_current(seg, d, 20 * 70 + 10, [0], tie_band=band)
+        assert n_ties == ties and np.array_equal(I2, I)
 
 
 def test_nearest_lookup_conserves_charge():

@@ -143,6 +143,15 @@ MUTANTS = [
      "double fb = floor(s / dx);", "double fb = floor(s / dx + 0.5);"),
     ("dqdx_distance_without_z", "Sec. 6 (distance from the track)", "hits",
      "double d = sqrt(ex * ex + ey * ey + ez * ez);", "double d = sqrt(ex * ex + ey * ey);"),
+    # the margins and tie counts the GPU parity tests excuse near-boundary decisions by
+    ("dqdx_margin_without_piece_edges", "Sec. 6 (dQ/dx pieces)", "hits",
+     "        if (ms < m) m = ms;", "        (void)ms;"),
+    ("digitiser_margin_one_sided", "Sec. 4.3 (ADC)", "light",
+     "margin[m] = fmin(w - cd, cd + 1.0 - w);", "margin[m] = w - cd;"),
+    ("poisson_margin_dropped", "Sec. 4.2 (Poisson fluctuations)", "light",
+     "            if (m2 < mg) mg = m2;", "            (void)m2;"),
+    ("nearest_ties_not_counted", "nearest-lookup variant", "map",
+     "if (mx < tie_band || my < tie_band || ma < tie_band) ++ties;", "if (0) ++ties;"),
     # Sec. 4: light
     ("photons_without_quenched_charge", "Sec. 4.1 (N_gamma)", "light",
      "double ngam = (double)p[8] / L->w_ph - QR;", "double ngam = (double)p[8] / L->w_ph;"),
