@@ -137,6 +137,11 @@ def test_scintillation_impulse_and_truncated_sum():
     rp, rs = math.exp(-dt / tp), math.exp(-dt / ts)
     geo = fp / tp * (1 - rp ** (N + 1)) / (1 - rp) + (1 - fp) / ts * (1 - rs ** (N + 1)) / (1 - rs)
     assert S.sum() == pytest.approx(geo, rel=1e-12)
+    # an impulse on the window's first tick: the sum's last term (u = t) carries it
+    I0 = np.zeros(9000)
+    I0[0] = 1.0
+    S0 = lo.scintillation(I0)
+    assert np.allclose(S0[:N + 1], exp, rtol=1e-12) and np.all(S0[N + 1:] == 0)
 
 
 def test_poisson_inverse_transform_is_the_quantile():
@@ -238,6 +243,11 @@ def test_digitiser_samples_a_ramp():
     # each sample's margin: how far v + pedestal + 1/2 lies from the nearest integer (a code boundary)
     w = g * 0.37 * p + ped + 0.5
     assert np.allclose(mg, np.abs(w - np.round(w)), rtol=0, atol=1e-6)
+    # a window of 16 k + 1 ticks: its last sample falls on its last tick, read without a neighbour
+    lo3 = oracle.LightOracle(cfg, L, tab2, -0.05, 2049)
+    assert lo3.n_samples == 129
+    _, vs3, _, _ = lo3.electronics(np.arange(2049) * 0.37, 3, 0)
+    assert np.allclose(vs3, g * 0.37 * 16.0 * np.arange(129), rtol=1e-12)
 
 
 def test_light_truth_arrival_time_of_a_one_bin_row():

@@ -166,6 +166,11 @@ MUTANTS = [
      "pk *= lam / (double)k;", "pk *= lam / (double)(k + 1);"),
     ("digitiser_weights_swapped", "Sec. 4.3 (sampling)", "light",
      "(1.0 - fr) * V[i] + fr * V[i + 1]", "fr * V[i] + (1.0 - fr) * V[i + 1]"),
+    ("scintillation_sum_without_its_last_term", "Sec. 4.2 (truncated convolution)", "light",
+     "int umax = t < L->n_trunc ? t : L->n_trunc;", "int umax = L->n_trunc < t ? L->n_trunc : (t > 0 ? t - 1 : 0);"),
+    ("digitiser_last_tick_dropped", "Sec. 4.3 (sampling)", "light",
+     "double v = i + 1 < L->n_ticks ? (1.0 - fr) * V[i] + fr * V[i + 1] : V[i];",
+     "double v = i + 1 < L->n_ticks ? (1.0 - fr) * V[i] + fr * V[i + 1] : 0.0;"),
     ("light_truth_bin_start", "Sec. 4.4 (mean arrival time)", "light",
      "m += ((double)u + 0.5) * f[u];", "m += (double)u * f[u];"),
     ("light_depth_from_z0", "Sec. 4.1 (voxel of the segment's own drift volume)", "light",
