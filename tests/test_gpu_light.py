@@ -169,3 +169,23 @@ def test_light_module_event_sampled_and_reproducible():
         sim.sim_light_event(lr.c, lr.light, lr.seg, lr.dr, wave, ws)
         torch.cuda.synchronize()
         assert torch.equal(wave, lr.wave)
+
+
+def test_light_path_window_edges():
+    """Light that starts on the window's first tick (the scintillation sum's
+    u = t term) in a window of 16 k + 1 ticks, whose last digitiser sample
+    falls on the last tick (read without a neighbour): step by step against
+    the oracle."""
+    cfg = params.small_config()
+    seg = events.scatter_event(cfg, 79, 30, max_len=0.8)
+    seg["t0"][:] = np.float32(-0.05 + 0.0004)           # 0.4 ns after the window start: tick 0
+    seg["t1"][:] = np.float32(-0.05 + 0.0004)
+    lr = LightRun(cfg, seg, n_ticks=4097).run()
+    g = lr.np()
+    lo = oracle.LightOracle(cfg, lr.L, lr.tab, -0.05, lr.T)
+    assert lr.light.n_samples == lo.n_samples == 257           # the last sample at tick 4096
+    act = g["anode"] >= 0
+    assert np.all(g["tick"][act] == 0)
+    assert g["pe"][:, 0].max() > 1.0                            # light on the first tick
+    dets = np.argsort(-g["pe"][:, 0])[:3].tolist()
+    _check_steps(cfg, seg, lr, g, dets, lo)
