@@ -258,6 +258,40 @@ def test_electronics_closed_form_gpu():
         assert np.all(np.diff(g["t_cross"]) == 16 + n_up)
 
 
+def test_electronics_adc_range_gpu():
+    """Noise off: a current far above the ADC range saturates every code at
+    2^8 - 1, and a charge that crossed the threshold and is negative when the
+    ADC samples it (a bipolar current) digitises as 0; hits bit-exact with
+    the oracle's front end on the same current."""
+    cfg = params.small_config(sigma_reset_e=0.0, sigma_disc_e=0.0, sigma_unc_e=0.0, n_ticks=1000)
+    c = sim.make_config(cfg)
+    dev = torch.device("cuda:0")
+    I = np.zeros((2, 1000), np.float32)
+    I[0, :] = 1.0e6                                   # ~1000 ADC counts' worth per tick
+    I[1, 10] = 5010.0                                  # crosses the 5000 e- threshold at tick 10
+    I[1, 11] = -20000.0                                # negative at the ADC tick (10 + 16)
+    P = 2
+    cur = torch.as_tensor(I, device=dev)
+    active = torch.tensor([3, 11], dtype=torch.int32, device=dev)
+    hits = sim.Hits(10000, dev)
+    ws = torch.zeros((sim.workspace_size(c, 0, 0, P) + 7) // 8, dtype=torch.int64, device=dev)
+    counts = ws[:4]
+    counts[1] = P
+    sim.sim_electronics(c, 0, active, cur, counts, hits, ws)
+    torch.cuda.synchronize()
+    h = hits.to_numpy(int(counts[2]))
+    o = oracle.Oracle(cfg, params.LUT)
+    for row, pid in enumerate((3, 11)):
+        g = hits_of_pixel(h, pid)
+        r = o.electronics(pid, I[row].astype(np.float64), event_id=0)
+        assert len(g["t_cross"]) == len(r["t_cross"]) > 0
+        for k in ("t_cross", "t_adc", "adc"):
+            assert np.array_equal(g[k], r[k]), (pid, k)
+        assert np.allclose(g["q"], r["q"], rtol=1e-6)
+    assert np.all(hits_of_pixel(h, 3)["adc"] == 255)
+    assert list(hits_of_pixel(h, 11)["adc"]) == [0]
+
+
 def test_event_matches_steps_and_is_deterministic(small):
     cfg, seg, lut_dev = small["cfg"], small["seg"], small["lut_dev"]
     st = small["st"]
