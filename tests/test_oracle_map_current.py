@@ -592,6 +592,40 @@ def test_nearest_lookup_conserves_charge():
 
 # ------------------------------------------------------------- whole events --
 
+def test_whole_event_map_grows_its_buffer_and_fills_its_capacity_exactly():
+    """ora_map_event on a segment mapped to more pixels than its initial
+    per-segment buffer (4096: here a 50 cm segment widened by sigma_T ~ 2 cm)
+    and with an output capacity of exactly the pair count: the same pairs as
+    the per-segment brute-force maps, in segment order."""
+    import ctypes as C
+    cfg = params.small_config(diff_tran_cm2_s=12000.0)
+    o = oracle.Oracle(cfg, params.LUT)
+    seg = _seg([(5.0, 31.0, 25.0, 0, 55.0, 31.5, 25.0, 0, 50.0), (20.0, 10.0, 40.0, 0, 20.4, 10.2, 40.1, 0, 0.5)])
+    d = o.quench_drift(seg)
+    per = [o.map_segment(seg, d, s, box=False)[0] for s in range(2)]
+    assert len(per[0]) > 4096
+    cols = d["_seg"]
+    sT = np.ascontiguousarray(d["sigma_T"], dtype=np.float64)
+    an = np.ascontiguousarray(d["anode"], dtype=np.int32)
+    P = C.POINTER
+
+    def call(cap):
+        ps, pp, pm = np.zeros(max(cap, 1), np.int64), np.zeros(max(cap, 1), np.int32), np.zeros(max(cap, 1))
+        m = o.L.ora_map_event(C.byref(o.c), 2, cols[0].ctypes.data_as(P(C.c_float)),
+                              cols[1].ctypes.data_as(P(C.c_float)), cols[4].ctypes.data_as(P(C.c_float)),
+                              cols[5].ctypes.data_as(P(C.c_float)), sT.ctypes.data_as(P(C.c_double)),
+                              an.ctypes.data_as(P(C.c_int32)), cap, ps.ctypes.data_as(P(C.c_int64)),
+                              pp.ctypes.data_as(P(C.c_int32)), pm.ctypes.data_as(P(C.c_double)))
+        return m, ps[:min(m, cap)], pp[:min(m, cap)]
+
+    n_pairs = len(per[0]) + len(per[1])
+    m, ps, pp = call(n_pairs)
+    assert m == n_pairs
+    assert np.array_equal(pp, np.concatenate(per)) and np.array_equal(ps, np.repeat([0, 1], [len(x) for x in per]))
+    m2, _, pp2 = call(n_pairs - 1)                      # one short: the count is still reported in full
+    assert m2 == n_pairs and np.array_equal(pp2, pp[:-1])
+
+
 def test_whole_event_functions_equal_the_single_pixel_ones():
     """ora_map_event is ora_map_segment_box of every segment; the many-pixel
     current and front end are pixel_current and electronics of each pixel

@@ -70,6 +70,14 @@ MUTANTS = [
      "            if (d < R) {\n                if (cnt < cap) {\n                    ids[cnt] = pid;\n"
      "                    if (margin) margin[cnt] = R - d;\n                }\n                ++cnt;\n            }\n"
      "        }\n    }\n    return cnt;\n}\n\n/* Same map"),
+    ("event_map_buffer_growth_short", "Sec. 3.3.2 (the whole event's map)", "map",
+     "            bcap = m;\n", "            bcap = m - 1;\n"),
+    ("event_map_not_recomputed_after_growth", "Sec. 3.3.2 (the whole event's map)", "map",
+     "            m = ora_map_segment_box(c, x0[s], y0[s], x1[s], y1[s], sigma_T[s], anode[s], ids, mg, bcap);\n"
+     "        }", "        }"),
+    ("event_map_capacity_off_by_one", "Sec. 3.3.2 (the whole event's map)", "map",
+     "            if (total < cap) {\n                pair_seg[total] = s;",
+     "            if (total < cap - 1) {\n                pair_seg[total] = s;"),
     ("pixel_row_and_column_transposed", "pixel ids (row-major over the anode)", "map",
      "int32_t iy = rem / nx, ix = rem % nx;", "int32_t iy = rem / ny, ix = rem % ny;"),
     ("pixel_module_order_transposed", "pixel ids (modules row-major)", "map",
