@@ -908,8 +908,19 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
+def check_ranks(gpus: int, world: int):
+    """--gpus N runs as N ranks, one per GPU, started by a launcher that sets
+    WORLD_SIZE (torch.distributed.run); a mismatch is an error, not a
+    silent single-GPU run."""
+    if gpus != world:
+        raise SystemExit(f"bench.py --gpus {gpus} needs {gpus} ranks, found WORLD_SIZE={world}: launch it with "
+                         f"python -m torch.distributed.run --nnodes=1 --nproc-per-node {gpus} "
+                         f"--master-addr 127.0.0.1 --master-port <port> bench.py --gpus {gpus} ...")
+
+
 def main():
     args = parse()
+    check_ranks(args.gpus, dist()[0])
     if args.impl == "reference":
         run_reference(args)
     else:

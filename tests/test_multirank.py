@@ -63,3 +63,13 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     bench.run_reference(ns)                              # returns at once on rank 1
     assert capsys.readouterr().out == ""
     assert bench.max_over_ranks(3.5) == 3.5              # alone: no collective
+
+
+def test_gpus_must_match_the_launched_ranks():
+    sys.path.insert(0, ROOT)
+    import bench
+    bench.check_ranks(1, 1)
+    bench.check_ranks(4, 4)
+    for gpus, world in ((2, 1), (1, 2), (8, 4)):
+        with pytest.raises(SystemExit, match="torch.distributed.run"):
+            bench.check_ranks(gpus, world)
