@@ -131,6 +131,33 @@ def test_boundary_distance_counts_as_mapped(box):
     assert 20 * 70 + 9 not in ids.tolist()
 
 
+def test_pixel_side_map_agrees_with_the_segment_side():
+    """The map read per pixel (segments_for_pixel, pair_margin: brute force
+    over the segments) equals the map read per segment; a pixel exactly R_map
+    away is mapped (margin 0), and a pixel of the other anode is never mapped
+    (margin -inf), whatever its x-y distance."""
+    from synth import events
+    cfg = params.small_config()
+    o = oracle.Oracle(cfg, params.LUT)
+    seg = events.scatter_event(cfg, 9, 25, max_len=0.8)
+    d = o.quench_drift(seg)
+    pix, _, _, _ = o.pixel_map(seg, d)
+    for p in sorted(pix)[::7]:
+        segs, mg = o.segments_for_pixel(seg, d, p)
+        assert segs.tolist() == pix[p] and np.all(mg >= 0)
+    # the boundary case of test_boundary_distance_counts_as_mapped, read per pixel
+    o2 = oracle.Oracle(_exact_cfg(n_tpc=2), LUT_SMALL)            # two drift volumes: anodes 0 and 1
+    p_, R = 0.46875, o2.map_radius(0.0)
+    xc, yc = 10.5 * p_, 20.5 * p_
+    seg2 = _seg([(xc + R, yc, 1.0 - 2 ** -12, 0, xc + R, yc, 1.0 + 2 ** -12, 0, 1.0)])
+    d2 = o2.quench_drift(seg2)
+    segs, mg = o2.segments_for_pixel(seg2, d2, 20 * 70 + 10)
+    assert segs.tolist() == [0] and mg.tolist() == [0.0]
+    assert o2.segments_for_pixel(seg2, d2, 20 * 70 + 9)[0].tolist() == []
+    other = 1 * 70 * 70 + 20 * 70 + 10                          # the same pixel of anode 1
+    assert d2["anode"][0] == 0 and o2.pair_margin(seg2, d2, 0, other) == -np.inf
+
+
 def test_box_restricted_map_equals_full_brute_force():
     cfg = params.small_config()
     o = oracle.Oracle(cfg, params.LUT)

@@ -78,6 +78,8 @@ MUTANTS = [
     ("event_map_capacity_off_by_one", "Sec. 3.3.2 (the whole event's map)", "map",
      "            if (total < cap) {\n                pair_seg[total] = s;",
      "            if (total < cap - 1) {\n                pair_seg[total] = s;"),
+    ("pair_margin_ignores_the_anode", "Sec. 3.2 (charge drifts to its own anode)", "map",
+     "    if (g != anode || anode < 0) return -INFINITY;", "    if (anode < 0) return -INFINITY;"),
     ("pixel_row_and_column_transposed", "pixel ids (row-major over the anode)", "map",
      "int32_t iy = rem / nx, ix = rem % nx;", "int32_t iy = rem / ny, ix = rem % ny;"),
     ("pixel_module_order_transposed", "pixel ids (modules row-major)", "map",
@@ -233,6 +235,8 @@ PY_MUTANTS = [
      'l.poisson_max, l.sample, l.pedestal = _f32(L["poisson_max_mean"]), _f32(L["sample_us"]), 0.0'),
     ("hit_signal_drops_adc_tick", "Sec. 3.4 (integration up to the ADC tick)", "hits",
      "return Q, full[k1 + 1] - full[k0], k0, k1", "return Q, full[k1] - full[k0], k0, k1"),
+    ("pixel_side_map_boundary_excluded", "Sec. 3.3.2 (distance exactly R_map is mapped)", "map",
+     "            if m >= 0:\n                out.append(s)", "            if m > 0:\n                out.append(s)"),
     ("cfg_w_ion_doubled", "Sec. 3.1 (Q_0 = E / W_ion)", "rng",
      'c.w_ion = _f32(cfg["w_ion_MeV"])', 'c.w_ion = 2 * _f32(cfg["w_ion_MeV"])'),
     ("light_voxel_size_off", "Sec. 4.1 (visibility voxel)", "light",
